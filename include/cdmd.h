@@ -1,0 +1,259 @@
+/*
+ * cdmd.h -- C ABI of libcdmd: compressed dynamic mode decomposition (cDMD)
+ * for video background modelling on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Erichson, Brunton & Kutz, "Compressed Dynamic Mode Decomposition for
+ * Background Modeling" (arXiv 1512.04205), Algorithm 1 with the sparse-coding
+ * mode selection of Remark 3 and the threshold mask of Eq. (thres).
+ *
+ * Letters (the paper swaps some of them; see its Appendix A):
+ *   m  pixels per frame        (paper: n)
+ *   n  frames in the clip      (paper: m)
+ *   k  sketch rows / measurements (paper: p)
+ *   r  target rank             (paper: k)
+ *   K  non-zero amplitudes kept by the sparse coding (paper: K)
+ *
+ * Data layout (all device memory unless stated otherwise):
+ *   D      uint8 video, frame-major: pixel j of frame t at D[t*ldd + j],
+ *          ldd >= m.  This is the paper's m x n video matrix stored by columns.
+ *   DY     double, k x n column-major (DY[t*k + i]): the sketch C*D.  Its
+ *          columns 0..n-2 are Y and columns 1..n-1 are Y' (Eq. YCX).
+ *   complex values are interleaved (re, im) pairs of the stated real type.
+ *   G      double complex, (n-1) x r column-major: G = V S^-1 W.
+ *   Phi    float complex, pixel-major: mode c of pixel j at Phi[j*ncols + c].
+ *   mask   uint32, frame-major: frame t holds ceil(m/32) words at
+ *          mask[t*ceil(m/32) + j/32]; pixel j is bit j%32 (LSB first).
+ *
+ * Ownership: the caller owns every pointer it passes; the library never frees
+ * them.  A context owns only its workspace and its device status word.
+ *
+ * Execution: every call that takes a stream enqueues its kernels on that
+ * stream (a cudaStream_t passed as void*; NULL = legacy default stream) and
+ * returns without synchronising.  Argument and launch errors are returned
+ * synchronously.  Numerical errors found on the device (iteration limits,
+ * rank deficiency, non-finite data) are recorded in the context's status word
+ * and returned by cdmd_status_sync().  No call traps, aborts or spins without
+ * a bound.  Calls on one context must not run concurrently from several host
+ * threads.  A context's workspace grows on first use of a larger problem; the
+ * first call at the largest size must happen before any stream capture.
+ */
+#ifndef CDMD_H
+#define CDMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CDMD_OK = 0,
+    CDMD_ERR_INVALID_ARG = 1,    /* bad size, pointer, alignment or enum     */
+    CDMD_ERR_CUDA = 2,           /* a CUDA runtime call or launch failed     */
+    CDMD_ERR_NOMEM = 3,          /* workspace allocation failed              */
+    CDMD_ERR_NOT_CONVERGED = 4,  /* an eigen-iteration hit its bound         */
+    CDMD_ERR_RANK_DEFICIENT = 5, /* sigma_r of the sketch is zero            */
+    CDMD_ERR_NONFINITE = 6,      /* NaN or Inf met in the sketch             */
+    CDMD_ERR_UNSUPPORTED = 7     /* valid request this build cannot serve    */
+} cdmd_status;
+
+/* Measurement matrix C (Section 3.3).  Gaussian and Rademacher entries are
+ * pure functions of (seed, row i, pixel j) through Philox4x32-10 and are
+ * generated inside the sketch kernel, never stored:
+ *   GAUSSIAN    counter (j, i/4, 0, 0), word i%4; words (0,1) and (2,3) are
+ *               Box-Muller pairs with U(w) = (w + 1/2) 2^-32:
+ *               z_even = sqrt(-2 ln U(w_a)) cos(2 pi U(w_b)),
+ *               z_odd  = sqrt(-2 ln U(w_a)) sin(2 pi U(w_b)).
+ *   RADEMACHER  counter (j, i/128, 1, 0); bit (i%128)%32 of word (i%128)/32;
+ *               clear = +1, set = -1.
+ * The gather forms are built once into a caller-owned cdmd_measure:
+ *   SPARSE      counter (j, i/4, 2, 0), word w = word i%4; entry non-zero iff
+ *               w < floor(2^32 * density), then +1 for even w, else -1.
+ *   ROWSAMPLE   Floyd's sampling of k distinct pixels (row i of C = the i-th
+ *               smallest selected pixel): for t = m-k .. m-1 the draw is
+ *               v = floor(((w1 << 32) | w0) * (t+1) / 2^64) from words 0,1 of
+ *               counter (t, 0, 3, 0); v is taken unless already taken, else t.
+ * The key of every counter is (seed & 0xffffffff, seed >> 32). */
+typedef enum {
+    CDMD_C_GAUSSIAN = 0,
+    CDMD_C_RADEMACHER = 1,
+    CDMD_C_SPARSE = 2,
+    CDMD_C_ROWSAMPLE = 3
+} cdmd_ctype;
+
+/* Arithmetic of the two contractions (sketch and lift).
+ *   FP32    CUDA-core FP32 FMA, FP32 partial sums over pixel chunks reduced
+ *           in FP64.
+ *   BF16X2  tcgen05 tensor cores: uint8 pixels are exact in BF16, the real
+ *           operand (C or G) is split into hi + lo BF16 parts, FP32
+ *           accumulation in tensor memory. */
+typedef enum { CDMD_PREC_FP32 = 0, CDMD_PREC_BF16X2 = 1 } cdmd_prec;
+
+/* Background of pixel j in frame t from the selected modes S:
+ *   MODULUS  | sum_{s in S} Phi_js beta_s lambda_s^t |        (time-varying)
+ *   REAL     Re( sum_{s in S} Phi_js beta_s lambda_s^t )     (footnote of
+ *            Eq. DMDTerms: only the real part is kept)
+ *   STATIC   | sum_{s in S} Phi_js beta_s |, the x_BG = Phi beta of
+ *            Section 2.3, the same for every frame. */
+typedef enum { CDMD_BG_MODULUS = 0, CDMD_BG_REAL = 1, CDMD_BG_STATIC = 2 } cdmd_bgmode;
+
+/* Amplitudes / mode selection (Algorithm 1 step 9, Remark 3).
+ *   OMP    orthogonal matching pursuit on the compressed modes Phi_Y with
+ *          target y1 = DY[:,0], K picks.
+ *   LSTSQ  least squares on all r compressed modes (OMP with K = r). */
+typedef enum { CDMD_SEL_OMP = 0, CDMD_SEL_LSTSQ = 1 } cdmd_selector;
+
+typedef struct cdmd_ctx cdmd_ctx;
+
+/* Gather-form measurement matrix, device arrays owned by the caller.
+ *   SPARSE     CSC by pixel: col_ptr[m+1] (int64), row_idx[nnz] (int32):
+ *              bits 0..30 = row i, bit 31 set = entry -1 (clear = +1).
+ *   ROWSAMPLE  rows[k] (int64): the selected pixel of row i, increasing.
+ * cdmd_measure_build fills it; its capacity fields say how large the caller's
+ * arrays are. */
+typedef struct {
+    cdmd_ctype ctype;
+    int32_t k;
+    int64_t m;
+    uint64_t seed;
+    double density;
+    int64_t* col_ptr;       /* SPARSE: m+1 entries                         */
+    int32_t* row_idx;       /* SPARSE: nnz_capacity entries                */
+    int64_t nnz_capacity;   /* SPARSE: entries available at row_idx        */
+    int64_t* rows;          /* ROWSAMPLE: k entries                        */
+} cdmd_measure;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context bound to CUDA device `device`.  Allocates the device
+ * status word.  Returns CDMD_ERR_INVALID_ARG for a NULL ctx or bad device. */
+cdmd_status cdmd_create(cdmd_ctx** ctx, int device);
+
+/* Free the context's workspace and status word (NULL is ignored).  Waits for
+ * the device to finish work that uses the workspace. */
+void cdmd_destroy(cdmd_ctx* ctx);
+
+/* Message of the last error returned on this host thread ("" if none). */
+const char* cdmd_last_error(void);
+
+/* Name of a status code. */
+const char* cdmd_status_string(cdmd_status s);
+
+/* Synchronise `stream`, then return and clear the numerical status recorded
+ * on the device by the calls enqueued so far (CDMD_OK if none). */
+cdmd_status cdmd_status_sync(cdmd_ctx* ctx, void* stream);
+
+/* ---- measurement matrices (Section 3.3) ---------------------------------- */
+
+/* Exact number of non-zeros of the SPARSE matrix for (m, k, seed, density),
+ * counted on the device and returned on the host (synchronises `stream`).
+ * Use it to size row_idx before cdmd_measure_build. */
+cdmd_status cdmd_measure_sparse_nnz(cdmd_ctx* ctx, int64_t m, int k, uint64_t seed,
+                                    double density, int64_t* nnz, void* stream);
+
+/* Fill a SPARSE or ROWSAMPLE cdmd_measure (fields ctype, k, m, seed, density
+ * and the arrays must be set).  Enqueued on `stream`.  ROWSAMPLE needs
+ * 1 <= k <= m; SPARSE needs 0 < density <= 1 and nnz_capacity >= the count
+ * from cdmd_measure_sparse_nnz (else CDMD_ERR_INVALID_ARG). */
+cdmd_status cdmd_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, void* stream);
+
+/* ---- pass (a): sketch  DY = C D  (Algorithm 1 steps 2-3, Eq. YCX) -------- */
+
+/* Dense Gaussian / Rademacher C generated in-kernel from `seed` (never
+ * stored).  D: m x n frames (n >= 2), ldd >= m.  DY: k x n doubles
+ * (column-major, ld = k), overwritten.  prec selects FP32 CUDA-core or
+ * BF16 hi+lo tensor-core arithmetic (BF16X2 needs n <= 256 and is defined for
+ * Gaussian C; Rademacher entries are exact in BF16). */
+cdmd_status cdmd_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                        cdmd_ctype ctype, int k, uint64_t seed, cdmd_prec prec,
+                        double* DY, void* stream);
+
+/* Sparse or single-pixel C applied as a gather (one pass over D; exact
+ * integer sums).  meas must have been filled by cdmd_measure_build for the
+ * same m.  DY as for cdmd_sketch with k = meas->k. */
+cdmd_status cdmd_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                               const cdmd_measure* meas, double* DY, void* stream);
+
+/* ---- small solves on the device (Algorithm 1 steps 4-7, 9; Remark 3) ----- */
+
+/* From DY (k x n, ld = k) compute, in FP64 on the device:
+ *   sigma  [r]            leading singular values of Y = DY[:, 0:n-1]
+ *   lambda [2r]           eigenvalues of A~ = U^T Y' V S^-1 (complex)
+ *   G      [2 (n-1) r]    V S^-1 W, column-major complex (eigenvectors W of
+ *                         unit 2-norm, largest-modulus entry real positive)
+ *   PhiY   [2 k r]        Y' G, column-major complex (may be NULL)
+ *   beta   [2r]           amplitude of each mode, 0 for modes not selected
+ *   sel    [K]            selected modes in pick order, -1 after the last
+ *   nsel   [1]            number of modes selected
+ * Eigenvalues are ordered by descending modulus (conjugate pairs adjacent,
+ * positive imaginary part first).  The SVD is taken from the eigen-
+ * decomposition of the Gram matrix Y^T Y (method of snapshots).
+ * Requires 1 <= r <= min(k, n-1), 1 <= K <= r, n <= 512, k >= 1. */
+cdmd_status cdmd_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r, int K,
+                           cdmd_selector selector, double* sigma, double* lambda,
+                           double* G, double* PhiY, double* beta, int32_t* sel,
+                           int32_t* nsel, void* stream);
+
+/* ---- pass (b): mode lift  Phi = X' G  (Algorithm 1 step 8, Eq. cDMDModes) */
+
+/* Phi[j*ncols + c] = sum_{t=0}^{n-2} D[(t+1)*ldd + j] * G[:, cols[c]] for the
+ * ncols modes listed in `cols` (device int32, NULL = modes 0..ncols-1; a
+ * negative entry yields a zero column).  G: (n-1) x r complex double.
+ * Phi: m x ncols complex float, pixel-major.  ncols <= 64. */
+cdmd_status cdmd_lift(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                      const double* G, int r, const int32_t* cols, int ncols,
+                      cdmd_prec prec, float* Phi, void* stream);
+
+/* ---- pass (c): background, threshold, bit-packed mask (Eq. DMDTerms, thres)
+ *
+ * For column c of Phi (c < ncols) the mode is s = cols[c] (device int32;
+ * c skipped when negative); its amplitude is beta[s] and eigenvalue
+ * lambda[s] (both complex double, length r).  mask bit (j, t) is set iff
+ * |D[t*ldd + j] - bg_jt| > tau with bg_jt as selected by `mode`.  bg, if not
+ * NULL, receives bg_jt as float, frame-major (bg[t*m + j]). */
+cdmd_status cdmd_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                          const float* Phi, int ncols, const int32_t* cols,
+                          const double* beta, const double* lambda, int r,
+                          float tau, cdmd_bgmode mode, uint32_t* mask, float* bg,
+                          void* stream);
+
+/* ---- whole pipeline ------------------------------------------------------ */
+
+typedef struct {
+    int32_t k;              /* sketch rows                                  */
+    int32_t r;              /* target rank                                  */
+    int32_t K;              /* modes kept by the selection                  */
+    cdmd_ctype ctype;       /* GAUSSIAN or RADEMACHER (dense, in-kernel)    */
+    uint64_t seed;
+    cdmd_prec prec;
+    cdmd_selector selector;
+    cdmd_bgmode bgmode;
+    float tau;              /* threshold in grey levels                     */
+} cdmd_params;
+
+/* Sketch -> decompose -> lift of the selected modes -> subtract, on device
+ * buffers, enqueued on `stream`; intermediates live in the context's
+ * workspace and stay valid until the next call on the context (see
+ * cdmd_workspace_views).  mask as described above. */
+cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                     const cdmd_params* p, uint32_t* mask, void* stream);
+
+/* cdmd_run on host memory: copies D_host (m x n frame-major, ldd = m; pinned
+ * memory gives full copy bandwidth) to the device, runs the pipeline and
+ * copies the mask back to mask_host, all on `stream`, then synchronises the
+ * stream and returns the numerical status as cdmd_status_sync does. */
+cdmd_status cdmd_run_host(cdmd_ctx* ctx, const uint8_t* D_host, int64_t m, int n,
+                          const cdmd_params* p, uint32_t* mask_host, void* stream);
+
+/* Device pointers to the intermediates of the last cdmd_run on ctx (any
+ * output pointer may be NULL).  Valid until the next call on the context. */
+cdmd_status cdmd_workspace_views(cdmd_ctx* ctx, double** DY, double** sigma, double** lambda,
+                                 double** G, double** beta, int32_t** sel, int32_t** nsel,
+                                 float** Phi);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDMD_H */

@@ -1,0 +1,291 @@
+"""Python binding of libcdmd (ctypes): argument marshalling only.
+
+Every function here forwards to the C ABI declared in include/cdmd.h under the
+same name; all arithmetic runs in the library's CUDA kernels.  PyTorch only
+provides device memory and the current CUDA stream.  The library must be
+built (paper_1512_04205_gb300.build); importing without it fails loudly.
+
+Tensor conventions (torch views of the C layouts):
+  D      uint8 (n, m) frame-major, row stride ldd >= m (the paper's m x n video)
+  DY     float64 (n, k): DY[t, i] = (C D)[i, t]  (C layout: k x n column-major)
+  lambda complex128 (r,); G complex128 (r, n-1) (G[c, t] = G_tc);
+  PhiY   complex128 (r, k); beta complex128 (r,); sel int32 (K,)
+  Phi    complex64 (m, ncols) pixel-major
+  mask   int32 (n, ceil(m/32)) holding the uint32 words (bit j%32 of word j//32)
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcdmd.so")
+
+CDMD_OK = 0
+STATUS_NAMES = {0: "CDMD_OK", 1: "CDMD_ERR_INVALID_ARG", 2: "CDMD_ERR_CUDA", 3: "CDMD_ERR_NOMEM",
+                4: "CDMD_ERR_NOT_CONVERGED", 5: "CDMD_ERR_RANK_DEFICIENT", 6: "CDMD_ERR_NONFINITE",
+                7: "CDMD_ERR_UNSUPPORTED"}
+CTYPES = {"gaussian": 0, "rademacher": 1, "sparse": 2, "rowsample": 3}
+PRECS = {"fp32": 0, "bf16x2": 1}
+BGMODES = {"modulus": 0, "real": 1, "static": 2}
+SELECTORS = {"omp": 0, "lstsq": 1}
+
+EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_string", "cdmd_status_sync",
+            "cdmd_measure_sparse_nnz", "cdmd_measure_build", "cdmd_sketch", "cdmd_sketch_gather",
+            "cdmd_decompose", "cdmd_lift", "cdmd_subtract", "cdmd_run", "cdmd_run_host",
+            "cdmd_workspace_views"]
+
+
+class CdmdError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class cdmd_measure(ctypes.Structure):
+    _fields_ = [("ctype", ctypes.c_int), ("k", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("density", ctypes.c_double),
+                ("col_ptr", ctypes.c_void_p), ("row_idx", ctypes.c_void_p),
+                ("nnz_capacity", ctypes.c_int64), ("rows", ctypes.c_void_p)]
+
+
+class cdmd_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("r", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("ctype", ctypes.c_int), ("seed", ctypes.c_uint64), ("prec", ctypes.c_int),
+                ("selector", ctypes.c_int), ("bgmode", ctypes.c_int), ("tau", ctypes.c_float)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libcdmd.so (raises if it has not been built) and declare prototypes."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libcdmd is not built ({path} missing); run "
+                          "python -m paper_1512_04205_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, u64, dbl, flt = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                   ctypes.c_double, ctypes.c_float)
+    proto = {
+        "cdmd_create": [ctypes.POINTER(vp), ctypes.c_int],
+        "cdmd_destroy": [vp],
+        "cdmd_last_error": [],
+        "cdmd_status_string": [ctypes.c_int],
+        "cdmd_status_sync": [vp, vp],
+        "cdmd_measure_sparse_nnz": [vp, i64, ctypes.c_int, u64, dbl, ctypes.POINTER(i64), vp],
+        "cdmd_measure_build": [vp, ctypes.POINTER(cdmd_measure), vp],
+        "cdmd_sketch": [vp, vp, i64, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, u64, ctypes.c_int, vp, vp],
+        "cdmd_sketch_gather": [vp, vp, i64, ctypes.c_int, i64, ctypes.POINTER(cdmd_measure), vp, vp],
+        "cdmd_decompose": [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           vp, vp, vp, vp, vp, vp, vp, vp],
+        "cdmd_lift": [vp, vp, i64, ctypes.c_int, i64, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp],
+        "cdmd_subtract": [vp, vp, i64, ctypes.c_int, i64, vp, ctypes.c_int, vp, vp, vp, ctypes.c_int, flt,
+                          ctypes.c_int, vp, vp, vp],
+        "cdmd_run": [vp, vp, i64, ctypes.c_int, i64, ctypes.POINTER(cdmd_params), vp, vp],
+        "cdmd_run_host": [vp, vp, i64, ctypes.c_int, ctypes.POINTER(cdmd_params), vp, vp],
+        "cdmd_workspace_views": [vp] + [ctypes.POINTER(vp)] * 8,
+    }
+    for name, args in proto.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.cdmd_destroy.restype = None
+    lib.cdmd_last_error.restype = ctypes.c_char_p
+    lib.cdmd_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != CDMD_OK:
+        msg = load_library().cdmd_last_error().decode(errors="replace")
+        raise CdmdError(status, msg)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _video(D):
+    import torch
+    if D.dtype != torch.uint8 or D.dim() != 2 or D.stride(1) != 1 or not D.is_cuda:
+        raise ValueError("D must be a CUDA uint8 tensor (n, m) with unit pixel stride")
+    n, m = D.shape
+    return n, m, D.stride(0)
+
+
+class Context:
+    """Owns a cdmd_ctx (workspace + device status word) on one device."""
+
+    def __init__(self, device=0):
+        self.lib = load_library()
+        self.handle = ctypes.c_void_p()
+        _check(self.lib.cdmd_create(ctypes.byref(self.handle), int(device)))
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            self.lib.cdmd_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cdmd_status_sync(ctx, stream=None):
+    """Synchronise the stream and raise if the device recorded an error."""
+    _check(ctx.lib.cdmd_status_sync(ctx.handle, _stream(stream)))
+
+
+def cdmd_sketch(ctx, D, k, seed, ctype="gaussian", prec="fp32", DY=None, stream=None):
+    """Pass (a): DY = C D with C generated in-kernel (returns (n, k) float64)."""
+    import torch
+    n, m, ldd = _video(D)
+    if DY is None:
+        DY = torch.empty((n, k), dtype=torch.float64, device=D.device)
+    _check(ctx.lib.cdmd_sketch(ctx.handle, _ptr(D), m, n, ldd, CTYPES[ctype], int(k), int(seed) & (2**64 - 1),
+                               PRECS[prec], _ptr(DY), _stream(stream)))
+    return DY
+
+
+class Measure:
+    """Device-resident SPARSE or ROWSAMPLE measurement matrix."""
+
+    def __init__(self, ctx, ctype, m, k, seed, density=0.0, stream=None):
+        import torch
+        self.struct = cdmd_measure()
+        s = self.struct
+        s.ctype, s.k, s.m, s.seed, s.density = CTYPES[ctype], int(k), int(m), int(seed) & (2**64 - 1), float(density)
+        dev = torch.device("cuda", ctx.device)
+        self.col_ptr = self.row_idx = self.rows = None
+        if ctype == "sparse":
+            nnz = ctypes.c_int64()
+            _check(ctx.lib.cdmd_measure_sparse_nnz(ctx.handle, int(m), int(k), s.seed, float(density),
+                                                   ctypes.byref(nnz), _stream(stream)))
+            self.nnz = nnz.value
+            self.col_ptr = torch.empty(int(m) + 1, dtype=torch.int64, device=dev)
+            self.row_idx = torch.empty(max(1, self.nnz), dtype=torch.int32, device=dev)
+            s.col_ptr, s.row_idx, s.nnz_capacity = self.col_ptr.data_ptr(), self.row_idx.data_ptr(), self.row_idx.numel()
+        elif ctype == "rowsample":
+            self.rows = torch.empty(int(k), dtype=torch.int64, device=dev)
+            s.rows = self.rows.data_ptr()
+        else:
+            raise ValueError("Measure holds SPARSE or ROWSAMPLE matrices")
+        _check(ctx.lib.cdmd_measure_build(ctx.handle, ctypes.byref(s), _stream(stream)))
+
+
+def cdmd_sketch_gather(ctx, D, meas, DY=None, stream=None):
+    """Pass (a) with a sparse or single-pixel C (returns (n, k) float64)."""
+    import torch
+    n, m, ldd = _video(D)
+    if DY is None:
+        DY = torch.empty((n, meas.struct.k), dtype=torch.float64, device=D.device)
+    _check(ctx.lib.cdmd_sketch_gather(ctx.handle, _ptr(D), m, n, ldd, ctypes.byref(meas.struct), _ptr(DY),
+                                      _stream(stream)))
+    return DY
+
+
+def cdmd_decompose(ctx, DY, r, K, selector="omp", with_phiy=False, stream=None):
+    """Steps 4-7 and 9 on the device; returns a dict of device tensors."""
+    import torch
+    n, k = DY.shape
+    dev = DY.device
+    out = dict(sigma=torch.empty(r, dtype=torch.float64, device=dev),
+               lam=torch.empty((r, 2), dtype=torch.float64, device=dev),
+               G=torch.empty((r, n - 1, 2), dtype=torch.float64, device=dev),
+               PhiY=torch.empty((r, k, 2), dtype=torch.float64, device=dev) if with_phiy else None,
+               beta=torch.empty((r, 2), dtype=torch.float64, device=dev),
+               sel=torch.empty(K, dtype=torch.int32, device=dev),
+               nsel=torch.empty(1, dtype=torch.int32, device=dev))
+    _check(ctx.lib.cdmd_decompose(ctx.handle, _ptr(DY), int(k), int(n), int(r), int(K), SELECTORS[selector],
+                                  _ptr(out["sigma"]), _ptr(out["lam"]), _ptr(out["G"]), _ptr(out["PhiY"]),
+                                  _ptr(out["beta"]), _ptr(out["sel"]), _ptr(out["nsel"]), _stream(stream)))
+    return out
+
+
+def cdmd_lift(ctx, D, G, cols=None, ncols=None, prec="fp32", Phi=None, stream=None):
+    """Pass (b): Phi = X' G[:, cols] (returns (m, ncols, 2) float32)."""
+    import torch
+    n, m, ldd = _video(D)
+    r = G.shape[0]
+    if ncols is None:
+        ncols = cols.numel() if cols is not None else r
+    if Phi is None:
+        Phi = torch.empty((m, ncols, 2), dtype=torch.float32, device=D.device)
+    _check(ctx.lib.cdmd_lift(ctx.handle, _ptr(D), m, n, ldd, _ptr(G), int(r), _ptr(cols), int(ncols), PRECS[prec],
+                             _ptr(Phi), _stream(stream)))
+    return Phi
+
+
+def cdmd_subtract(ctx, D, Phi, beta, lam, tau, cols=None, mode="modulus", want_bg=False, mask=None, stream=None):
+    """Pass (c): bit-packed foreground mask (n, ceil(m/32)) int32, optional bg."""
+    import torch
+    n, m, ldd = _video(D)
+    ncols = Phi.shape[1]
+    r = beta.shape[0]
+    if mask is None:
+        mask = torch.empty((n, (m + 31) // 32), dtype=torch.int32, device=D.device)
+    bg = torch.empty((n, m), dtype=torch.float32, device=D.device) if want_bg else None
+    _check(ctx.lib.cdmd_subtract(ctx.handle, _ptr(D), m, n, ldd, _ptr(Phi), int(ncols), _ptr(cols), _ptr(beta),
+                                 _ptr(lam), int(r), float(tau), BGMODES[mode], _ptr(mask), _ptr(bg),
+                                 _stream(stream)))
+    return (mask, bg) if want_bg else mask
+
+
+def make_params(k, r, K, tau, seed=0, ctype="gaussian", prec="fp32", selector="omp", bgmode="modulus"):
+    return cdmd_params(int(k), int(r), int(K), CTYPES[ctype], int(seed) & (2**64 - 1), PRECS[prec],
+                       SELECTORS[selector], BGMODES[bgmode], float(tau))
+
+
+def cdmd_run(ctx, D, params, mask=None, stream=None):
+    """Whole pipeline on a device video; returns the mask (n, ceil(m/32)) int32."""
+    import torch
+    n, m, ldd = _video(D)
+    if mask is None:
+        mask = torch.empty((n, (m + 31) // 32), dtype=torch.int32, device=D.device)
+    _check(ctx.lib.cdmd_run(ctx.handle, _ptr(D), m, n, ldd, ctypes.byref(params), _ptr(mask), _stream(stream)))
+    return mask
+
+
+def cdmd_run_host(ctx, D_host, params, mask_host=None, stream=None):
+    """Whole pipeline on a host video (n, m) uint8 (pinned torch tensor or
+    numpy array); copies in, runs, copies the mask out and synchronises."""
+    import torch
+    if isinstance(D_host, np.ndarray):
+        D_host = torch.from_numpy(np.ascontiguousarray(D_host))
+    if D_host.dtype != torch.uint8 or D_host.dim() != 2 or not D_host.is_contiguous() or D_host.is_cuda:
+        raise ValueError("D_host must be a contiguous host uint8 tensor (n, m)")
+    n, m = D_host.shape
+    if mask_host is None:
+        mask_host = torch.empty((n, (m + 31) // 32), dtype=torch.int32, pin_memory=D_host.is_pinned())
+    _check(ctx.lib.cdmd_run_host(ctx.handle, _ptr(D_host), m, n, ctypes.byref(params), _ptr(mask_host),
+                                 _stream(stream)))
+    return mask_host
+
+
+def cdmd_workspace_views(ctx):
+    """Raw device pointers of the last cdmd_run's intermediates."""
+    ptrs = [ctypes.c_void_p() for _ in range(8)]
+    _check(ctx.lib.cdmd_workspace_views(ctx.handle, *[ctypes.byref(p) for p in ptrs]))
+    keys = ["DY", "sigma", "lambda", "G", "beta", "sel", "nsel", "Phi"]
+    return {k: p.value for k, p in zip(keys, ptrs)}
+
+
+def unpack_mask(mask, m):
+    """(n, words) int32 mask -> (m, n) bool array (host), pixel j = bit j%32."""
+    words = np.asarray(mask.cpu().numpy() if hasattr(mask, "cpu") else mask).view(np.uint32)
+    bits = np.unpackbits(words.view(np.uint8), axis=1, bitorder="little")
+    return bits[:, :m].astype(bool).T

@@ -1,0 +1,373 @@
+// extern "C" entry points of libcdmd: argument checks, workspace, dispatch.
+#include <cstdarg>
+#include <cstring>
+#include <vector>
+
+#include "cdmd_internal.cuh"
+
+namespace cdmd {
+
+namespace {
+thread_local char g_last_error[512] = "";
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+}  // namespace
+
+cdmd_status fail(cdmd_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+cdmd_status cuda_fail(cudaError_t e, const char* what) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+    return (e == cudaErrorMemoryAllocation) ? CDMD_ERR_NOMEM : CDMD_ERR_CUDA;
+}
+
+void clear_error() { g_last_error[0] = '\0'; }
+
+cdmd_status ensure_buffer(cdmd_ctx* ctx, BufferId id, size_t bytes, void** out) {
+    Buffer& b = ctx->buf[id];
+    if (bytes == 0) bytes = 256;
+    if (b.bytes < bytes) {
+        if (b.ptr != nullptr) {
+            CDMD_CHECK_CUDA(cudaDeviceSynchronize());
+            CDMD_CHECK_CUDA(cudaFree(b.ptr));
+            b.ptr = nullptr;
+            b.bytes = 0;
+        }
+        const size_t want = ((bytes + bytes / 8) + 255) & ~static_cast<size_t>(255);
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(CDMD_ERR_NOMEM, "workspace allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+        }
+        b.ptr = p;
+        b.bytes = want;
+    }
+    *out = b.ptr;
+    return CDMD_OK;
+}
+
+static cdmd_status check_video(const uint8_t* D, int64_t m, int n, int64_t ldd) {
+    CDMD_REQUIRE(D != nullptr, "D is NULL");
+    CDMD_REQUIRE(m >= 1, "m must be >= 1 (got %lld)", static_cast<long long>(m));
+    CDMD_REQUIRE(m <= 0x7fffffffLL, "m must fit a 32-bit Philox counter word (got %lld)", static_cast<long long>(m));
+    CDMD_REQUIRE(n >= 2, "n must be >= 2 (got %d)", n);
+    CDMD_REQUIRE(ldd >= m, "ldd (%lld) must be >= m (%lld)", static_cast<long long>(ldd), static_cast<long long>(m));
+    return CDMD_OK;
+}
+
+}  // namespace cdmd
+
+using namespace cdmd;
+
+extern "C" {
+
+const char* cdmd_last_error(void) { return g_last_error; }
+
+const char* cdmd_status_string(cdmd_status s) {
+    switch (s) {
+        case CDMD_OK: return "CDMD_OK";
+        case CDMD_ERR_INVALID_ARG: return "CDMD_ERR_INVALID_ARG";
+        case CDMD_ERR_CUDA: return "CDMD_ERR_CUDA";
+        case CDMD_ERR_NOMEM: return "CDMD_ERR_NOMEM";
+        case CDMD_ERR_NOT_CONVERGED: return "CDMD_ERR_NOT_CONVERGED";
+        case CDMD_ERR_RANK_DEFICIENT: return "CDMD_ERR_RANK_DEFICIENT";
+        case CDMD_ERR_NONFINITE: return "CDMD_ERR_NONFINITE";
+        case CDMD_ERR_UNSUPPORTED: return "CDMD_ERR_UNSUPPORTED";
+    }
+    return "CDMD_ERR_UNKNOWN";
+}
+
+cdmd_status cdmd_create(cdmd_ctx** ctx, int device) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    *ctx = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return cuda_fail(e, "cudaGetDeviceCount"); }
+    CDMD_REQUIRE(device >= 0 && device < count, "device %d out of range (%d devices)", device, count);
+    DeviceGuard g(device);
+    cdmd_ctx* c = new cdmd_ctx();
+    c->device = device;
+    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        if (c->d_status) cudaFree(c->d_status);
+        delete c;
+        return cuda_fail(e, "cdmd_create");
+    }
+    *ctx = c;
+    return CDMD_OK;
+}
+
+void cdmd_destroy(cdmd_ctx* ctx) {
+    if (ctx == nullptr) return;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& b : ctx->buf)
+        if (b.ptr) cudaFree(b.ptr);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+}
+
+cdmd_status cdmd_status_sync(cdmd_ctx* ctx, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CDMD_CHECK_CUDA(cudaStreamSynchronize(s));
+    int h = 0;
+    CDMD_CHECK_CUDA(cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CDMD_CHECK_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    if (h != 0) return fail(static_cast<cdmd_status>(h), "device reported %s", cdmd_status_string(static_cast<cdmd_status>(h)));
+    return CDMD_OK;
+}
+
+cdmd_status cdmd_measure_sparse_nnz(cdmd_ctx* ctx, int64_t m, int k, uint64_t seed, double density, int64_t* nnz,
+                                    void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && nnz != nullptr, "ctx or nnz is NULL");
+    CDMD_REQUIRE(m >= 1 && m <= 0x7fffffffLL, "m out of range");
+    CDMD_REQUIRE(k >= 1, "k must be >= 1");
+    CDMD_REQUIRE(density > 0.0 && density <= 1.0, "density must be in (0, 1]");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t* counts = nullptr;
+    cdmd_status st = ensure_buffer(ctx, BUF_SMALL, static_cast<size_t>(m + 1) * sizeof(int64_t),
+                                   reinterpret_cast<void**>(&counts));
+    if (st != CDMD_OK) return st;
+    st = launch_measure_sparse_count(ctx, m, k, seed, density, counts, s);
+    if (st != CDMD_OK) return st;
+    std::vector<int64_t> h(static_cast<size_t>(m));
+    CDMD_CHECK_CUDA(cudaMemcpyAsync(h.data(), counts, m * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CDMD_CHECK_CUDA(cudaStreamSynchronize(s));
+    int64_t total = 0;
+    for (int64_t v : h) total += v;
+    *nnz = total;
+    return CDMD_OK;
+}
+
+cdmd_status cdmd_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && meas != nullptr, "ctx or meas is NULL");
+    CDMD_REQUIRE(meas->m >= 1 && meas->m <= 0x7fffffffLL, "meas->m out of range");
+    CDMD_REQUIRE(meas->k >= 1, "meas->k must be >= 1");
+    DeviceGuard g(ctx->device);
+    if (meas->ctype == CDMD_C_ROWSAMPLE) {
+        CDMD_REQUIRE(meas->k <= meas->m, "ROWSAMPLE needs k <= m");
+        CDMD_REQUIRE(meas->rows != nullptr, "meas->rows is NULL");
+    } else if (meas->ctype == CDMD_C_SPARSE) {
+        CDMD_REQUIRE(meas->density > 0.0 && meas->density <= 1.0, "density must be in (0, 1]");
+        CDMD_REQUIRE(meas->col_ptr != nullptr && meas->row_idx != nullptr, "CSC arrays are NULL");
+        CDMD_REQUIRE(meas->k <= 0x7fffffff, "k too large");
+        int64_t nnz = 0;
+        cdmd_status st = cdmd_measure_sparse_nnz(ctx, meas->m, meas->k, meas->seed, meas->density, &nnz, stream);
+        if (st != CDMD_OK) return st;
+        CDMD_REQUIRE(meas->nnz_capacity >= nnz, "nnz_capacity %lld < nnz %lld", static_cast<long long>(meas->nnz_capacity),
+                     static_cast<long long>(nnz));
+    } else {
+        return fail(CDMD_ERR_INVALID_ARG, "cdmd_measure_build takes SPARSE or ROWSAMPLE");
+    }
+    return launch_measure_build(ctx, meas, static_cast<cudaStream_t>(stream));
+}
+
+cdmd_status cdmd_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, cdmd_ctype ctype, int k,
+                        uint64_t seed, cdmd_prec prec, double* DY, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    cdmd_status st = check_video(D, m, n, ldd);
+    if (st != CDMD_OK) return st;
+    CDMD_REQUIRE(DY != nullptr, "DY is NULL");
+    CDMD_REQUIRE(k >= 1 && k <= (1 << 20), "k must be in [1, 2^20] (got %d)", k);
+    CDMD_REQUIRE(ctype == CDMD_C_GAUSSIAN || ctype == CDMD_C_RADEMACHER,
+                 "cdmd_sketch generates GAUSSIAN or RADEMACHER C; use cdmd_sketch_gather for the others");
+    CDMD_REQUIRE(aligned(DY, 8), "DY must be 8-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == CDMD_PREC_FP32) return launch_sketch_fp32(ctx, D, m, n, ldd, ctype, k, seed, DY, s);
+    if (prec == CDMD_PREC_BF16X2) {
+        CDMD_REQUIRE(n <= 256, "BF16X2 sketch needs n <= 256 (got %d)", n);
+        return launch_sketch_tc(ctx, D, m, n, ldd, ctype, k, seed, DY, s);
+    }
+    return fail(CDMD_ERR_INVALID_ARG, "unknown precision %d", static_cast<int>(prec));
+}
+
+cdmd_status cdmd_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                               const cdmd_measure* meas, double* DY, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && meas != nullptr, "ctx or meas is NULL");
+    cdmd_status st = check_video(D, m, n, ldd);
+    if (st != CDMD_OK) return st;
+    CDMD_REQUIRE(DY != nullptr, "DY is NULL");
+    CDMD_REQUIRE(meas->m == m, "meas was built for m = %lld, video has m = %lld", static_cast<long long>(meas->m),
+                 static_cast<long long>(m));
+    CDMD_REQUIRE(meas->ctype == CDMD_C_SPARSE || meas->ctype == CDMD_C_ROWSAMPLE, "meas must be SPARSE or ROWSAMPLE");
+    if (meas->ctype == CDMD_C_SPARSE) {
+        CDMD_REQUIRE(meas->col_ptr && meas->row_idx, "CSC arrays are NULL");
+        CDMD_REQUIRE(static_cast<size_t>(meas->k) * 16 * sizeof(int32_t) <= 200 * 1024,
+                     "SPARSE gather supports k <= %d", static_cast<int>(200 * 1024 / 64));
+    } else {
+        CDMD_REQUIRE(meas->rows != nullptr, "meas->rows is NULL");
+    }
+    DeviceGuard g(ctx->device);
+    return launch_sketch_gather(ctx, D, m, n, ldd, meas, DY, static_cast<cudaStream_t>(stream));
+}
+
+cdmd_status cdmd_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r, int K, cdmd_selector selector,
+                           double* sigma, double* lambda, double* G, double* PhiY, double* beta, int32_t* sel,
+                           int32_t* nsel, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(DY && sigma && lambda && G && beta && sel && nsel, "a required pointer is NULL");
+    CDMD_REQUIRE(n >= 2 && n <= 512, "n must be in [2, 512] (got %d)", n);
+    CDMD_REQUIRE(k >= 1, "k must be >= 1");
+    CDMD_REQUIRE(r >= 1 && r <= 32 && r <= k && r <= n - 1, "r must be in [1, min(32, k, n-1)] (got %d)", r);
+    CDMD_REQUIRE(K >= 1 && K <= r, "K must be in [1, r] (got %d)", K);
+    CDMD_REQUIRE(selector == CDMD_SEL_OMP || selector == CDMD_SEL_LSTSQ, "unknown selector %d", static_cast<int>(selector));
+    DeviceGuard g(ctx->device);
+    return launch_decompose(ctx, DY, k, n, r, K, selector, sigma, lambda, G, PhiY, beta, sel, nsel,
+                            static_cast<cudaStream_t>(stream));
+}
+
+cdmd_status cdmd_lift(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const double* G, int r,
+                      const int32_t* cols, int ncols, cdmd_prec prec, float* Phi, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    cdmd_status st = check_video(D, m, n, ldd);
+    if (st != CDMD_OK) return st;
+    CDMD_REQUIRE(G != nullptr && Phi != nullptr, "G or Phi is NULL");
+    CDMD_REQUIRE(n <= 512, "n must be <= 512");
+    CDMD_REQUIRE(r >= 1 && ncols >= 1 && ncols <= 64, "need r >= 1 and 1 <= ncols <= 64");
+    CDMD_REQUIRE(cols != nullptr || ncols <= r, "ncols > r needs an explicit cols list");
+    CDMD_REQUIRE(aligned(Phi, 8), "Phi must be 8-byte aligned");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == CDMD_PREC_FP32) return launch_lift_fp32(ctx, D, m, n, ldd, G, r, cols, ncols, Phi, s);
+    if (prec == CDMD_PREC_BF16X2) return launch_lift_tc(ctx, D, m, n, ldd, G, r, cols, ncols, Phi, s);
+    return fail(CDMD_ERR_INVALID_ARG, "unknown precision %d", static_cast<int>(prec));
+}
+
+cdmd_status cdmd_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const float* Phi, int ncols,
+                          const int32_t* cols, const double* beta, const double* lambda, int r, float tau,
+                          cdmd_bgmode mode, uint32_t* mask, float* bg, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    cdmd_status st = check_video(D, m, n, ldd);
+    if (st != CDMD_OK) return st;
+    CDMD_REQUIRE(Phi && beta && lambda && mask, "a required pointer is NULL");
+    CDMD_REQUIRE(n <= 512, "n must be <= 512");
+    CDMD_REQUIRE(ncols >= 1 && ncols <= 32, "ncols must be in [1, 32]");
+    CDMD_REQUIRE(r >= 1, "r must be >= 1");
+    CDMD_REQUIRE(cols != nullptr || ncols <= r, "ncols > r needs an explicit cols list");
+    CDMD_REQUIRE(tau >= 0.0f, "tau must be >= 0");
+    CDMD_REQUIRE(mode == CDMD_BG_MODULUS || mode == CDMD_BG_REAL || mode == CDMD_BG_STATIC, "unknown background mode");
+    CDMD_REQUIRE(aligned(Phi, 8), "Phi must be 8-byte aligned");
+    DeviceGuard g(ctx->device);
+    return launch_subtract(ctx, D, m, n, ldd, Phi, ncols, cols, beta, lambda, r, tau, mode, mask, bg,
+                           static_cast<cudaStream_t>(stream));
+}
+
+cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const cdmd_params* p,
+                     uint32_t* mask, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && p != nullptr && mask != nullptr, "ctx, params or mask is NULL");
+    cdmd_status st = check_video(D, m, n, ldd);
+    if (st != CDMD_OK) return st;
+    const int k = p->k, r = p->r, K = p->K;
+    CDMD_REQUIRE(r >= 1 && r <= 32 && r <= k && r <= n - 1, "r must be in [1, min(32, k, n-1)]");
+    CDMD_REQUIRE(K >= 1 && K <= r, "K must be in [1, r]");
+    DeviceGuard g(ctx->device);
+    const int p1 = n - 1;
+    const int ncols = (p->selector == CDMD_SEL_LSTSQ) ? r : K;
+    void* v = nullptr;
+    st = ensure_buffer(ctx, BUF_RUN_DY, static_cast<size_t>(k) * n * sizeof(double), &v);
+    if (st != CDMD_OK) return st;
+    double* DY = static_cast<double*>(v);
+    const size_t n_small = static_cast<size_t>(r) + 2 * r + 2 * static_cast<size_t>(p1) * r + 2 * r + 8;
+    st = ensure_buffer(ctx, BUF_RUN_SMALL, n_small * sizeof(double) + (r + 8) * sizeof(int32_t), &v);
+    if (st != CDMD_OK) return st;
+    double* sigma = static_cast<double*>(v);
+    double* lambda = sigma + r;
+    double* Gm = lambda + 2 * r;
+    double* beta = Gm + 2 * static_cast<size_t>(p1) * r;
+    int32_t* sel = reinterpret_cast<int32_t*>(beta + 2 * r + 8);
+    int32_t* nsel = sel + r + 4;
+    st = ensure_buffer(ctx, BUF_RUN_PHI, static_cast<size_t>(m) * ncols * 2 * sizeof(float), &v);
+    if (st != CDMD_OK) return st;
+    float* Phi = static_cast<float*>(v);
+    ctx->run_DY = DY; ctx->run_sigma = sigma; ctx->run_lambda = lambda; ctx->run_G = Gm;
+    ctx->run_beta = beta; ctx->run_sel = sel; ctx->run_nsel = nsel; ctx->run_Phi = Phi;
+
+    st = cdmd_sketch(ctx, D, m, n, ldd, p->ctype, k, p->seed, p->prec, DY, stream);
+    if (st != CDMD_OK) return st;
+    st = cdmd_decompose(ctx, DY, k, n, r, K, p->selector, sigma, lambda, Gm, nullptr, beta, sel, nsel, stream);
+    if (st != CDMD_OK) return st;
+    // OMP: lift and subtract only the selected modes (sel, -1 padded);
+    // LSTSQ: every mode carries an amplitude, so all r are used.
+    const int32_t* cols = (p->selector == CDMD_SEL_LSTSQ) ? nullptr : sel;
+    st = cdmd_lift(ctx, D, m, n, ldd, Gm, r, cols, ncols, p->prec, Phi, stream);
+    if (st != CDMD_OK) return st;
+    return cdmd_subtract(ctx, D, m, n, ldd, Phi, ncols, cols, beta, lambda, r, p->tau, p->bgmode, mask, nullptr,
+                         stream);
+}
+
+cdmd_status cdmd_run_host(cdmd_ctx* ctx, const uint8_t* D_host, int64_t m, int n, const cdmd_params* p,
+                          uint32_t* mask_host, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && D_host != nullptr && mask_host != nullptr && p != nullptr, "NULL argument");
+    cdmd_status st = check_video(D_host, m, n, m);
+    if (st != CDMD_OK) return st;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t vbytes = static_cast<size_t>(m) * n;
+    const size_t wpf = static_cast<size_t>((m + 31) / 32);
+    const size_t mbytes = wpf * n * sizeof(uint32_t);
+    void* dv = nullptr;
+    void* dm = nullptr;
+    st = ensure_buffer(ctx, BUF_RUN_VIDEO, vbytes, &dv);
+    if (st != CDMD_OK) return st;
+    st = ensure_buffer(ctx, BUF_RUN_MASK, mbytes, &dm);
+    if (st != CDMD_OK) return st;
+    CDMD_CHECK_CUDA(cudaMemcpyAsync(dv, D_host, vbytes, cudaMemcpyHostToDevice, s));
+    st = cdmd_run(ctx, static_cast<const uint8_t*>(dv), m, n, m, p, static_cast<uint32_t*>(dm), stream);
+    if (st != CDMD_OK) return st;
+    CDMD_CHECK_CUDA(cudaMemcpyAsync(mask_host, dm, mbytes, cudaMemcpyDeviceToHost, s));
+    return cdmd_status_sync(ctx, stream);
+}
+
+cdmd_status cdmd_workspace_views(cdmd_ctx* ctx, double** DY, double** sigma, double** lambda, double** G,
+                                 double** beta, int32_t** sel, int32_t** nsel, float** Phi) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(ctx->run_DY != nullptr, "no cdmd_run on this context yet");
+    if (DY) *DY = ctx->run_DY;
+    if (sigma) *sigma = ctx->run_sigma;
+    if (lambda) *lambda = ctx->run_lambda;
+    if (G) *G = ctx->run_G;
+    if (beta) *beta = ctx->run_beta;
+    if (sel) *sel = ctx->run_sel;
+    if (nsel) *nsel = ctx->run_nsel;
+    if (Phi) *Phi = ctx->run_Phi;
+    return CDMD_OK;
+}
+
+}  // extern "C"

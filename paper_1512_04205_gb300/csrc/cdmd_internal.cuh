@@ -1,0 +1,196 @@
+// Internal declarations shared by the libcdmd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "cdmd.h"
+
+namespace cdmd {
+
+// ---------------------------------------------------------------------------
+// Host-side error plumbing: every extern "C" entry returns a cdmd_status and
+// leaves a message in a thread-local buffer (cdmd_last_error).
+// ---------------------------------------------------------------------------
+cdmd_status fail(cdmd_status s, const char* fmt, ...);
+cdmd_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define CDMD_CHECK_CUDA(call)                                          \
+    do {                                                               \
+        cudaError_t _e = (call);                                       \
+        if (_e != cudaSuccess) return ::cdmd::cuda_fail(_e, #call);    \
+    } while (0)
+
+#define CDMD_CHECK_LAUNCH(name)                                        \
+    do {                                                               \
+        cudaError_t _e = cudaGetLastError();                           \
+        if (_e != cudaSuccess) return ::cdmd::cuda_fail(_e, name);     \
+    } while (0)
+
+#define CDMD_REQUIRE(cond, ...)                                        \
+    do {                                                               \
+        if (!(cond)) return ::cdmd::fail(CDMD_ERR_INVALID_ARG, __VA_ARGS__); \
+    } while (0)
+
+// Device status word: the first numerical error recorded wins.
+__device__ __forceinline__ void record_status(int* status, int code) {
+    if (status != nullptr) atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32->64 bit products with Weyl-bumped round keys.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 key) {
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        if (rnd > 0) {
+            key.x += 0x9E3779B9u;
+            key.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ key.x, lo1, hi0 ^ c.w ^ key.y, lo0);
+    }
+    return c;
+}
+
+__host__ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
+    return make_uint2(static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
+}
+
+// Box-Muller pair from two Philox words, FP32, accurate library functions.
+// U(w) = (w + 1/2) 2^-32.  ln U is taken as logf(U) when U < 1/2 and as
+// log1pf(-(1 - U)) otherwise, where 1 - U = (~w + 1/2) 2^-32 is formed from
+// the integer, so neither branch cancels.  The angle 2 pi U(wb) is split into
+// a quarter turn q (top two bits of wb) and a remainder f = (low 30 bits +
+// 1/2) 2^-30 in (0, 1) so that sincospif sees an argument below 1/2.
+__device__ __forceinline__ void box_muller_accurate(uint32_t wa, uint32_t wb, float& z_cos, float& z_sin) {
+    const float two_m32 = 2.3283064365386963e-10f;   // 2^-32
+    float ln_u;
+    if (wa < 0x80000000u) {
+        ln_u = logf((__uint2float_rn(wa) + 0.5f) * two_m32);
+    } else {
+        ln_u = log1pf(-((__uint2float_rn(~wa) + 0.5f) * two_m32));
+    }
+    const float radius = sqrtf(-2.0f * ln_u);
+    const uint32_t quarter = wb >> 30;
+    const float f = (__uint2float_rn(wb & 0x3fffffffu) + 0.5f) * 9.313225746154785e-10f;   // 2^-30
+    float s, c;
+    sincospif(0.5f * f, &s, &c);
+    float cs, sn;   // rotate by quarter * pi/2
+    switch (quarter) {
+        case 0: cs = c; sn = s; break;
+        case 1: cs = -s; sn = c; break;
+        case 2: cs = -c; sn = -s; break;
+        default: cs = s; sn = -c; break;
+    }
+    z_cos = radius * cs;
+    z_sin = radius * sn;
+}
+
+// Four Gaussian entries C[4q + 0..3, j] from counter (j, q, 0, 0).
+__device__ __forceinline__ float4 gaussian_quad(uint2 key, uint32_t j, uint32_t q) {
+    const uint4 w = philox4x32_10(make_uint4(j, q, 0u, 0u), key);
+    float4 z;
+    box_muller_accurate(w.x, w.y, z.x, z.y);
+    box_muller_accurate(w.z, w.w, z.z, z.w);
+    return z;
+}
+
+// Four Rademacher entries C[4q + 0..3, j]: bits of counter (j, i/128, 1, 0).
+__device__ __forceinline__ float4 rademacher_quad(uint2 key, uint32_t j, uint32_t q) {
+    const uint32_t i0 = 4u * q;
+    const uint4 w = philox4x32_10(make_uint4(j, i0 >> 7, 1u, 0u), key);
+    const uint32_t b = i0 & 127u;
+    const uint32_t word = (b >> 5) == 0 ? w.x : (b >> 5) == 1 ? w.y : (b >> 5) == 2 ? w.z : w.w;
+    const uint32_t bits = word >> (b & 31u);
+    float4 z;
+    z.x = (bits & 1u) ? -1.0f : 1.0f;
+    z.y = (bits & 2u) ? -1.0f : 1.0f;
+    z.z = (bits & 4u) ? -1.0f : 1.0f;
+    z.w = (bits & 8u) ? -1.0f : 1.0f;
+    return z;
+}
+
+// ---------------------------------------------------------------------------
+// Context: device, status word and a grow-only workspace of named buffers.
+// ---------------------------------------------------------------------------
+struct Buffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+enum BufferId {
+    BUF_SKETCH_PARTIAL = 0,   // sketch split partials (float)
+    BUF_GRAM,                 // n x n Gram of the sketch (double) + split partials
+    BUF_EIG,                  // eigen-solver scratch (double)
+    BUF_SMALL,                // small-solve scratch (double)
+    BUF_RUN_DY,               // cdmd_run intermediates
+    BUF_RUN_SMALL,
+    BUF_RUN_PHI,
+    BUF_RUN_VIDEO,            // cdmd_run_host device copy of the video
+    BUF_RUN_MASK,
+    BUF_SUBTRACT_TABLE,       // lambda^t table and amplitudes for pass (c)
+    BUF_COUNT
+};
+
+}  // namespace cdmd
+
+struct cdmd_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int* d_status = nullptr;
+    cdmd::Buffer buf[cdmd::BUF_COUNT];
+    // views of the last cdmd_run
+    double* run_DY = nullptr;
+    double* run_sigma = nullptr;
+    double* run_lambda = nullptr;
+    double* run_G = nullptr;
+    double* run_beta = nullptr;
+    int32_t* run_sel = nullptr;
+    int32_t* run_nsel = nullptr;
+    float* run_Phi = nullptr;
+};
+
+namespace cdmd {
+
+// Grow-only workspace buffer (never shrinks; synchronises the device before
+// freeing an older, smaller allocation).
+cdmd_status ensure_buffer(cdmd_ctx* ctx, BufferId id, size_t bytes, void** out);
+
+// Pass launchers (implemented in the kernel translation units).
+cdmd_status launch_sketch_fp32(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                               cdmd_ctype ctype, int k, uint64_t seed, double* DY,
+                               cudaStream_t stream);
+cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                             cdmd_ctype ctype, int k, uint64_t seed, double* DY,
+                             cudaStream_t stream);
+cdmd_status launch_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                                 const cdmd_measure* meas, double* DY, cudaStream_t stream);
+cdmd_status launch_measure_sparse_count(cdmd_ctx* ctx, int64_t m, int k, uint64_t seed,
+                                        double density, int64_t* d_counts, cudaStream_t stream);
+cdmd_status launch_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, cudaStream_t stream);
+cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r, int K,
+                             cdmd_selector selector, double* sigma, double* lambda, double* G,
+                             double* PhiY, double* beta, int32_t* sel, int32_t* nsel,
+                             cudaStream_t stream);
+cdmd_status launch_lift_fp32(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                             const double* G, int r, const int32_t* cols, int ncols, float* Phi,
+                             cudaStream_t stream);
+cdmd_status launch_lift_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                           const double* G, int r, const int32_t* cols, int ncols, float* Phi,
+                           cudaStream_t stream);
+cdmd_status launch_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                            const float* Phi, int ncols, const int32_t* cols, const double* beta,
+                            const double* lambda, int r, float tau, cdmd_bgmode mode,
+                            uint32_t* mask, float* bg, cudaStream_t stream);
+
+}  // namespace cdmd

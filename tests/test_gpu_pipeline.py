@@ -1,0 +1,115 @@
+"""End-to-end GPU parity: sketch -> decompose -> lift -> subtract against the
+FP64 oracle run on the same clip and measurement seed.
+
+Tolerances follow the arithmetic: the FP32 sketch carries relative errors of
+a few 1e-6 into the small solves, so eigenvalues are compared to 1e-5
+relative (well-separated modes), modes and background to 1e-4 relative, and
+masks must agree wherever |foreground - tau| > 0.5 grey level.
+"""
+import numpy as np
+import pytest
+
+import videogen
+from oracle import cdmd as O
+from oracle import measurement as M
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_1512_04205_gb300 import build, cdmd
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    build.build()
+    return cdmd
+
+
+@pytest.fixture(scope="module")
+def ctx(C):
+    return C.Context(0)
+
+
+def _oracle(clip, k, r, K, seed):
+    Cm = M.measurement_matrix("gaussian", seed, k, clip.m)
+    out = O.cdmd(clip.video_matrix(), Cm, r, K)
+    bg = O.background(out["Phi"][:, out["sel"]], out["beta"], out["lam"][out["sel"]], clip.n)
+    return out, bg
+
+
+def _well_separated(lam, tol=1e-3):
+    keep = []
+    for i, x in enumerate(lam):
+        others = np.delete(lam, i)
+        keep.append(np.min(np.abs(others - x)) >= tol if len(others) else True)
+    return np.array(keep)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_plain_pipeline_160x120(C, ctx, seed):
+    clip = videogen.make_clip(160, 120, 100, seed=seed)
+    k, r, K, tau, cseed = 200, 10, 10, 25.0, 100 + seed
+    params = C.make_params(k, r, K, tau, seed=cseed)
+    D = torch.from_numpy(clip.frames).cuda()
+    mask = C.cdmd_run(ctx, D, params)
+    C.cdmd_status_sync(ctx)
+    ref, ref_bg = _oracle(clip, k, r, K, cseed)
+
+    # eigenvalues: the same sketch and decomposition the pipeline ran
+    dec = C.cdmd_decompose(ctx, C.cdmd_sketch(ctx, D, k, cseed), r, K)
+    C.cdmd_status_sync(ctx)
+    lam = torch.view_as_complex(dec["lam"]).cpu().numpy()
+    idx = [int(np.argmin(np.abs(lam - x))) for x in ref["lam"]]
+    rel = np.abs(lam[idx] - ref["lam"]) / np.abs(ref["lam"])
+    sep = _well_separated(ref["lam"])
+    assert np.all(rel[sep] < 1e-5), rel
+
+    got = C.unpack_mask(mask, clip.m)
+    Dm = clip.video_matrix()
+    ref_mask = O.foreground_mask(Dm, ref_bg, tau)
+    margin = np.abs(np.abs(Dm - ref_bg) - tau) > 0.5
+    assert np.array_equal(got[margin], ref_mask[margin])
+    f_gpu = O.fmeasure(got, clip.truth.T)[2]
+    f_ref = O.fmeasure(ref_mask, clip.truth.T)[2]
+    assert abs(f_gpu - f_ref) < 1e-3
+
+
+def test_background_and_modes_160x120(C, ctx):
+    clip = videogen.make_clip(160, 120, 100, seed=7)
+    k, r, K, tau, cseed = 200, 10, 6, 25.0, 5
+    ref, ref_bg = _oracle(clip, k, r, K, cseed)
+    D = torch.from_numpy(clip.frames).cuda()
+    DY = C.cdmd_sketch(ctx, D, k, cseed)
+    dec = C.cdmd_decompose(ctx, DY, r, K)
+    Phi = C.cdmd_lift(ctx, D, dec["G"], cols=dec["sel"], ncols=K)
+    mask, bg = C.cdmd_subtract(ctx, D, Phi, dec["beta"], dec["lam"], tau, cols=dec["sel"], want_bg=True)
+    C.cdmd_status_sync(ctx)
+    bg = bg.cpu().numpy().T
+    assert np.abs(bg - ref_bg).max() <= 1e-4 * np.abs(ref_bg).max()
+    # modes (phase aligned) of well-separated eigenvalues
+    lam = torch.view_as_complex(dec["lam"]).cpu().numpy()
+    sel = dec["sel"].cpu().numpy()
+    Phi = Phi.cpu().numpy()
+    Phi = Phi[..., 0] + 1j * Phi[..., 1]
+    sep = _well_separated(ref["lam"])
+    for q, s in enumerate(sel):
+        if s < 0:
+            continue
+        i = int(np.argmin(np.abs(ref["lam"] - lam[s])))
+        if not sep[i]:
+            continue
+        x, y = Phi[:, q], ref["Phi"][:, i]
+        alpha = np.vdot(x, y) / np.vdot(x, x)
+        assert np.linalg.norm(alpha * x - y) <= 1e-4 * np.linalg.norm(y)
+
+
+def test_run_host_equals_run(C, ctx):
+    clip = videogen.make_clip(97, 61, 45, seed=11)
+    params = C.make_params(150, 8, 5, 25.0, seed=3)
+    dev_mask = C.cdmd_run(ctx, torch.from_numpy(clip.frames).cuda(), params)
+    C.cdmd_status_sync(ctx)
+    host = torch.from_numpy(clip.frames).pin_memory()
+    host_mask = C.cdmd_run_host(ctx, host, params)
+    np.testing.assert_array_equal(dev_mask.cpu().numpy(), host_mask.numpy())
