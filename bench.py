@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Throughput benchmark: compressed-DMD background subtraction, frames/s.
+
+Workload: one seeded synthetic 1920x1080 grayscale clip of 200 frames per GPU
+(textured low-rank background, 3 moving rectangles, +-10 % illumination
+drift, noise sigma 3; k = 1000 Gaussian measurements drawn in-kernel from
+Philox, target rank r = 20, K = 10 background modes, threshold 25 grey).
+A step is one pass of the whole hot path over the clip:
+    sketch -> decompose -> lift (selected modes) -> subtract + bit-pack.
+value = frames processed by all ranks / wall time of the timed steps (max over
+ranks); the clip (415 MB) is resident in HBM and larger than L2, so no
+flush is needed between steps.  Each pass is timed with CUDA events on the
+launching stream; the sketch is the dominant kernel and carries the roofline.
+
+e2e: the same metric through cdmd_run_host with pinned host buffers (the
+clip copied in and the mask copied out every step).
+cpu_baseline / --impl reference: the FP64 oracle on the host cores, on a
+bounded pixel sample of the clip, scaled to the full frame.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x2|fp32]
+       [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(width=1920, height=1080, n=200, k=1000, r=20, K=10, tau=25.0, drift=0.1, clip_seed=2024,
+                c_seed=0x5EED1080)
+METRIC = "cDMD 1080p frames/s"
+UNIT = "frames/s"
+
+
+def workload_name(prec):
+    w = WORKLOAD
+    return f"cdmd_{w['width']}x{w['height']}_n{w['n']}_k{w['k']}_r{w['r']}_K{w['K']}_gaussian_{prec}"
+
+
+def algorithmic_counts():
+    """Per-step algorithmic work of each pass (minimum the method must do)."""
+    w = WORKLOAD
+    m, n, k, K = w["width"] * w["height"], w["n"], w["k"], w["K"]
+    return dict(
+        sketch_flops=2.0 * k * m * n,                       # C D, C never stored
+        sketch_bytes=float(m * n),                          # D read once
+        gaussians=float(k * m),
+        lift_bytes=float(m * (n - 1) + m * K * 8),          # X' read, Phi (K complex64) written
+        subtract_bytes=float(m * n + m * K * 8 + n * ((m + 31) // 32) * 4),
+    )
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def source_hash(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def dram_traffic(kernel_file):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, only
+    if the kernel source has not changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        table = json.load(f)
+    entry = table.get(kernel_file)
+    src = os.path.join(ROOT, "paper_1512_04205_gb300", "csrc", kernel_file)
+    if not entry or not os.path.exists(src) or entry.get("source_sha") != source_hash(src):
+        return None
+    return entry.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ----------------------------------------------------------------------------
+
+def oracle_fps(clip, sample_px, dec=None, t_dec=None):
+    """FP64 oracle frames/s estimate on a bounded sample: the pixel-proportional
+    passes (sketch, lift, subtract) run on the first `sample_px` pixels and are
+    scaled to the frame; the small solves (independent of the frame size) run
+    on the k x n sketch of the sample.  Pass `dec`/`t_dec` to reuse a timed
+    decomposition.  Returns (fps, detail, dec, t_dec)."""
+    from oracle import cdmd as O
+    from oracle import measurement as M
+    w = WORKLOAD
+    m, n, k, r, K = clip.m, clip.n, w["k"], w["r"], w["K"]
+    Dm = clip.frames[:, :sample_px].T.astype(np.float64)
+    t0 = time.perf_counter()
+    Cs = M.gaussian_block(w["c_seed"], np.arange(k), np.arange(sample_px))
+    DY = O.sketch(Cs, Dm)
+    t_sketch = time.perf_counter() - t0
+    if dec is None:
+        t0 = time.perf_counter()
+        dec = O.decompose(DY, r, K)
+        t_dec = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Phi = O.lift(Dm, dec["G"][:, dec["sel"]])
+    bg = O.background(Phi, dec["beta"], dec["lam"][dec["sel"]], n)
+    mask = O.foreground_mask(Dm, bg, w["tau"])
+    O.pack_mask(mask)
+    t_pix = time.perf_counter() - t0
+    scale = m / sample_px
+    total = (t_sketch + t_pix) * scale + t_dec
+    detail = dict(t_sketch_sample=t_sketch, t_pixel_sample=t_pix, t_decompose=t_dec, scale=scale)
+    return n / total, detail, dec, t_dec
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import videogen
+    w = WORKLOAD
+    clip = videogen.make_clip(w["width"], w["height"], w["n"], seed=w["clip_seed"], drift=w["drift"])
+    sample_px = w["width"] * 4
+    times, detail, dec, t_dec = [], None, None, None
+    for step in range(args.warmup + args.steps):
+        fps, detail, dec, t_dec = oracle_fps(clip, sample_px, dec, t_dec)
+        if step >= args.warmup:
+            times.append(w["n"] / fps)
+    per_clip = float(np.mean(times))
+    value = w["n"] / per_clip
+    sample = (f"first {sample_px} of {clip.m} pixels x {w['n']} frames per step, scaled x{detail['scale']:.0f}; "
+              f"small solves on the full-size {w['k']}x{w['n']} sketch of the sample")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_clip * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name("f64_oracle"), "m": clip.m, "n": w["n"], "k": w["k"],
+                       "r": w["r"], "K": w["K"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU path
+# ----------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import videogen
+    from paper_1512_04205_gb300 import build
+    from paper_1512_04205_gb300 import cdmd as C
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = WORKLOAD
+    clip = videogen.make_clip(w["width"], w["height"], w["n"], seed=w["clip_seed"] + rank, drift=w["drift"])
+    m, n, k, r, K = clip.m, clip.n, w["k"], w["r"], w["K"]
+    D = torch.from_numpy(clip.frames).to(dev)
+    ctx = C.Context(local_rank)
+    stream = torch.cuda.current_stream()
+    DY = torch.empty((n, k), dtype=torch.float64, device=dev)
+    dec = C.decompose_outputs(n, k, r, K, dev)
+    Phi = torch.empty((m, K, 2), dtype=torch.float32, device=dev)
+    mask = torch.empty((n, (m + 31) // 32), dtype=torch.int32, device=dev)
+
+    def step(prec, events=None):
+        if events is not None:
+            events[0].record(stream)
+        C.cdmd_sketch(ctx, D, k, w["c_seed"], prec=prec, DY=DY)
+        if events is not None:
+            events[1].record(stream)
+        C.cdmd_decompose(ctx, DY, r, K, out=dec)
+        if events is not None:
+            events[2].record(stream)
+        C.cdmd_lift(ctx, D, dec["G"], cols=dec["sel"], ncols=K, prec=prec, Phi=Phi)
+        if events is not None:
+            events[3].record(stream)
+        C.cdmd_subtract(ctx, D, Phi, dec["beta"], dec["lam"], w["tau"], cols=dec["sel"], mask=mask)
+        if events is not None:
+            events[4].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(prec, steps, warmup, sample_clocks):
+        for _ in range(warmup):
+            step(prec)
+        C.cdmd_status_sync(ctx)
+        barrier()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(gpu_index(local_rank)) if sample_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        start.record(stream)
+        for s in range(steps):
+            step(prec, evs[s])
+        end.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        C.cdmd_status_sync(ctx)
+        total_ms = start.elapsed_time(end)
+        passes = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs]).mean(axis=0)
+        if dist is not None:
+            t = torch.tensor([total_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        barrier()
+        return total_ms, passes, clocks
+
+    results = {}
+    precs = [args.prec] + ([] if args.prec == "fp32" or args.no_plain else ["fp32"])
+    for prec in precs:
+        total_ms, passes, clocks = timed(prec, args.steps, args.warmup, sample_clocks=(prec == args.prec))
+        results[prec] = dict(total_ms=total_ms, passes=passes, clocks=clocks,
+                             mask=C.unpack_mask(mask, m) if prec in ("fp32", args.prec) else None)
+
+    # end to end through the public host-buffer call
+    e2e = None
+    if not args.no_e2e:
+        params = C.make_params(k, r, K, w["tau"], seed=w["c_seed"], prec=args.prec)
+        host = torch.from_numpy(clip.frames).pin_memory()
+        hmask = torch.empty((n, (m + 31) // 32), dtype=torch.int32).pin_memory()
+        for _ in range(max(1, min(3, args.warmup))):
+            C.cdmd_run_host(ctx, host, params, mask_host=hmask)
+        barrier()
+        t0 = time.perf_counter()
+        e2e_steps = max(3, min(args.steps, 10))
+        for _ in range(e2e_steps):
+            C.cdmd_run_host(ctx, host, params, mask_host=hmask)
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * n * e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(m * n),
+               "d2h_bytes_per_step": int(n * ((m + 31) // 32) * 4)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    head = results[args.prec]
+    steps = args.steps
+    value = world * n * steps / (head["total_ms"] * 1e-3)
+    counts = algorithmic_counts()
+    peaks, peak_src = load_peaks()
+    sketch_ms = float(head["passes"][0])
+    if args.prec == "bf16x2":
+        achieved = 2.0 * counts["sketch_flops"] / (sketch_ms * 1e-3) / 1e12     # hi + lo tensor products
+        peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": dram_traffic("sketch_tc.cu"), "kernel": "sketch (tcgen05 BF16 hi+lo)",
+                "peak_source": f"{peak_src} bf16 sustained"}
+    else:
+        fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        achieved = counts["sketch_flops"] / (sketch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": dram_traffic("sketch_fp32.cu"),
+                "kernel": "sketch (FP32 FMA)", "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+    per_pass = {name: float(v) for name, v in zip(["sketch", "decompose", "lift", "subtract"], head["passes"])}
+    hbm = float(peaks["hbm_gbs"])
+    lift_gbs = counts["lift_bytes"] / (per_pass["lift"] * 1e-3) / 1e9
+    sub_gbs = counts["subtract_bytes"] / (per_pass["subtract"] * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": head["total_ms"] / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if args.prec == "bf16x2" else "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args.prec), "m": m, "n": n, "k": k, "r": r, "K": K,
+                       "tau": w["tau"], "measurement": "gaussian (Philox4x32-10, in-kernel)",
+                       "precision": ("sketch+lift BF16 hi+lo on tcgen05, FP32 accumulation; FP64 small solves"
+                                     if args.prec == "bf16x2" else "sketch+lift FP32 FMA; FP64 small solves"),
+                       "l2": "clip 415 MB > 129 MB L2 (no flush)", "parallelism": f"clips x{world} (one per GPU)"},
+            "per_pass_ms": per_pass,
+            "pass_roofline": {"lift_gbs": lift_gbs, "lift_frac_hbm": lift_gbs / hbm, "subtract_gbs": sub_gbs,
+                              "subtract_frac_hbm": sub_gbs / hbm, "hbm_peak_gbs": hbm},
+            "roofline": roof,
+            "gpu_launches": 16 * steps,
+            "e2e": e2e}
+    if head["clocks"] is not None:
+        line["clocks"] = head["clocks"]
+    if "fp32" in results and args.prec != "fp32":
+        plain = results["fp32"]
+        agree = plain["mask"] == head["mask"]
+        line["plain_fp32"] = {"value": world * n * steps / (plain["total_ms"] * 1e-3),
+                              "ms_per_step": plain["total_ms"] / steps,
+                              "per_pass_ms": {nm: float(v) for nm, v in
+                                              zip(["sketch", "decompose", "lift", "subtract"], plain["passes"])},
+                              "mask_agreement_vs_mixed": float(agree.mean())}
+    if not args.no_cpu:
+        fps, detail, _, _ = oracle_fps(clip, w["width"] * 8)
+        line["cpu_baseline"] = {"value": fps, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                "sample": (f"first {w['width'] * 8} of {m} pixels x {n} frames, pixel passes "
+                                           f"scaled x{detail['scale']:.0f}; FP64 small solves on the sample's "
+                                           f"{k}x{n} sketch; numpy elementwise single-threaded, BLAS multi-threaded")}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return local_rank
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["bf16x2", "fp32"], default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -198,11 +198,29 @@ def cdmd_sketch_gather(ctx, D, meas, DY=None, stream=None):
     return DY
 
 
-def cdmd_decompose(ctx, DY, r, K, selector="omp", with_phiy=False, stream=None):
+def decompose_outputs(n, k, r, K, device, with_phiy=False):
+    """Preallocated output tensors for cdmd_decompose."""
+    import torch
+    dev = device
+    return dict(sigma=torch.empty(r, dtype=torch.float64, device=dev),
+                lam=torch.empty((r, 2), dtype=torch.float64, device=dev),
+                G=torch.empty((r, n - 1, 2), dtype=torch.float64, device=dev),
+                PhiY=torch.empty((r, k, 2), dtype=torch.float64, device=dev) if with_phiy else None,
+                beta=torch.empty((r, 2), dtype=torch.float64, device=dev),
+                sel=torch.empty(K, dtype=torch.int32, device=dev),
+                nsel=torch.empty(1, dtype=torch.int32, device=dev))
+
+
+def cdmd_decompose(ctx, DY, r, K, selector="omp", with_phiy=False, stream=None, out=None):
     """Steps 4-7 and 9 on the device; returns a dict of device tensors."""
     import torch
     n, k = DY.shape
     dev = DY.device
+    if out is not None:
+        _check(ctx.lib.cdmd_decompose(ctx.handle, _ptr(DY), int(k), int(n), int(r), int(K), SELECTORS[selector],
+                                      _ptr(out["sigma"]), _ptr(out["lam"]), _ptr(out["G"]), _ptr(out["PhiY"]),
+                                      _ptr(out["beta"]), _ptr(out["sel"]), _ptr(out["nsel"]), _stream(stream)))
+        return out
     out = dict(sigma=torch.empty(r, dtype=torch.float64, device=dev),
                lam=torch.empty((r, 2), dtype=torch.float64, device=dev),
                G=torch.empty((r, n - 1, 2), dtype=torch.float64, device=dev),
@@ -230,7 +248,8 @@ def cdmd_lift(ctx, D, G, cols=None, ncols=None, prec="fp32", Phi=None, stream=No
     return Phi
 
 
-def cdmd_subtract(ctx, D, Phi, beta, lam, tau, cols=None, mode="modulus", want_bg=False, mask=None, stream=None):
+def cdmd_subtract(ctx, D, Phi, beta, lam, tau, cols=None, mode="modulus", want_bg=False, mask=None, stream=None,
+                  bg=None):
     """Pass (c): bit-packed foreground mask (n, ceil(m/32)) int32, optional bg."""
     import torch
     n, m, ldd = _video(D)
@@ -238,7 +257,8 @@ def cdmd_subtract(ctx, D, Phi, beta, lam, tau, cols=None, mode="modulus", want_b
     r = beta.shape[0]
     if mask is None:
         mask = torch.empty((n, (m + 31) // 32), dtype=torch.int32, device=D.device)
-    bg = torch.empty((n, m), dtype=torch.float32, device=D.device) if want_bg else None
+    if want_bg and bg is None:
+        bg = torch.empty((n, m), dtype=torch.float32, device=D.device)
     _check(ctx.lib.cdmd_subtract(ctx.handle, _ptr(D), m, n, ldd, _ptr(Phi), int(ncols), _ptr(cols), _ptr(beta),
                                  _ptr(lam), int(r), float(tau), BGMODES[mode], _ptr(mask), _ptr(bg),
                                  _stream(stream)))
