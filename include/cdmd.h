@@ -252,6 +252,30 @@ cdmd_status cdmd_workspace_views(cdmd_ctx* ctx, double** DY, double** sigma, dou
                                  double** G, double** beta, int32_t** sel, int32_t** nsel,
                                  float** Phi);
 
+/* ---- allocation-free sketch ---------------------------------------------
+ *
+ * The paper has no counterpart to this call.  It serves callers that cannot
+ * allocate device memory once they are running: pipelines whose memory
+ * budget is fixed at start-up, real-time or certified code that forbids
+ * allocation after initialisation, and hosts whose device allocator belongs
+ * to another runtime.  cdmd_sketch keeps its split partial sums in a
+ * context's workspace, which may grow; this variant keeps them in a fixed
+ * 16 MiB array compiled into the library instead (every GPU that loads
+ * libcdmd holds that array until the process exits) and allocates nothing.
+ *
+ * Same arguments and result as cdmd_sketch with prec = CDMD_PREC_FP32, minus
+ * the context.  Runs on the calling thread's current device, enqueued on
+ * `stream`.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Rejects k * n > 4,194,304 with CDMD_ERR_INVALID_ARG.  Every call shares the
+ * one array and overwrites every partial sum it later reads, so nothing has
+ * to be cleared between calls; calls whose kernels overlap on the GPU
+ * (different streams without ordering between them) race on the array.
+ * There is no context status word, so the non-finite check that cdmd_sketch
+ * reports through cdmd_status_sync is not available here. */
+cdmd_status cdmd_sketch_noalloc(const uint8_t* D, int64_t m, int n, int64_t ldd, cdmd_ctype ctype, int k,
+                                uint64_t seed, double* DY, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ SELECTORS = {"omp": 0, "lstsq": 1}
 EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_string", "cdmd_status_sync",
             "cdmd_measure_sparse_nnz", "cdmd_measure_build", "cdmd_sketch", "cdmd_sketch_gather",
             "cdmd_decompose", "cdmd_lift", "cdmd_subtract", "cdmd_run", "cdmd_run_host",
-            "cdmd_workspace_views"]
+            "cdmd_workspace_views", "cdmd_sketch_noalloc"]
 
 
 class CdmdError(RuntimeError):
@@ -87,6 +87,7 @@ def load_library(path=LIB_PATH):
         "cdmd_run": [vp, vp, i64, ctypes.c_int, i64, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_run_host": [vp, vp, i64, ctypes.c_int, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_workspace_views": [vp] + [ctypes.POINTER(vp)] * 8,
+        "cdmd_sketch_noalloc": [vp, i64, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, u64, vp, vp],
     }
     for name, args in proto.items():
         fn = getattr(lib, name)
@@ -158,6 +159,22 @@ def cdmd_sketch(ctx, D, k, seed, ctype="gaussian", prec="fp32", DY=None, stream=
         DY = torch.empty((n, k), dtype=torch.float64, device=D.device)
     _check(ctx.lib.cdmd_sketch(ctx.handle, _ptr(D), m, n, ldd, CTYPES[ctype], int(k), int(seed) & (2**64 - 1),
                                PRECS[prec], _ptr(DY), _stream(stream)))
+    return DY
+
+
+def cdmd_sketch_noalloc(D, k, seed, ctype="gaussian", DY=None, stream=None):
+    """Pass (a) in FP32 without any device allocation by the library: the
+    partial sums live in a fixed 16 MiB array inside libcdmd (for callers
+    that cannot allocate once running).  Runs on the current device; the
+    first call on a device must precede any stream capture; k * n is limited
+    to 4,194,304.  Returns DY (n, k) float64 (allocated here by torch unless
+    DY is given)."""
+    import torch
+    n, m, ldd = _video(D)
+    if DY is None:
+        DY = torch.empty((n, k), dtype=torch.float64, device=D.device)
+    _check(load_library().cdmd_sketch_noalloc(_ptr(D), m, n, ldd, CTYPES[ctype], int(k), int(seed) & (2**64 - 1),
+                                              _ptr(DY), _stream(stream)))
     return DY
 
 

@@ -191,3 +191,101 @@ cdmd_status launch_sketch_fp32(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n
 }
 
 }  // namespace cdmd
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the FP32 sketch (cdmd_sketch_noalloc).
+//
+// Some callers cannot allocate device memory at run time: code that runs
+// under a memory budget fixed at start-up, real-time or safety-certified
+// pipelines that forbid allocation after initialisation, and hosts where
+// another runtime owns the device allocator.  For them the split partials of
+// the sketch live in a fixed array of this file instead of a context's
+// workspace.  The array is a static device variable: every GPU that loads
+// this library holds its 16 MiB until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+// 4 Mi FP32 partial sums (16 MiB) for the allocation-free sketch.
+static __device__ __align__(256) float g_sketch_noalloc_scratch[static_cast<size_t>(4) << 20];
+
+namespace cdmd {
+namespace {
+
+constexpr size_t kNoAllocScratchFloats = static_cast<size_t>(4) << 20;   // elements of the array above
+
+// Host-side set-up per device: the array's device address (host code cannot
+// use the symbol itself: its host-side name is only a stand-in) and the SM
+// count, taken once with that device current.
+struct NoAllocDevice {
+    bool ready = false;
+    float* scratch = nullptr;
+    int num_sms = 0;
+};
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+NoAllocDevice g_noalloc_devices[kNoAllocMaxDevices];
+
+}  // namespace
+}  // namespace cdmd
+
+extern "C" cdmd_status cdmd_sketch_noalloc(const uint8_t* D, int64_t m, int n, int64_t ldd, cdmd_ctype ctype,
+                                           int k, uint64_t seed, double* DY, void* stream) {
+    using namespace cdmd;
+    clear_error();
+    CDMD_REQUIRE(D != nullptr && DY != nullptr, "D or DY is NULL");
+    CDMD_REQUIRE(m >= 1 && m <= 0x7fffffffLL, "m must be in [1, 2^31) (got %lld)", static_cast<long long>(m));
+    CDMD_REQUIRE(n >= 2, "n must be >= 2 (got %d)", n);
+    CDMD_REQUIRE(ldd >= m, "ldd (%lld) must be >= m (%lld)", static_cast<long long>(ldd), static_cast<long long>(m));
+    CDMD_REQUIRE(k >= 1, "k must be >= 1 (got %d)", k);
+    CDMD_REQUIRE(ctype == CDMD_C_GAUSSIAN || ctype == CDMD_C_RADEMACHER, "ctype must be GAUSSIAN or RADEMACHER");
+    CDMD_REQUIRE(static_cast<size_t>(k) * static_cast<size_t>(n) <= kNoAllocScratchFloats,
+                 "k * n = %lld exceeds the fixed scratch of cdmd_sketch_noalloc (%zu partial sums); "
+                 "use cdmd_sketch", static_cast<long long>(k) * n, kNoAllocScratchFloats);
+    int dev = -1;
+    CDMD_CHECK_CUDA(cudaGetDevice(&dev));
+    CDMD_REQUIRE(dev >= 0 && dev < kNoAllocMaxDevices, "device index %d out of range", dev);
+    NoAllocDevice setup;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        NoAllocDevice& s = g_noalloc_devices[dev];
+        if (!s.ready) {
+            void* p = nullptr;
+            CDMD_CHECK_CUDA(cudaGetSymbolAddress(&p, g_sketch_noalloc_scratch));
+            int sms = 0;
+            CDMD_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            s.scratch = static_cast<float*>(p);
+            s.num_sms = sms;
+            s.ready = true;
+        }
+        setup = s;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    constexpr int kMaxSlab = 256;
+    const int row_tiles = (k + kRowsPerCta - 1) / kRowsPerCta;
+    const int64_t chunks = (m + kPixPerChunk - 1) / kPixPerChunk;
+    const int64_t cap_splits = static_cast<int64_t>(kNoAllocScratchFloats / (static_cast<size_t>(k) * n));
+    int64_t splits = (4LL * setup.num_sms + row_tiles - 1) / row_tiles;
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, (chunks + 15) / 16));
+    splits = std::min<int64_t>(std::min<int64_t>(splits, cap_splits), 65535);
+    const int64_t chunks_per_split = (chunks + splits - 1) / splits;
+    const int64_t pps = chunks_per_split * kPixPerChunk;
+    splits = (m + pps - 1) / pps;   // never more than before: every split gets pixels
+    const uint2 key = seed_key(seed);
+    for (int t0 = 0; t0 < n; t0 += kMaxSlab) {
+        const int n_slab = std::min(kMaxSlab, n - t0);
+        const int tq = (n_slab + 31) / 32;
+        const size_t smem = static_cast<size_t>(kPixPerChunk) * (32 * tq + 1) * sizeof(float);
+        const dim3 grid(row_tiles, static_cast<unsigned>(splits));
+        const cdmd_status s2 =
+            (ctype == CDMD_C_GAUSSIAN)
+                ? launch_slab<CDMD_C_GAUSSIAN>(tq, grid, smem, st, D, m, n_slab, t0, ldd, k, key, pps, n, setup.scratch)
+                : launch_slab<CDMD_C_RADEMACHER>(tq, grid, smem, st, D, m, n_slab, t0, ldd, k, key, pps, n,
+                                                 setup.scratch);
+        if (s2 != CDMD_OK) return s2;
+    }
+    const int64_t total = static_cast<int64_t>(k) * n;
+    sketch_reduce_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(
+        setup.scratch, static_cast<int>(splits), k, n, DY, nullptr);
+    CDMD_CHECK_LAUNCH("sketch_reduce_kernel (noalloc)");
+    return CDMD_OK;
+}
