@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libcdmd.so")
 CDMD_OK = 0
 STATUS_NAMES = {0: "CDMD_OK", 1: "CDMD_ERR_INVALID_ARG", 2: "CDMD_ERR_CUDA", 3: "CDMD_ERR_NOMEM",
                 4: "CDMD_ERR_NOT_CONVERGED", 5: "CDMD_ERR_RANK_DEFICIENT", 6: "CDMD_ERR_NONFINITE",
-                7: "CDMD_ERR_UNSUPPORTED"}
+                7: "CDMD_ERR_UNSUPPORTED", 8: "CDMD_ERR_TIMEOUT"}
 CTYPES = {"gaussian": 0, "rademacher": 1, "sparse": 2, "rowsample": 3}
 PRECS = {"fp32": 0, "bf16x2": 1}
 BGMODES = {"modulus": 0, "real": 1, "static": 2}

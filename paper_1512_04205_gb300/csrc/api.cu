@@ -92,6 +92,7 @@ const char* cdmd_status_string(cdmd_status s) {
         case CDMD_ERR_RANK_DEFICIENT: return "CDMD_ERR_RANK_DEFICIENT";
         case CDMD_ERR_NONFINITE: return "CDMD_ERR_NONFINITE";
         case CDMD_ERR_UNSUPPORTED: return "CDMD_ERR_UNSUPPORTED";
+        case CDMD_ERR_TIMEOUT: return "CDMD_ERR_TIMEOUT";
     }
     return "CDMD_ERR_UNKNOWN";
 }

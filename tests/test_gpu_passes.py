@@ -272,3 +272,34 @@ def test_subtract_matches_oracle(C, ctx, mode):
     if tail:
         assert np.all(words[:, -1] >> np.uint32(tail) == 0)
     np.testing.assert_array_equal(words, O.pack_mask(got))
+
+
+# ----------------------------------------------------- sketch, tensor cores
+
+@pytest.mark.parametrize("w,h,n,k", [(160, 120, 100, 200), (97, 61, 37, 203), (64, 33, 256, 300),
+                                     (300, 40, 16, 513)])
+def test_sketch_bf16x2_gaussian(C, ctx, w, h, n, k):
+    # BF16 hi+lo C (2^-16 relative per entry), fast MUFU Box-Muller, FP32
+    # accumulation: DY within 1e-4 of sqrt(m) * 255 of the FP64 oracle.
+    clip = videogen.make_clip(w, h, n, seed=w + 7 * n)
+    m = clip.m
+    ldd = (m + 15) // 16 * 16
+    padded = np.full((n, ldd), 255, dtype=np.uint8)     # bytes past m must be ignored
+    padded[:, :m] = clip.frames
+    D = _dev(padded)[:, :m]
+    seed = 4242 + k
+    DY = C.cdmd_sketch(ctx, D, k, seed, prec="bf16x2").cpu().numpy().T
+    C.cdmd_status_sync(ctx)
+    ref = O.sketch(M.measurement_matrix("gaussian", seed, k, m), clip.video_matrix())
+    err = np.abs(DY - ref).max()
+    assert err <= 1e-4 * np.sqrt(m) * 255.0, err
+    # and it is a sketch of the same C as the FP32 path, not merely close in norm
+    DY32 = C.cdmd_sketch(ctx, D, k, seed, prec="fp32").cpu().numpy().T
+    rel = np.linalg.norm(DY - DY32) / np.linalg.norm(DY32)
+    assert rel < 2e-5, rel
+
+
+def test_sketch_bf16x2_rejects_unaligned_stride(C, ctx):
+    frames = np.zeros((8, 1001), dtype=np.uint8)
+    with pytest.raises(C.CdmdError):
+        C.cdmd_sketch(ctx, _dev(frames), 64, 1, prec="bf16x2")     # ldd = 1001 is not a multiple of 16
