@@ -303,3 +303,31 @@ def test_sketch_bf16x2_rejects_unaligned_stride(C, ctx):
     frames = np.zeros((8, 1001), dtype=np.uint8)
     with pytest.raises(C.CdmdError):
         C.cdmd_sketch(ctx, _dev(frames), 64, 1, prec="bf16x2")     # ldd = 1001 is not a multiple of 16
+
+
+# ------------------------------------------------------- lift, tensor cores
+
+@pytest.mark.parametrize("w,h,n,r,modes", [(160, 120, 100, 10, [9, -1, 0, 2]), (97, 61, 37, 13, list(range(13))),
+                                           (33, 9, 256, 30, list(range(29, 9, -1))), (300, 40, 2, 1, [0])])
+def test_lift_bf16x2(C, ctx, w, h, n, r, modes):
+    # G in BF16 hi+lo (2^-16 relative), pixels exact: each Phi column within
+    # 5e-5 of the FP64 oracle in 2-norm.
+    clip = videogen.make_clip(w, h, n, seed=n + r)
+    m = clip.m
+    ldd = (m + 15) // 16 * 16
+    padded = np.full((n, ldd), 255, dtype=np.uint8)
+    padded[:, :m] = clip.frames
+    rng = np.random.default_rng(n)
+    G = (rng.standard_normal((n - 1, r)) + 1j * rng.standard_normal((n - 1, r))) * 1e-7
+    Gt = _dev(np.stack([G.T.real, G.T.imag], axis=-1))
+    cols = np.array(modes, dtype=np.int32)
+    Phi = C.cdmd_lift(ctx, _dev(padded)[:, :m], Gt, cols=_dev(cols), prec="bf16x2").cpu().numpy()
+    C.cdmd_status_sync(ctx)
+    Phi = Phi[..., 0] + 1j * Phi[..., 1]
+    ref = O.lift(clip.video_matrix(), G)
+    for q, s in enumerate(cols):
+        if s < 0:
+            assert np.all(Phi[:, q] == 0)
+        else:
+            err = np.linalg.norm(Phi[:, q] - ref[:, s]) / np.linalg.norm(ref[:, s])
+            assert err <= 5e-5, (q, s, err)

@@ -113,3 +113,31 @@ def test_run_host_equals_run(C, ctx):
     host = torch.from_numpy(clip.frames).pin_memory()
     host_mask = C.cdmd_run_host(ctx, host, params)
     np.testing.assert_array_equal(dev_mask.cpu().numpy(), host_mask.numpy())
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_mixed_precision_pipeline_160x120(C, ctx, seed):
+    # BF16 hi+lo sketch and lift, FP64 small solves: background within 1e-3
+    # relative of the FP64 oracle, F-measure within 0.001.
+    clip = videogen.make_clip(160, 120, 100, seed=seed)
+    k, r, K, tau, cseed = 200, 10, 6, 25.0, 300 + seed
+    ref, ref_bg = _oracle(clip, k, r, K, cseed)
+    D = torch.from_numpy(clip.frames).cuda()
+    DY = C.cdmd_sketch(ctx, D, k, cseed, prec="bf16x2")
+    dec = C.cdmd_decompose(ctx, DY, r, K)
+    Phi = C.cdmd_lift(ctx, D, dec["G"], cols=dec["sel"], ncols=K, prec="bf16x2")
+    mask, bg = C.cdmd_subtract(ctx, D, Phi, dec["beta"], dec["lam"], tau, cols=dec["sel"], want_bg=True)
+    C.cdmd_status_sync(ctx)
+    bg = bg.cpu().numpy().T
+    rel = np.linalg.norm(bg - ref_bg) / np.linalg.norm(ref_bg)
+    assert rel <= 1e-3, rel
+    got = C.unpack_mask(mask, clip.m)
+    Dm = clip.video_matrix()
+    ref_mask = O.foreground_mask(Dm, ref_bg, tau)
+    f_gpu = O.fmeasure(got, clip.truth.T)[2]
+    f_ref = O.fmeasure(ref_mask, clip.truth.T)[2]
+    assert abs(f_gpu - f_ref) <= 1e-3, (f_gpu, f_ref)
+    # the whole-pipeline entry point gives the same mask
+    mask2 = C.cdmd_run(ctx, D, C.make_params(k, r, K, tau, seed=cseed, prec="bf16x2"))
+    C.cdmd_status_sync(ctx)
+    assert np.array_equal(mask2.cpu().numpy(), mask.cpu().numpy())
