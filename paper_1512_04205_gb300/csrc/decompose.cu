@@ -8,22 +8,32 @@
 //            compressed modes Phi_Y = Y' G (Remark 3)
 // so no kernel after the Gram touches the k-long sketch rows again.
 //
-// FP64 on this GPU runs at about 1/64 of the FP32 rate, so each O(p^3) or
-// O(p^2 r) stage is spread over many SMs:
+// FP64 on this GPU is slow in both senses: about 1/64 of the FP32 FMA rate,
+// 64 cycles for a dependent FMA and ~640 for a division or square root.  So
+// the O(p^3) / O(p^2 r) stages are spread over SMs, serial chains are kept
+// short (several independent accumulators, more lanes), divisions and square
+// roots on critical paths become approximate reciprocals refined by Newton
+// steps, and the one iteration-heavy r x r stage runs in FP32 with an FP64
+// Newton correction per eigenpair:
 //   gram_partial / gram_reduce   multi-CTA, split over the sketch rows
 //   tridiag                      Householder tridiagonalisation of Y^T Y on a
 //                                thread-block cluster, rows distributed over
 //                                the CTAs' shared memory, vectors exchanged
 //                                through distributed shared memory
 //   tridiag_eigpair              one CTA per wanted eigenvalue: Sturm-count
-//                                multisection, then inverse iteration
-//   orthonormalise               modified Gram-Schmidt, twice (one CTA)
-//   backtransform                one CTA per eigenvector: V = Q z, B = (Y^T Y') V
-//   atilde                       one CTA per column of A~
-//   eig_small                    one CTA: Hessenberg + complex-shift QR on A~
+//                                multisection (64 shifts per pass), then
+//                                inverse iteration with reciprocal pivots
+//   orthonormalise               classical Gram-Schmidt, twice (one CTA)
+//   backtransform                one CTA per eigenvector: V = Q z
+//   bmat, atilde                 B = (Y^T Y') V, A~ = S^-1 V^T B S^-1
+//   eig_f32                      one warp: Hessenberg + complex-shift QR on A~
+//                                in FP32, eigenvectors by back-substitution
+//   eig_refine                   one CTA per eigenpair: FP64 Newton on
+//                                (A~ - mu) w = 0 with one entry of w fixed
+//   eig_order                    normalise, order (conjugate pairs adjacent)
 //   gmat                         G = V S^-1 W
 //   hmat                         H = (Y'^T Y') G, M = G^H H, c = G^H (Y'^T y1)
-//   omp                          one CTA: OMP / least squares in Gram form
+//   omp                          one warp: OMP / least squares in Gram form
 //   phiy (optional)              Phi_Y = Y' G
 #include <cooperative_groups.h>
 
@@ -35,10 +45,17 @@ namespace cdmd {
 namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
+constexpr int kMaxR = 32;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -59,6 +76,48 @@ __device__ double block_sum(double v, double* red) {
     const double out = red[0];
     __syncthreads();
     return out;
+}
+
+// 1/a and 1/sqrt(a) to full FP64 precision: hardware approximation refined by
+// two Newton steps (each step doubles the number of correct bits).
+__device__ __forceinline__ double rcp64(double a) {
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(a));
+    double e = fma(-a, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-a, x, 1.0);
+    x = fma(x, e, x);
+    return x;
+}
+
+__device__ __forceinline__ double rsqrt64(double a) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+    const double h = 0.5 * a;
+    double t = fma(-h * y, y, 0.5);
+    y = fma(y, t, y);
+    t = fma(-h * y, y, 0.5);
+    y = fma(y, t, y);
+    return y;
+}
+
+// complex helpers
+struct cd {
+    double x, y;
+};
+__device__ __forceinline__ cd cmul(cd a, cd b) { return {fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)}; }
+__device__ __forceinline__ cd cadd(cd a, cd b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ cd csub(cd a, cd b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ cd cconj(cd a) { return {a.x, -a.y}; }
+__device__ __forceinline__ double cabs2(cd a) { return fma(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ cd cscale(cd a, double s) { return {a.x * s, a.y * s}; }
+// 1/a for complex a != 0
+__device__ __forceinline__ cd cinv(cd a) {
+    const double s = rcp64(cabs2(a));
+    return {a.x * s, -a.y * s};
+}
+__device__ __forceinline__ cd shfl_cd(cd v, int src) {
+    return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
 }
 
 // ---------------------------------------------------------------------------
@@ -164,10 +223,11 @@ tridiag_kernel(const double* __restrict__ R, int n, int p, double* __restrict__ 
             if (tail2 == 0.0) {
                 alpha = x0; tau = 0.0; v0 = 0.0;
             } else {
-                const double nrm = sqrt(x0 * x0 + tail2);
+                const double s2 = fma(x0, x0, tail2);
+                const double nrm = s2 * rsqrt64(s2);
                 alpha = (x0 >= 0.0) ? -nrm : nrm;
                 v0 = x0 - alpha;
-                tau = 2.0 / (v0 * v0 + tail2);
+                tau = 2.0 * rcp64(fma(v0, v0, tail2));
             }
             for (int rr = 0; rr < P; ++rr) {
                 double* rv = cluster.map_shared_rank(vbuf + buf * p, rr);
@@ -244,40 +304,61 @@ __global__ void tiny_tridiag_kernel(const double* R, int n, int p, double* dd, d
 
 // ---------------------------------------------------------------------------
 // 3. Eigenpairs of the symmetric tridiagonal T (d, e), the r largest.
-// Sturm count N(x) = #eigenvalues < x = sign changes of the leading minors
-// p_i(x) = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}, rescaled to stay in range.
+// Sturm count N(x) = #eigenvalues < x = sign changes in the leading minors
+// p_i(x) = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (p_{-1} = 1).  Signs are read
+// from the high words (no compare on the critical path); the pair (p_i,
+// p_{i-1}) is rescaled by a power of two every eight steps.
 // ---------------------------------------------------------------------------
-__device__ int sturm_count(const double* d, const double* e2, int p, double x) {
-    double a = d[0] - x;   // p_0
-    double b = 1.0;        // p_{-1}
-    int cnt = (a < 0.0) ? 1 : 0;
-    if (a == 0.0) { a = -kEps; cnt = 1; }
-    for (int i = 1; i < p; ++i) {
-        double c = fma(d[i] - x, a, -e2[i - 1] * b);
-        if (c == 0.0) c = (a < 0.0) ? kEps : -kEps;   // zero counts as a change
-        cnt += ((c < 0.0) != (a < 0.0)) ? 1 : 0;
-        b = a;
-        a = c;
-        const double m = fabs(a);
-        if (m > 1e150) { a *= 1e-150; b *= 1e-150; }
-        else if (m < 1e-150 && fabs(b) < 1e-150) { a *= 1e150; b *= 1e150; }
+__device__ __forceinline__ void rescale_pair(double& a, double& b) {
+    const int e = (__double2hiint(a) >> 20) & 0x7ff;
+    if (e > 1023 + 400 || (e > 0 && e < 1023 - 400)) {
+        const double s = __hiloint2double((2046 - e) << 20, 0);   // 2^(1023 - e)
+        a *= s;
+        b *= s;
     }
-    return cnt;
 }
 
-constexpr int kSections = 8;   // lanes used by the multisection
+__device__ __forceinline__ void sturm_count2(const double* d, const double* e2, int p, double x0, double x1,
+                                             int& n0, int& n1) {
+    double a0 = d[0] - x0, a1 = d[0] - x1, b0 = 1.0, b1 = 1.0;
+    int c0 = static_cast<int>(static_cast<unsigned>(__double2hiint(a0)) >> 31);
+    int c1 = static_cast<int>(static_cast<unsigned>(__double2hiint(a1)) >> 31);
+    for (int i = 1; i < p; ++i) {
+        const double ei = e2[i - 1], di = d[i];
+        const double t0 = fma(di - x0, a0, -ei * b0);
+        const double t1 = fma(di - x1, a1, -ei * b1);
+        c0 += static_cast<int>(static_cast<unsigned>(__double2hiint(t0) ^ __double2hiint(a0)) >> 31);
+        c1 += static_cast<int>(static_cast<unsigned>(__double2hiint(t1) ^ __double2hiint(a1)) >> 31);
+        b0 = a0;
+        a0 = t0;
+        b1 = a1;
+        a1 = t1;
+        if ((i & 7) == 0) {
+            rescale_pair(a0, b0);
+            rescale_pair(a1, b1);
+        }
+    }
+    n0 = c0;
+    n1 = c1;
+}
 
-// Every array this kernel writes and reads back lives in shared memory, so
-// no load can be served from a read-only cache path that misses the write.
+constexpr int kShifts = 64;   // shifts tested per multisection pass (two per lane)
+
 __global__ void __launch_bounds__(32)
-tridiag_eigpair_kernel(const double* __restrict__ dd, const double* __restrict__ ee, int p, int r,
-                       double* lam, double* Z, int* status) {
+tridiag_eigpair_kernel(const double* __restrict__ dd, const double* __restrict__ ee, int p, int r, double* lam,
+                       double* Z, int* status) {
     extern __shared__ double tsm[];
-    double* d = tsm;          // p
-    double* e = d + p;        // p (e[p-1] = 0)
-    double* e2 = e + p;       // p
-    double* work = e2 + p;    // 6 p: LU factors, pivots, iterate
-    const int w = blockIdx.x;             // w-th largest
+    double* d = tsm;            // p
+    double* e = d + p;          // p (e[p-1] = 0)
+    double* e2 = e + p;         // p
+    double* lmul = e2 + p;      // p: elimination multipliers
+    double* udg = lmul + p;     // p: U diagonal
+    double* u1 = udg + p;       // p: U first super-diagonal
+    double* u2 = u1 + p;        // p: U second super-diagonal
+    double* invd = u2 + p;      // p: 1 / U diagonal
+    double* z = invd + p;       // p: iterate
+    int* piv = reinterpret_cast<int*>(z + p);   // p
+    const int w = blockIdx.x;
     const int lane = threadIdx.x;
     for (int i = lane; i < p; i += 32) {
         d[i] = dd[i];
@@ -285,7 +366,6 @@ tridiag_eigpair_kernel(const double* __restrict__ dd, const double* __restrict__
         e2[i] = e[i] * e[i];
     }
     __syncwarp();
-    // Gershgorin interval
     double lo = 1e300, hi = -1e300, tn = 0.0;
     for (int i = lane; i < p; i += 32) {
         const double rad = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0);
@@ -302,133 +382,153 @@ tridiag_eigpair_kernel(const double* __restrict__ dd, const double* __restrict__
     const double pad = 2.0 * kEps * tn + 1e-300;
     lo -= pad;
     hi += pad;
-    const int idx = p - 1 - w;   // ascending index of the target
+    const int idx = p - 1 - w;   // ascending index of the target eigenvalue
     bool converged = false;
-    for (int it = 0; it < 80; ++it) {
+    for (int it = 0; it < 40; ++it) {
         const double width = hi - lo;
         if (width <= 2.0 * kEps * fmax(fabs(lo), fabs(hi)) + kEps * tn + 1e-300) { converged = true; break; }
-        const double x = lo + width * static_cast<double>(lane + 1) / (kSections + 1);
-        int cnt = 0;
-        if (lane < kSections) cnt = sturm_count(d, e2, p, x);
-        const unsigned above = __ballot_sync(0xffffffffu, lane < kSections && cnt > idx);
-        const int f = above ? __ffs(above) - 1 : kSections;
-        const double xf = lo + width * static_cast<double>(f + 1) / (kSections + 1);
-        const double xl = lo + width * static_cast<double>(f) / (kSections + 1);
-        const double nlo = (f == 0) ? lo : xl;
-        const double nhi = (f == kSections) ? hi : xf;
+        const double step = width * (1.0 / (kShifts + 1));
+        int n0, n1;
+        sturm_count2(d, e2, p, fma(step, static_cast<double>(lane + 1), lo),
+                     fma(step, static_cast<double>(lane + 33), lo), n0, n1);
+        const unsigned b0 = __ballot_sync(0xffffffffu, n0 > idx);
+        const unsigned b1 = __ballot_sync(0xffffffffu, n1 > idx);
+        const int f = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : kShifts);
+        const double nlo = (f == 0) ? lo : fma(step, static_cast<double>(f), lo);
+        const double nhi = (f == kShifts) ? hi : fma(step, static_cast<double>(f + 1), lo);
         if (nlo >= nhi || (nlo == lo && nhi == hi)) { converged = true; break; }
         lo = nlo;
         hi = nhi;
     }
     const double lambda = 0.5 * (lo + hi);
     if (!converged && lane == 0) record_status(status, CDMD_ERR_NOT_CONVERGED);
-    if (lane == 0) lam[w] = lambda;
-
-    // inverse iteration by lane 0: LU with partial pivoting of T - mu I
-    if (lane == 0) {
-        double* ldl = work;                                    // sub multipliers
-        double* ldd = ldl + p;                                 // U diagonal
-        double* ldu = ldd + p;                                 // U first super
-        double* ldu2 = ldu + p;                                // U second super
-        double* piv = ldu2 + p;                                // 1.0 = rows swapped
-        double* z = piv + p;
-        const double mu = lambda + kEps * tn;   // keep the shifted matrix non-singular
-        const double tiny = kEps * tn + 1e-300;
-        for (int i = 0; i < p; ++i) {
-            ldd[i] = d[i] - mu;
-            ldl[i] = (i + 1 < p) ? e[i] : 0.0;
-            ldu[i] = (i + 1 < p) ? e[i] : 0.0;
-            ldu2[i] = 0.0;
-            piv[i] = 0.0;
-        }
-        for (int i = 0; i + 1 < p; ++i) {
-            if (fabs(ldd[i]) >= fabs(ldl[i])) {
-                if (ldd[i] == 0.0) ldd[i] = tiny;
-                const double fct = ldl[i] / ldd[i];
-                ldl[i] = fct;
-                ldd[i + 1] -= fct * ldu[i];
-            } else {
-                const double fct = ldd[i] / ldl[i];
-                ldd[i] = ldl[i];
-                ldl[i] = fct;
-                const double tmp = ldu[i];
-                ldu[i] = ldd[i + 1];
-                ldd[i + 1] = tmp - fct * ldd[i + 1];
-                if (i + 2 < p) {
-                    ldu2[i] = ldu[i + 1];
-                    ldu[i + 1] = -fct * ldu[i + 1];
-                }
-                piv[i] = 1.0;
-            }
-        }
-        if (ldd[p - 1] == 0.0) ldd[p - 1] = tiny;
-        // deterministic start vector
-        uint32_t hs = 0x9E3779B9u * static_cast<uint32_t>(w + 1);
-        for (int i = 0; i < p; ++i) {
-            hs ^= hs << 13; hs ^= hs >> 17; hs ^= hs << 5;
-            z[i] = 1.0 + static_cast<double>(hs & 0xffff) * (1.0 / 65536.0);
-        }
-        for (int itr = 0; itr < 3; ++itr) {
-            for (int i = 0; i + 1 < p; ++i) {
-                if (piv[i] == 0.0) {
-                    z[i + 1] -= ldl[i] * z[i];
-                } else {
-                    const double tmp = z[i];
-                    z[i] = z[i + 1];
-                    z[i + 1] = tmp - ldl[i] * z[i];
-                }
-            }
-            z[p - 1] /= ldd[p - 1];
-            if (p > 1) z[p - 2] = (z[p - 2] - ldu[p - 2] * z[p - 1]) / ldd[p - 2];
-            for (int i = p - 3; i >= 0; --i)
-                z[i] = (z[i] - ldu[i] * z[i + 1] - ldu2[i] * z[i + 2]) / ldd[i];
-            double nrm = 0.0;
-            for (int i = 0; i < p; ++i) nrm = fma(z[i], z[i], nrm);
-            nrm = sqrt(nrm);
-            if (!(nrm > 0.0) || !isfinite(nrm)) { record_status(status, CDMD_ERR_NOT_CONVERGED); nrm = 1.0; }
-            const double inv = 1.0 / nrm;
-            for (int i = 0; i < p; ++i) z[i] *= inv;
-        }
-        for (int i = 0; i < p; ++i) Z[static_cast<int64_t>(w) * p + i] = z[i];
+    if (lane != 0) return;
+    lam[w] = lambda;
+    // inverse iteration: LU with partial pivoting of T - mu I, reciprocal pivots
+    const double mu = lambda + kEps * tn;   // keeps T - mu I away from exact singularity
+    const double tiny = kEps * tn + 1e-300;
+    for (int i = 0; i < p; ++i) {
+        udg[i] = d[i] - mu;
+        lmul[i] = e[i];
+        u1[i] = e[i];
+        u2[i] = 0.0;
+        piv[i] = 0;
     }
+    for (int i = 0; i + 1 < p; ++i) {
+        if (fabs(udg[i]) >= fabs(lmul[i])) {
+            if (udg[i] == 0.0) udg[i] = tiny;
+            const double inv = rcp64(udg[i]);
+            invd[i] = inv;
+            const double fct = lmul[i] * inv;
+            lmul[i] = fct;
+            udg[i + 1] = fma(-fct, u1[i], udg[i + 1]);
+        } else {
+            const double inv = rcp64(lmul[i]);
+            invd[i] = inv;
+            const double fct = udg[i] * inv;
+            udg[i] = lmul[i];
+            lmul[i] = fct;
+            const double tmp = u1[i];
+            u1[i] = udg[i + 1];
+            udg[i + 1] = fma(-fct, udg[i + 1], tmp);
+            if (i + 2 < p) {
+                u2[i] = u1[i + 1];
+                u1[i + 1] = -fct * u1[i + 1];
+            }
+            piv[i] = 1;
+        }
+    }
+    if (udg[p - 1] == 0.0) udg[p - 1] = tiny;
+    invd[p - 1] = rcp64(udg[p - 1]);
+    uint32_t hs = 0x9E3779B9u * static_cast<uint32_t>(w + 1);
+    for (int i = 0; i < p; ++i) {
+        hs ^= hs << 13;
+        hs ^= hs >> 17;
+        hs ^= hs << 5;
+        z[i] = 1.0 + static_cast<double>(hs & 0xffff) * (1.0 / 65536.0);
+    }
+    for (int itr = 0; itr < 2; ++itr) {
+        for (int i = 0; i + 1 < p; ++i) {
+            if (piv[i] == 0) {
+                z[i + 1] = fma(-lmul[i], z[i], z[i + 1]);
+            } else {
+                const double tmp = z[i];
+                z[i] = z[i + 1];
+                z[i + 1] = fma(-lmul[i], z[i], tmp);
+            }
+        }
+        z[p - 1] *= invd[p - 1];
+        if (p > 1) z[p - 2] = fma(-u1[p - 2], z[p - 1], z[p - 2]) * invd[p - 2];
+        for (int i = p - 3; i >= 0; --i) z[i] = fma(-u2[i], z[i + 2], fma(-u1[i], z[i + 1], z[i])) * invd[i];
+        double s0 = 0.0, s1 = 0.0;
+        for (int i = 0; i + 1 < p; i += 2) {
+            s0 = fma(z[i], z[i], s0);
+            s1 = fma(z[i + 1], z[i + 1], s1);
+        }
+        if (p & 1) s0 = fma(z[p - 1], z[p - 1], s0);
+        const double nrm2 = s0 + s1;
+        if (!(nrm2 > 0.0) || !isfinite(nrm2)) {
+            record_status(status, CDMD_ERR_NOT_CONVERGED);
+            break;
+        }
+        const double inv = rsqrt64(nrm2);
+        for (int i = 0; i < p; ++i) z[i] *= inv;
+    }
+    for (int i = 0; i < p; ++i) Z[static_cast<int64_t>(w) * p + i] = z[i];
 }
 
-// 4a. Modified Gram-Schmidt over the r columns of Z (descending eigenvalue
-// order), applied twice.
-// Threads read entries other threads wrote (ordered by __syncthreads), so Z
-// is deliberately not __restrict__: its loads must stay coherent.
-__global__ void __launch_bounds__(256)
+// 4a. Classical Gram-Schmidt over the r columns of Z (descending eigenvalue
+// order), applied twice: the dots of a column with all earlier columns are
+// taken in parallel (one warp each).  Z is not __restrict__: threads read
+// entries other threads wrote, ordered by __syncthreads.
+__global__ void __launch_bounds__(1024)
 orthonormalise_kernel(double* Z, int p, int r) {
+    __shared__ double dots[32];
     __shared__ double red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int pass = 0; pass < 2; ++pass) {
         for (int c = 0; c < r; ++c) {
             double* zc = Z + static_cast<int64_t>(c) * p;
-            for (int q = 0; q < c; ++q) {
-                const double* zq = Z + static_cast<int64_t>(q) * p;
-                double s = 0.0;
-                for (int i = threadIdx.x; i < p; i += blockDim.x) s = fma(zq[i], zc[i], s);
-                const double dot = block_sum(s, red);
-                for (int i = threadIdx.x; i < p; i += blockDim.x) zc[i] -= dot * zq[i];
-                __syncthreads();
+            if (wid < c) {
+                const double* zq = Z + static_cast<int64_t>(wid) * p;
+                double s0 = 0.0, s1 = 0.0;
+                int i = lane;
+                for (; i + 32 < p; i += 64) {
+                    s0 = fma(zq[i], zc[i], s0);
+                    s1 = fma(zq[i + 32], zc[i + 32], s1);
+                }
+                if (i < p) s0 = fma(zq[i], zc[i], s0);
+                const double s = warp_sum(s0 + s1);
+                if (lane == 0) dots[wid] = s;
             }
+            __syncthreads();
+            for (int i = threadIdx.x; i < p; i += blockDim.x) {
+                double a0 = zc[i], a1 = 0.0;
+                int q = 0;
+                for (; q + 1 < c; q += 2) {
+                    a0 = fma(-dots[q], Z[static_cast<int64_t>(q) * p + i], a0);
+                    a1 = fma(-dots[q + 1], Z[static_cast<int64_t>(q + 1) * p + i], a1);
+                }
+                if (q < c) a0 = fma(-dots[q], Z[static_cast<int64_t>(q) * p + i], a0);
+                zc[i] = a0 + a1;
+            }
+            __syncthreads();
             double s = 0.0;
             for (int i = threadIdx.x; i < p; i += blockDim.x) s = fma(zc[i], zc[i], s);
-            const double nrm = sqrt(block_sum(s, red));
-            const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+            const double nrm2 = block_sum(s, red);
+            const double inv = nrm2 > 0.0 ? rsqrt64(nrm2) : 0.0;
             for (int i = threadIdx.x; i < p; i += blockDim.x) zc[i] *= inv;
             __syncthreads();
         }
     }
 }
 
-// 4b. V[:, c] = Q z_c (apply H_{p-3}, ..., H_0), sigma_c = sqrt(lambda_c),
-// B[:, c] = (Y^T Y') V[:, c].  One CTA (one warp) per column.
+// 4b. V[:, c] = Q z_c (apply H_{p-3}, ..., H_0) and sigma_c = sqrt(lambda_c);
+// one CTA (one warp) per column, four partial sums per lane.
 __global__ void __launch_bounds__(32)
 backtransform_kernel(const double* __restrict__ Z, const double* __restrict__ Hv,
-                     const double* __restrict__ htau, const double* __restrict__ lam,
-                     const double* __restrict__ R, int n, int p, int r,
-                     double* __restrict__ V, double* __restrict__ B, double* __restrict__ sigma,
-                     int* status) {
+                     const double* __restrict__ htau, const double* __restrict__ lam, int p, int r,
+                     double* __restrict__ V, double* __restrict__ sigma, int* status) {
     extern __shared__ double ysm[];   // p
     const int c = blockIdx.x;
     const int lane = threadIdx.x;
@@ -438,10 +538,17 @@ backtransform_kernel(const double* __restrict__ Z, const double* __restrict__ Hv
         const double tau = htau[j];
         if (tau == 0.0) continue;
         const double* v = Hv + static_cast<int64_t>(j) * p;
-        double s = 0.0;
-        for (int l = j + 1 + lane; l < p; l += 32) s = fma(v[l], ysm[l], s);
-        s = warp_sum(s) * tau;
-        for (int l = j + 1 + lane; l < p; l += 32) ysm[l] -= s * v[l];
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int l = j + 1 + lane;
+        for (; l + 96 < p; l += 128) {
+            s0 = fma(v[l], ysm[l], s0);
+            s1 = fma(v[l + 32], ysm[l + 32], s1);
+            s2 = fma(v[l + 64], ysm[l + 64], s2);
+            s3 = fma(v[l + 96], ysm[l + 96], s3);
+        }
+        for (; l < p; l += 32) s0 = fma(v[l], ysm[l], s0);
+        const double s = warp_sum((s0 + s1) + (s2 + s3)) * tau;
+        for (int q = j + 1 + lane; q < p; q += 32) ysm[q] = fma(-s, v[q], ysm[q]);
         __syncwarp();
     }
     for (int i = lane; i < p; i += 32) V[static_cast<int64_t>(c) * p + i] = ysm[i];
@@ -449,16 +556,28 @@ backtransform_kernel(const double* __restrict__ Z, const double* __restrict__ Hv
         const double l0 = lam[0];
         const double lc = lam[c];
         if (!(lc > static_cast<double>(p) * kEps * fabs(l0))) record_status(status, CDMD_ERR_RANK_DEFICIENT);
-        sigma[c] = sqrt(fmax(lc, 0.0));
+        sigma[c] = lc > 0.0 ? lc * rsqrt64(lc) : 0.0;
     }
-    // B[a][c] = sum_b R[a][b+1] V[b][c]
-    for (int a = 0; a < p; ++a) {
-        const double* row = R + static_cast<int64_t>(a) * n + 1;
-        double s = 0.0;
-        for (int b = lane; b < p; b += 32) s = fma(row[b], ysm[b], s);
-        s = warp_sum(s);
-        if (lane == 0) B[static_cast<int64_t>(c) * p + a] = s;
+}
+
+// 4c. B[a][c] = sum_b R[a][b+1] V[b][c] = ((Y^T Y') V)[a][c]; one warp per entry.
+__global__ void __launch_bounds__(256)
+bmat_kernel(const double* __restrict__ R, const double* __restrict__ V, int n, int p, double* __restrict__ B) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int a = blockIdx.x * 8 + wid;
+    const int c = blockIdx.y;
+    if (a >= p) return;
+    const double* row = R + static_cast<int64_t>(a) * n + 1;
+    const double* vc = V + static_cast<int64_t>(c) * p;
+    double s0 = 0.0, s1 = 0.0;
+    int b = lane;
+    for (; b + 32 < p; b += 64) {
+        s0 = fma(row[b], vc[b], s0);
+        s1 = fma(row[b + 32], vc[b + 32], s1);
     }
+    if (b < p) s0 = fma(row[b], vc[b], s0);
+    const double s = warp_sum(s0 + s1);
+    if (lane == 0) B[static_cast<int64_t>(c) * p + a] = s;
 }
 
 // 5. A~[a][c] = V[:,a]^T B[:,c] / (sigma_a sigma_c), one CTA per column c.
@@ -475,307 +594,369 @@ atilde_kernel(const double* __restrict__ V, const double* __restrict__ B,
         s = warp_sum(s);
         if (lane == 0) {
             const double den = sigma[a] * sigma[c];
-            At[static_cast<int64_t>(c) * r + a] = den > 0.0 ? s / den : 0.0;
+            At[static_cast<int64_t>(c) * r + a] = den > 0.0 ? s * rcp64(den) : 0.0;
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// 6. Eigen-decomposition of the real r x r A~ in one CTA: Householder
-// Hessenberg reduction, complex single-shift QR (Wilkinson shift, bulge chase
-// with Givens rotations) to a complex Schur form, eigenvectors by
-// back-substitution, W = Q Z X; columns scaled to unit norm with the
-// largest-modulus entry real positive; eigenvalues ordered by descending
-// modulus with conjugate pairs adjacent (+Im first).
+// 6. Eigen-decomposition of the real r x r A~ (r <= 32).
+// 6a (FP32, one warp): Householder Hessenberg reduction, complex single-shift
+//     QR (Wilkinson shift, bulge chase with Givens rotations) to a complex
+//     Schur form, eigenvectors by back-substitution, W = Q Z X.
+// 6b (FP64, one CTA per eigenpair): Newton's method on (A~ - mu I) w = 0 with
+//     the largest entry of w held at 1: each step solves the bordered linear
+//     system for (delta w, delta mu) by Gaussian elimination with partial
+//     pivoting; quadratic convergence from the FP32 start.
+// 6c (one warp): unit-norm eigenvectors with the largest-modulus entry real
+//     positive; eigenvalues ordered by descending modulus, conjugate pairs
+//     adjacent with the positive imaginary part first.
 // ---------------------------------------------------------------------------
-struct cplx {
-    double x, y;
+struct cf {
+    float x, y;
 };
-__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
-__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.x + b.x, a.y + b.y}; }
-__device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.x - b.x, a.y - b.y}; }
-__device__ __forceinline__ cplx cconj(cplx a) { return {a.x, -a.y}; }
-__device__ __forceinline__ double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
-__device__ __forceinline__ double cabsd(cplx a) { return hypot(a.x, a.y); }
-__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
-    const double s = fabs(b.x) + fabs(b.y);
-    const cplx as = {a.x / s, a.y / s}, bs = {b.x / s, b.y / s};
-    const double den = bs.x * bs.x + bs.y * bs.y;
+__device__ __forceinline__ cf fmulc(cf a, cf b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ cf faddc(cf a, cf b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ cf fsubc(cf a, cf b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ cf fconjc(cf a) { return {a.x, -a.y}; }
+__device__ __forceinline__ float fabs2c(cf a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float fabsc(cf a) { return hypotf(a.x, a.y); }
+__device__ __forceinline__ cf fdivc(cf a, cf b) {
+    const float s = fabsf(b.x) + fabsf(b.y);
+    const cf as = {a.x / s, a.y / s}, bs = {b.x / s, b.y / s};
+    const float den = bs.x * bs.x + bs.y * bs.y;
     return {(as.x * bs.x + as.y * bs.y) / den, (as.y * bs.x - as.x * bs.y) / den};
 }
-__device__ __forceinline__ cplx csqrt_(cplx a) {
-    const double m = cabsd(a);
-    if (m == 0.0) return {0.0, 0.0};
-    double re = sqrt(0.5 * (m + fabs(a.x)));
-    double im = 0.5 * a.y / re;
-    if (a.x < 0.0) {
-        const double t = re;
-        re = fabs(im);
-        im = (a.y >= 0.0) ? t : -t;
+__device__ __forceinline__ cf fsqrtc(cf a) {
+    const float m = fabsc(a);
+    if (m == 0.0f) return {0.0f, 0.0f};
+    float re = sqrtf(0.5f * (m + fabsf(a.x)));
+    float im = 0.5f * a.y / re;
+    if (a.x < 0.0f) {
+        const float t = re;
+        re = fabsf(im);
+        im = (a.y >= 0.0f) ? t : -t;
     }
     return {re, im};
 }
 
-constexpr int kMaxR = 32;
-
-__global__ void __launch_bounds__(64)
-eig_small_kernel(const double* __restrict__ At, int r, double* __restrict__ lam_out,
-                 double* __restrict__ W_out, int* status) {
-    extern __shared__ double esm[];
-    typedef double RowD[kMaxR + 1];
-    typedef cplx RowC[kMaxR + 1];
-    RowD* Hr = reinterpret_cast<RowD*>(esm);
-    RowD* Q = Hr + kMaxR;
-    RowC* T = reinterpret_cast<RowC*>(Q + kMaxR);
-    RowC* Zs = T + kMaxR;
-    RowC* X = Zs + kMaxR;
-    __shared__ double hv[kMaxR];
-    __shared__ cplx lamv[kMaxR];
-    __shared__ int order[kMaxR];
-    __shared__ double scal[4];
-    __shared__ cplx rot[2];
-    __shared__ int flag[2];
-    const int tid = threadIdx.x;
-    const int nt = blockDim.x;
-    for (int idx = tid; idx < r * r; idx += nt) {
+__global__ void __launch_bounds__(32)
+eig_f32_kernel(const double* __restrict__ At, int r, float2* __restrict__ lam32, float2* __restrict__ W32,
+               int* status) {
+    __shared__ float Hr[kMaxR][kMaxR + 1];
+    __shared__ float Q[kMaxR][kMaxR + 1];
+    __shared__ cf T[kMaxR][kMaxR + 1];
+    __shared__ cf Zs[kMaxR][kMaxR + 1];
+    __shared__ cf X[kMaxR][kMaxR + 1];
+    __shared__ float hv[kMaxR];
+    const int lane = threadIdx.x;
+    for (int idx = lane; idx < r * r; idx += 32) {
         const int i = idx % r, c = idx / r;
-        Hr[i][c] = At[static_cast<int64_t>(c) * r + i];
-        Q[i][c] = (i == c) ? 1.0 : 0.0;
+        Hr[i][c] = static_cast<float>(At[static_cast<int64_t>(c) * r + i]);
+        Q[i][c] = (i == c) ? 1.0f : 0.0f;
     }
-    __syncthreads();
-    // --- Hessenberg reduction ---
+    __syncwarp();
     for (int j = 0; j + 2 < r; ++j) {
-        if (tid == 0) {
-            double nrm2 = 0.0;
-            for (int i = j + 1; i < r; ++i) nrm2 += Hr[i][j] * Hr[i][j];
-            const double nrm = sqrt(nrm2);
-            const double x0 = Hr[j + 1][j];
-            if (nrm == 0.0) {
-                scal[0] = 0.0;
-            } else {
-                for (int i = j + 1; i < r; ++i) hv[i] = Hr[i][j];
-                hv[j + 1] += (x0 >= 0.0 ? nrm : -nrm);
-                double vn = 0.0;
-                for (int i = j + 1; i < r; ++i) vn += hv[i] * hv[i];
-                scal[0] = vn > 0.0 ? 2.0 / vn : 0.0;
+        float nrm2 = 0.0f;
+        for (int i = j + 1; i < r; ++i) nrm2 += Hr[i][j] * Hr[i][j];
+        const float nrm = sqrtf(nrm2);
+        const float x0 = Hr[j + 1][j];
+        float beta = 0.0f;
+        if (nrm > 0.0f) {
+            float vn = 0.0f;
+            for (int i = j + 1; i < r; ++i) {
+                const float hvi = (i == j + 1) ? x0 + (x0 >= 0.0f ? nrm : -nrm) : Hr[i][j];
+                vn += hvi * hvi;
             }
+            beta = vn > 0.0f ? 2.0f / vn : 0.0f;
         }
-        __syncthreads();
-        const double beta = scal[0];
-        if (beta != 0.0) {
-            // rows: H[j+1:, c] -= beta v (v^T H[j+1:, c]) for every column c
-            for (int c = tid; c < r; c += nt) {
-                double s = 0.0;
-                for (int i = j + 1; i < r; ++i) s += hv[i] * Hr[i][c];
+        __syncwarp();
+        if (lane == 0)
+            for (int i = j + 1; i < r; ++i) hv[i] = (i == j + 1) ? x0 + (x0 >= 0.0f ? nrm : -nrm) : Hr[i][j];
+        __syncwarp();
+        if (beta != 0.0f) {
+            if (lane < r) {
+                float s = 0.0f;
+                for (int i = j + 1; i < r; ++i) s += hv[i] * Hr[i][lane];
                 s *= beta;
-                for (int i = j + 1; i < r; ++i) Hr[i][c] -= s * hv[i];
+                for (int i = j + 1; i < r; ++i) Hr[i][lane] -= s * hv[i];
             }
-            __syncthreads();
-            // columns: H[i, j+1:] -= beta (H[i, j+1:] v) v^T, same for Q
-            for (int i = tid; i < r; i += nt) {
-                double s = 0.0, sq = 0.0;
+            __syncwarp();
+            if (lane < r) {
+                float s = 0.0f, sq = 0.0f;
                 for (int c = j + 1; c < r; ++c) {
-                    s += Hr[i][c] * hv[c];
-                    sq += Q[i][c] * hv[c];
+                    s += Hr[lane][c] * hv[c];
+                    sq += Q[lane][c] * hv[c];
                 }
                 s *= beta;
                 sq *= beta;
                 for (int c = j + 1; c < r; ++c) {
-                    Hr[i][c] -= s * hv[c];
-                    Q[i][c] -= sq * hv[c];
+                    Hr[lane][c] -= s * hv[c];
+                    Q[lane][c] -= sq * hv[c];
                 }
             }
-            __syncthreads();
-            for (int i = j + 2 + tid; i < r; i += nt) Hr[i][j] = 0.0;
+            __syncwarp();
+            if (lane >= j + 2 && lane < r) Hr[lane][j] = 0.0f;
         }
-        __syncthreads();
+        __syncwarp();
     }
-    for (int idx = tid; idx < r * r; idx += nt) {
+    for (int idx = lane; idx < r * r; idx += 32) {
         const int i = idx % r, c = idx / r;
-        T[i][c] = {Hr[i][c], 0.0};
-        Zs[i][c] = {(i == c) ? 1.0 : 0.0, 0.0};
+        T[i][c] = {Hr[i][c], 0.0f};
+        Zs[i][c] = {(i == c) ? 1.0f : 0.0f, 0.0f};
     }
-    __syncthreads();
-    // --- complex Schur form by single-shift QR ---
+    __syncwarp();
+    const float eps32 = 1.1920929e-07f;
     int hi = r - 1, its = 0, total = 0;
     bool failed = false;
     while (hi > 0) {
-        if (tid == 0) {
-            int lo = hi;
-            while (lo > 0) {
-                const double s = cabsd(T[lo - 1][lo - 1]) + cabsd(T[lo][lo]);
-                if (cabsd(T[lo][lo - 1]) <= kEps * s) { T[lo][lo - 1] = {0.0, 0.0}; break; }
-                --lo;
-            }
-            flag[0] = lo;
+        int lo = hi;
+        while (lo > 0) {
+            const float s = fabsc(T[lo - 1][lo - 1]) + fabsc(T[lo][lo]);
+            if (fabsc(T[lo][lo - 1]) <= eps32 * s) break;
+            --lo;
         }
-        __syncthreads();
-        const int lo = flag[0];
-        if (lo == hi) { --hi; its = 0; __syncthreads(); continue; }
+        __syncwarp();
+        if (lo > 0 && lane == 0) T[lo][lo - 1] = {0.0f, 0.0f};
+        if (lo == hi) { --hi; its = 0; __syncwarp(); continue; }
         ++its;
         ++total;
         if (its > 60 || total > 60 * r) { failed = true; break; }
-        if (tid == 0) {
-            const cplx a = T[hi - 1][hi - 1], b = T[hi - 1][hi], c = T[hi][hi - 1], d = T[hi][hi];
-            cplx mu;
+        cf mu;
+        {
+            const cf a = T[hi - 1][hi - 1], b = T[hi - 1][hi], c = T[hi][hi - 1], dv = T[hi][hi];
             if (its % 11 == 0) {
-                mu = {d.x + cabsd(c), d.y};
+                mu = {dv.x + fabsc(c), dv.y};
             } else {
-                const cplx half = {0.5 * (a.x - d.x), 0.5 * (a.y - d.y)};
-                const cplx bc = cmul(b, c);
-                const cplx disc = csqrt_(cadd(cmul(half, half), bc));
-                const cplx s1 = cadd(half, disc), s2 = csub(half, disc);
-                cplx mu1 = d, mu2 = d;
-                if (cabs2(s1) > 0.0) mu1 = csub(d, cdiv(bc, s1));
-                if (cabs2(s2) > 0.0) mu2 = csub(d, cdiv(bc, s2));
-                mu = (cabs2(csub(mu1, d)) <= cabs2(csub(mu2, d))) ? mu1 : mu2;
+                const cf half = {0.5f * (a.x - dv.x), 0.5f * (a.y - dv.y)};
+                const cf bc = fmulc(b, c);
+                const cf disc = fsqrtc(faddc(fmulc(half, half), bc));
+                const cf s1 = faddc(half, disc), s2 = fsubc(half, disc);
+                cf mu1 = dv, mu2 = dv;
+                if (fabs2c(s1) > 0.0f) mu1 = fsubc(dv, fdivc(bc, s1));
+                if (fabs2c(s2) > 0.0f) mu2 = fsubc(dv, fdivc(bc, s2));
+                mu = (fabs2c(fsubc(mu1, dv)) <= fabs2c(fsubc(mu2, dv))) ? mu1 : mu2;
             }
-            rot[1] = mu;
         }
-        __syncthreads();
-        const cplx mu = rot[1];
+        __syncwarp();
         for (int q = lo; q < hi; ++q) {
-            if (tid == 0) {
-                cplx x, y;
-                if (q == lo) { x = csub(T[lo][lo], mu); y = T[lo + 1][lo]; }
-                else { x = T[q][q - 1]; y = T[q + 1][q - 1]; }
-                const double rr = sqrt(cabs2(x) + cabs2(y));
-                if (rr == 0.0) { rot[0] = {1.0, 0.0}; scal[1] = 0.0; scal[2] = 0.0; }
-                else { rot[0] = {x.x / rr, x.y / rr}; scal[1] = y.x / rr; scal[2] = y.y / rr; }
+            cf x, y;
+            if (q == lo) { x = fsubc(T[lo][lo], mu); y = T[lo + 1][lo]; }
+            else { x = T[q][q - 1]; y = T[q + 1][q - 1]; }
+            const float rr = sqrtf(fabs2c(x) + fabs2c(y));
+            cf cg_ = {1.0f, 0.0f}, sg = {0.0f, 0.0f};
+            if (rr > 0.0f) {
+                const float inv = 1.0f / rr;
+                cg_ = {x.x * inv, x.y * inv};
+                sg = {y.x * inv, y.y * inv};
             }
-            __syncthreads();
-            const cplx cg_ = rot[0];
-            const cplx sg = {scal[1], scal[2]};
-            // rows q, q+1: [conj(c) conj(s); -s c] applied from the left
+            __syncwarp();
             const int col0 = max(q - 1, 0);
-            for (int c = col0 + tid; c < r; c += nt) {
-                const cplx t0 = T[q][c], t1 = T[q + 1][c];
-                T[q][c] = cadd(cmul(cconj(cg_), t0), cmul(cconj(sg), t1));
-                T[q + 1][c] = csub(cmul(cg_, t1), cmul(sg, t0));
+            if (lane >= col0 && lane < r) {
+                const cf t0 = T[q][lane], t1 = T[q + 1][lane];
+                T[q][lane] = faddc(fmulc(fconjc(cg_), t0), fmulc(fconjc(sg), t1));
+                T[q + 1][lane] = fsubc(fmulc(cg_, t1), fmulc(sg, t0));
             }
-            __syncthreads();
-            // columns q, q+1: multiply by G^H from the right
+            __syncwarp();
             const int row1 = min(q + 3, hi + 1);
-            for (int i = tid; i < r; i += nt) {
-                if (i < row1) {
-                    const cplx t0 = T[i][q], t1 = T[i][q + 1];
-                    T[i][q] = cadd(cmul(t0, cg_), cmul(t1, sg));
-                    T[i][q + 1] = csub(cmul(t1, cconj(cg_)), cmul(t0, cconj(sg)));
+            if (lane < r) {
+                if (lane < row1) {
+                    const cf t0 = T[lane][q], t1 = T[lane][q + 1];
+                    T[lane][q] = faddc(fmulc(t0, cg_), fmulc(t1, sg));
+                    T[lane][q + 1] = fsubc(fmulc(t1, fconjc(cg_)), fmulc(t0, fconjc(sg)));
                 }
-                const cplx z0 = Zs[i][q], z1 = Zs[i][q + 1];
-                Zs[i][q] = cadd(cmul(z0, cg_), cmul(z1, sg));
-                Zs[i][q + 1] = csub(cmul(z1, cconj(cg_)), cmul(z0, cconj(sg)));
+                const cf z0 = Zs[lane][q], z1 = Zs[lane][q + 1];
+                Zs[lane][q] = faddc(fmulc(z0, cg_), fmulc(z1, sg));
+                Zs[lane][q + 1] = fsubc(fmulc(z1, fconjc(cg_)), fmulc(z0, fconjc(sg)));
             }
-            __syncthreads();
-            if (tid == 0 && q > lo) T[q + 1][q - 1] = {0.0, 0.0};
-            __syncthreads();
+            __syncwarp();
+            if (lane == 0 && q > lo) T[q + 1][q - 1] = {0.0f, 0.0f};
+            __syncwarp();
         }
     }
-    if (failed) {
-        if (tid == 0) record_status(status, CDMD_ERR_NOT_CONVERGED);
-    }
-    __syncthreads();
-    // --- eigenvectors of the triangular T ---
-    if (tid == 0) {
-        double tmax = 0.0;
-        for (int i = 0; i < r; ++i)
-            for (int c = i; c < r; ++c) tmax = fmax(tmax, cabsd(T[i][c]));
-        scal[3] = kEps * fmax(tmax, 1e-300);
-    }
-    __syncthreads();
-    const double small = scal[3];
-    for (int j = tid; j < r; j += nt) {
-        for (int i = 0; i < r; ++i) X[i][j] = {i == j ? 1.0 : 0.0, 0.0};
+    if (failed && lane == 0) record_status(status, CDMD_ERR_NOT_CONVERGED);
+    __syncwarp();
+    float tmax = 0.0f;
+    for (int i = 0; i < r; ++i)
+        for (int c = i; c < r; ++c) tmax = fmaxf(tmax, fabsc(T[i][c]));
+    const float small = eps32 * fmaxf(tmax, 1e-30f);
+    if (lane < r) {
+        const int j = lane;
+        for (int i = 0; i < r; ++i) X[i][j] = {i == j ? 1.0f : 0.0f, 0.0f};
         for (int i = j - 1; i >= 0; --i) {
-            cplx s = {0.0, 0.0};
-            for (int q = i + 1; q <= j; ++q) s = cadd(s, cmul(T[i][q], X[q][j]));
-            cplx den = csub(T[i][i], T[j][j]);
-            if (cabsd(den) < small) den = {small, 0.0};
-            const cplx v = cdiv(s, den);
+            cf s = {0.0f, 0.0f};
+            for (int q = i + 1; q <= j; ++q) s = faddc(s, fmulc(T[i][q], X[q][j]));
+            cf den = fsubc(T[i][i], T[j][j]);
+            if (fabsc(den) < small) den = {small, 0.0f};
+            const cf v = fdivc(s, den);
             X[i][j] = {-v.x, -v.y};
         }
-        lamv[j] = T[j][j];
     }
-    __syncthreads();
-    // W = Q (Z X): first Zs <- Zs X (column j by thread j), then Q
-    for (int j = tid; j < r; j += nt) {
-        cplx tmp[kMaxR];
+    __syncwarp();
+    if (lane < r) {
+        const int j = lane;
+        cf tmp[kMaxR];
         for (int i = 0; i < r; ++i) {
-            // X is upper triangular: X[q][j] = 0 for q > j
-            cplx s = {0.0, 0.0};
-            for (int q = 0; q <= j; ++q) s = cadd(s, cmul(Zs[i][q], X[q][j]));
+            cf s = {0.0f, 0.0f};
+            for (int q = 0; q <= j; ++q) s = faddc(s, fmulc(Zs[i][q], X[q][j]));
             tmp[i] = s;
         }
         for (int i = 0; i < r; ++i) {
-            double re = 0.0, im = 0.0;
+            float re = 0.0f, im = 0.0f;
             for (int q = 0; q < r; ++q) {
                 re += Q[i][q] * tmp[q].x;
                 im += Q[i][q] * tmp[q].y;
             }
-            X[i][j] = {re, im};   // column j is only touched by this thread
+            W32[static_cast<int64_t>(j) * r + i] = make_float2(re, im);
         }
+        lam32[j] = make_float2(T[j][j].x, T[j][j].y);
     }
-    __syncthreads();
-    // normalise: unit norm, largest-modulus entry real positive
-    for (int j = tid; j < r; j += nt) {
-        double nrm2 = 0.0, best = -1.0;
-        int bi = 0;
-        for (int i = 0; i < r; ++i) {
-            const double a2 = cabs2(X[i][j]);
-            nrm2 += a2;
-            if (a2 > best) { best = a2; bi = i; }
-        }
-        const double nrm = sqrt(nrm2);
-        cplx ph = {1.0, 0.0};
-        if (best > 0.0) {
-            const double ab = sqrt(best);
-            ph = {X[bi][j].x / ab, -X[bi][j].y / ab};   // conj(x_b) / |x_b|
-        }
-        const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-        for (int i = 0; i < r; ++i) {
-            const cplx v = cmul(X[i][j], ph);
-            X[i][j] = {v.x * inv, v.y * inv};
-        }
-        X[bi][j].y = 0.0;
+}
+
+__global__ void __launch_bounds__(32)
+eig_refine_kernel(const double* __restrict__ At, int r, const float2* __restrict__ lam32,
+                  const float2* __restrict__ W32, double* __restrict__ lamR, double* __restrict__ WR, int* status) {
+    __shared__ double A[kMaxR][kMaxR + 1];
+    __shared__ cd Mx[kMaxR][kMaxR + 1];
+    __shared__ cd wv[kMaxR];
+    __shared__ cd rhs[kMaxR];
+    __shared__ cd zz[kMaxR];
+    __shared__ int perm[kMaxR];
+    const int j = blockIdx.x;
+    const int lane = threadIdx.x;
+    for (int idx = lane; idx < r * r; idx += 32) {
+        const int i = idx % r, c = idx / r;
+        A[i][c] = At[static_cast<int64_t>(c) * r + i];
     }
-    __syncthreads();
-    // ordering (pair-aware, as the paper's modes come in conjugate pairs)
-    if (tid == 0) {
+    cd mu = {static_cast<double>(lam32[j].x), static_cast<double>(lam32[j].y)};
+    cd w = {0.0, 0.0};
+    if (lane < r) {
+        const float2 v = W32[static_cast<int64_t>(j) * r + lane];
+        w = {static_cast<double>(v.x), static_cast<double>(v.y)};
+    }
+    // hold the largest entry of w at 1
+    double key = (lane < r) ? cabs2(w) : -1.0;
+    const double kmax = warp_max(key);
+    const unsigned at = __ballot_sync(0xffffffffu, key == kmax && lane < r);
+    const int pidx = __ffs(at) - 1;
+    const cd wp = shfl_cd(w, pidx);
+    if (kmax > 0.0) w = cmul(w, cinv(wp));
+    if (lane == pidx) w = {1.0, 0.0};
+    if (lane < r) wv[lane] = w;
+    __syncwarp();
+    bool done = false;
+    for (int it = 0; it < 4 && !done; ++it) {
+        // residual and the bordered matrix: column pidx replaced by -w
+        if (lane < r) {
+            cd res = {-mu.x * wv[lane].x + mu.y * wv[lane].y, -mu.x * wv[lane].y - mu.y * wv[lane].x};
+            for (int c = 0; c < r; ++c) {
+                res.x = fma(A[lane][c], wv[c].x, res.x);
+                res.y = fma(A[lane][c], wv[c].y, res.y);
+                Mx[lane][c] = (c == pidx) ? cd{-wv[lane].x, -wv[lane].y}
+                                          : cd{A[lane][c] - (c == lane ? mu.x : 0.0), c == lane ? -mu.y : 0.0};
+            }
+            rhs[lane] = {-res.x, -res.y};
+            perm[lane] = lane;
+        }
+        __syncwarp();
+        // Gaussian elimination with partial pivoting; lane q owns logical row q
+        for (int k = 0; k < r; ++k) {
+            const double mag = (lane >= k && lane < r) ? cabs2(Mx[perm[lane]][k]) : -1.0;
+            const double mbest = warp_max(mag);
+            const unsigned bb = __ballot_sync(0xffffffffu, mag == mbest && lane >= k && lane < r);
+            const int pk = __ffs(bb) - 1;
+            __syncwarp();
+            if (lane == 0 && pk != k) {
+                const int t = perm[k];
+                perm[k] = perm[pk];
+                perm[pk] = t;
+            }
+            __syncwarp();
+            const int prow = perm[k];
+            const cd pv = Mx[prow][k];
+            if (cabs2(pv) == 0.0) continue;
+            const cd inv = cinv(pv);
+            if (lane > k && lane < r) {
+                const int row = perm[lane];
+                const cd l = cmul(Mx[row][k], inv);
+                for (int c = k + 1; c < r; ++c) Mx[row][c] = csub(Mx[row][c], cmul(l, Mx[prow][c]));
+                rhs[row] = csub(rhs[row], cmul(l, rhs[prow]));
+            }
+            __syncwarp();
+        }
+        // back substitution in logical order: z_q = (rhs - sum_{c>q} U_qc z_c) / U_qq
+        for (int q = r - 1; q >= 0; --q) {
+            const int row = perm[q];
+            cd part = {0.0, 0.0};
+            if (lane > q && lane < r) part = cmul(Mx[row][lane], zz[lane]);
+            part.x = warp_sum(part.x);
+            part.y = warp_sum(part.y);
+            if (lane == 0) {
+                const cd pv = Mx[row][q];
+                zz[q] = (cabs2(pv) > 0.0) ? cmul(csub(rhs[row], part), cinv(pv)) : cd{0.0, 0.0};
+            }
+            __syncwarp();
+        }
+        // update: z_pidx is the eigenvalue correction, the rest correct w
+        const cd dmu = zz[pidx];
+        double dw = 0.0;
+        if (lane < r && lane != pidx) {
+            wv[lane] = cadd(wv[lane], zz[lane]);
+            dw = cabs2(zz[lane]);
+        }
+        mu = cadd(mu, dmu);
+        dw = warp_max(dw);
+        done = (cabs2(dmu) <= 1e-28 * cabs2(mu)) && (dw <= 1e-26) && it > 0;
+        __syncwarp();
+    }
+    if (!done && lane == 0) record_status(status, CDMD_ERR_NOT_CONVERGED);
+    if (lane == 0) {
+        lamR[2 * j] = mu.x;
+        lamR[2 * j + 1] = mu.y;
+    }
+    if (lane < r) {
+        WR[2 * (static_cast<int64_t>(j) * r + lane)] = wv[lane].x;
+        WR[2 * (static_cast<int64_t>(j) * r + lane) + 1] = wv[lane].y;
+    }
+}
+
+__global__ void __launch_bounds__(32)
+eig_order_kernel(const double* __restrict__ lamR, const double* __restrict__ WR, int r, double* __restrict__ lam_out,
+                 double* __restrict__ W_out) {
+    __shared__ int order[kMaxR];
+    const int lane = threadIdx.x;
+    if (lane == 0) {
         bool used[kMaxR];
         double key_abs[kMaxR], key_im[kMaxR];
         int first[kMaxR], second[kMaxR];
         int nu = 0;
         for (int i = 0; i < r; ++i) used[i] = false;
         for (int pass = 0; pass < r; ++pass) {
-            // next unused index with the largest imaginary part
             int i = -1;
             for (int q = 0; q < r; ++q)
-                if (!used[q] && (i < 0 || lamv[q].y > lamv[i].y)) i = q;
+                if (!used[q] && (i < 0 || lamR[2 * q + 1] > lamR[2 * i + 1])) i = q;
+            if (i < 0) break;
             used[i] = true;
+            const cd li = {lamR[2 * i], lamR[2 * i + 1]};
             int partner = -1;
-            if (lamv[i].y > 0.0) {
+            if (li.y > 0.0) {
                 double bd = 1e300;
                 for (int q = 0; q < r; ++q) {
                     if (used[q]) continue;
-                    const cplx cj = cconj(lamv[i]);
-                    const double dd2 = cabsd(csub(lamv[q], cj));
-                    if (dd2 < bd) { bd = dd2; partner = q; }
+                    const cd lq = {lamR[2 * q], lamR[2 * q + 1]};
+                    const double d2 = cabs2(csub(lq, cconj(li)));
+                    if (d2 < bd) { bd = d2; partner = q; }
                 }
-                if (partner >= 0 && !(bd <= 1e-9 * fmax(1.0, cabsd(lamv[i])))) partner = -1;
+                const double tol = 1e-9 * fmax(1.0, sqrt(cabs2(li)));
+                if (partner >= 0 && !(bd <= tol * tol)) partner = -1;
                 if (partner >= 0) used[partner] = true;
             }
-            if (i >= 0) {
-                key_abs[nu] = cabsd(lamv[i]);
-                key_im[nu] = lamv[i].y;
-                first[nu] = i;
-                second[nu] = partner;
-                ++nu;
-            }
-            bool all = true;
-            for (int q = 0; q < r; ++q) all = all && used[q];
-            if (all) break;
+            key_abs[nu] = cabs2(li);
+            key_im[nu] = li.y;
+            first[nu] = i;
+            second[nu] = partner;
+            ++nu;
         }
-        // insertion sort of units by (-|lambda|, -Im)
         int perm[kMaxR];
         for (int u = 0; u < nu; ++u) perm[u] = u;
         for (int u = 1; u < nu; ++u) {
@@ -783,8 +964,7 @@ eig_small_kernel(const double* __restrict__ At, int r, double* __restrict__ lam_
             int v = u - 1;
             while (v >= 0) {
                 const int o = perm[v];
-                const bool before = (key_abs[cur] > key_abs[o]) ||
-                                    (key_abs[cur] == key_abs[o] && key_im[cur] > key_im[o]);
+                const bool before = (key_abs[cur] > key_abs[o]) || (key_abs[cur] == key_abs[o] && key_im[cur] > key_im[o]);
                 if (!before) break;
                 perm[v + 1] = perm[v];
                 --v;
@@ -797,14 +977,30 @@ eig_small_kernel(const double* __restrict__ At, int r, double* __restrict__ lam_
             if (second[perm[u]] >= 0) order[pos++] = second[perm[u]];
         }
     }
-    __syncthreads();
-    for (int j = tid; j < r; j += nt) {
-        const int s = order[j];
-        lam_out[2 * j] = lamv[s].x;
-        lam_out[2 * j + 1] = lamv[s].y;
+    __syncwarp();
+    if (lane < r) {
+        const int s = order[lane];
+        lam_out[2 * lane] = lamR[2 * s];
+        lam_out[2 * lane + 1] = lamR[2 * s + 1];
+        // unit 2-norm, largest-modulus entry real positive
+        double n2 = 0.0, best = -1.0;
+        int bi = 0;
         for (int i = 0; i < r; ++i) {
-            W_out[2 * (static_cast<int64_t>(j) * r + i)] = X[i][s].x;
-            W_out[2 * (static_cast<int64_t>(j) * r + i) + 1] = X[i][s].y;
+            const cd v = {WR[2 * (static_cast<int64_t>(s) * r + i)], WR[2 * (static_cast<int64_t>(s) * r + i) + 1]};
+            const double a2 = cabs2(v);
+            n2 += a2;
+            if (a2 > best) { best = a2; bi = i; }
+        }
+        const cd vb = {WR[2 * (static_cast<int64_t>(s) * r + bi)], WR[2 * (static_cast<int64_t>(s) * r + bi) + 1]};
+        const double inv_b = best > 0.0 ? rsqrt64(best) : 0.0;
+        const double inv_n = n2 > 0.0 ? rsqrt64(n2) : 0.0;
+        const cd ph = {vb.x * inv_b * inv_n, -vb.y * inv_b * inv_n};   // conj(v_b)/|v_b| / ||v||
+        for (int i = 0; i < r; ++i) {
+            const cd v = {WR[2 * (static_cast<int64_t>(s) * r + i)], WR[2 * (static_cast<int64_t>(s) * r + i) + 1]};
+            cd o = cmul(v, ph);
+            if (i == bi) o.y = 0.0;
+            W_out[2 * (static_cast<int64_t>(lane) * r + i)] = o.x;
+            W_out[2 * (static_cast<int64_t>(lane) * r + i) + 1] = o.y;
         }
     }
 }
@@ -877,97 +1073,114 @@ hmat_kernel(const double* __restrict__ R, const double* __restrict__ G, int n, i
     }
 }
 
-// 9. OMP in Gram form (one thread; r <= 64).  M = Phi_Y^H Phi_Y (Hermitian,
-// column-major), cvec = Phi_Y^H y1, y2 = ||y1||^2.  The least-squares fit on
-// the selected set solves M_SS beta = c_S through an incrementally grown
-// Cholesky factor.
-__global__ void omp_kernel(const double* __restrict__ M, const double* __restrict__ cvec,
-                           const double* __restrict__ R, const double* __restrict__ lam, int r,
-                           int K, int lstsq, double* __restrict__ beta, int32_t* __restrict__ sel,
-                           int32_t* __restrict__ nsel_out, int* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    cplx L[kMaxR][kMaxR];
-    cplx bsel[kMaxR];
-    cplx ytmp[kMaxR];
-    int S[kMaxR];
-    bool used[kMaxR];
-    const double y2 = R[0];
-    auto Mel = [&](int i, int j) -> cplx {   // M[i][j], column-major storage
-        return {M[2 * (static_cast<int64_t>(j) * r + i)], M[2 * (static_cast<int64_t>(j) * r + i) + 1]};
+// 9. OMP in Gram form, one warp (r <= 32; lane j owns mode j).  M = Phi_Y^H
+// Phi_Y (Hermitian, column-major), cvec = Phi_Y^H y1, ||y1||^2 = R[0][0].
+// Scores |phi_j^H rho|^2 / ||phi_j||^2 with phi_j^H rho = c_j - sum_q M[j][S_q]
+// beta_q; ties (relative 2e-9 on the squared score, i.e. 1e-9 on the score)
+// go to the largest Im(lambda), then the lowest index.  The least-squares fit
+// on the selected set solves M_SS beta = c_S through a Cholesky factor
+// M_SS = L L^H grown by one row per pick; every triangular solve is
+// right-looking (one row per lane, one broadcast per step).
+__global__ void __launch_bounds__(32)
+omp_kernel(const double* __restrict__ M, const double* __restrict__ cvec, const double* __restrict__ R,
+           const double* __restrict__ lam, int r, int K, int lstsq, double* __restrict__ beta,
+           int32_t* __restrict__ sel, int32_t* __restrict__ nsel_out, int* status) {
+    __shared__ cd L[kMaxR][kMaxR + 1];   // L[u][q], u >= q
+    __shared__ double invdiag[kMaxR];
+    __shared__ cd bsel[kMaxR];
+    __shared__ int S[kMaxR];
+    const int lane = threadIdx.x;
+    auto Mel = [&](int i, int jj) -> cd {
+        return {M[2 * (static_cast<int64_t>(jj) * r + i)], M[2 * (static_cast<int64_t>(jj) * r + i) + 1]};
     };
-    auto cv = [&](int i) -> cplx { return {cvec[2 * i], cvec[2 * i + 1]}; };
-    for (int i = 0; i < r; ++i) { used[i] = false; beta[2 * i] = 0.0; beta[2 * i + 1] = 0.0; }
-    const int kmax = lstsq ? r : min(K, r);
+    const bool live = lane < r;
+    const double mjj = live ? Mel(lane, lane).x : 0.0;
+    const double inv_m = (live && mjj > 0.0) ? rcp64(mjj) : 0.0;
+    const cd cj = live ? cd{cvec[2 * lane], cvec[2 * lane + 1]} : cd{0.0, 0.0};
+    const double imlam = live ? lam[2 * lane + 1] : 0.0;
+    bool used = false;
+    const double y2 = R[0];
+    const int kmax_steps = lstsq ? r : min(K, r);
     int ns = 0;
     double res2 = y2;
-    for (int step = 0; step < kmax; ++step) {
+    for (int step = 0; step < kmax_steps; ++step) {
         if (!lstsq && res2 <= 1e-24 * y2) break;
-        int best = -1;
+        int best;
         if (lstsq) {
             best = step;
         } else {
-            double bscore = -1.0;
-            double score[kMaxR];
-            for (int j = 0; j < r; ++j) {
-                score[j] = -1.0;
-                if (used[j]) continue;
-                const double mjj = Mel(j, j).x;
-                if (!(mjj > 0.0)) continue;
-                cplx g = cv(j);
-                for (int q = 0; q < ns; ++q) g = csub(g, cmul(Mel(j, S[q]), bsel[q]));
-                score[j] = sqrt(cabs2(g) / mjj);
-                bscore = fmax(bscore, score[j]);
+            double score = -1.0;
+            if (live && !used && mjj > 0.0) {
+                cd g = cj;
+                for (int q = 0; q < ns; ++q) g = csub(g, cmul(Mel(lane, S[q]), bsel[q]));
+                score = cabs2(g) * inv_m;
             }
-            if (!(bscore > 0.0)) break;
-            for (int j = 0; j < r; ++j) {
-                if (score[j] < bscore * (1.0 - 1e-9)) continue;
-                if (best < 0 || lam[2 * j + 1] > lam[2 * best + 1]) best = j;
-            }
+            const double bmax = warp_max(score);
+            if (!(bmax > 0.0)) break;
+            const bool cand = score >= bmax * (1.0 - 2e-9);
+            const double key = cand ? imlam : -1e300;
+            const double kbest = warp_max(key);
+            const unsigned bb = __ballot_sync(0xffffffffu, cand && key == kbest);
+            best = __ffs(bb) - 1;
         }
-        // grow the Cholesky factor with column `best`
-        cplx lrow[kMaxR];
-        double diag = Mel(best, best).x;
+        // new Cholesky row: solve L x = m (m_q = M[S_q][best]); row = conj(x)
+        cd t = (lane < ns) ? Mel(S[lane], best) : cd{0.0, 0.0};
+        double xs2 = 0.0;
         for (int q = 0; q < ns; ++q) {
-            cplx s = Mel(S[q], best);   // M[S_q][best]
-            for (int u = 0; u < q; ++u) s = csub(s, cmul(L[q][u], cconj(lrow[u])));
-            // L[ns][q] = conj(s / L[q][q]) in the convention M = L L^H
-            const cplx v = {s.x / L[q][q].x, s.y / L[q][q].x};
-            lrow[q] = cconj(v);
-            diag -= cabs2(lrow[q]);
+            cd xq = {0.0, 0.0};
+            if (lane == q) xq = cscale(t, invdiag[q]);
+            xq = shfl_cd(xq, q);
+            if (lane == q) { L[ns][q] = cconj(xq); xs2 = cabs2(xq); }
+            if (lane > q && lane < ns) t = csub(t, cmul(L[lane][q], xq));
         }
-        if (!(diag > kEps * Mel(best, best).x)) {
-            if (lstsq) record_status(status, CDMD_ERR_RANK_DEFICIENT);
+        const double diag2 = Mel(best, best).x - warp_sum(xs2);
+        if (!(diag2 > kEps * Mel(best, best).x)) {
+            if (lstsq && lane == 0) record_status(status, CDMD_ERR_RANK_DEFICIENT);
             break;
         }
-        for (int q = 0; q < ns; ++q) L[ns][q] = lrow[q];
-        L[ns][ns] = {sqrt(diag), 0.0};
-        S[ns] = best;
-        used[best] = true;
+        const double invd = rsqrt64(diag2);
+        if (lane == 0) {
+            L[ns][ns] = {diag2 * invd, 0.0};
+            invdiag[ns] = invd;
+            S[ns] = best;
+        }
+        if (lane == best) used = true;
         ++ns;
-        // solve L y = c_S, L^H beta = y
+        __syncwarp();
+        // beta: L y = c_S (forward), then L^H beta = y (backward); lane u owns row u
+        cd v = (lane < ns) ? cd{cvec[2 * S[lane]], cvec[2 * S[lane] + 1]} : cd{0.0, 0.0};
         for (int q = 0; q < ns; ++q) {
-            cplx s = cv(S[q]);
-            for (int u = 0; u < q; ++u) s = csub(s, cmul(L[q][u], ytmp[u]));
-            ytmp[q] = {s.x / L[q][q].x, s.y / L[q][q].x};
+            cd yq = {0.0, 0.0};
+            if (lane == q) { yq = cscale(v, invdiag[q]); v = yq; }
+            yq = shfl_cd(yq, q);
+            if (lane > q && lane < ns) v = csub(v, cmul(L[lane][q], yq));
         }
         for (int q = ns - 1; q >= 0; --q) {
-            cplx s = ytmp[q];
-            for (int u = q + 1; u < ns; ++u) s = csub(s, cmul(cconj(L[u][q]), bsel[u]));
-            bsel[q] = {s.x / L[q][q].x, s.y / L[q][q].x};
+            cd bq = {0.0, 0.0};
+            if (lane == q) { bq = cscale(v, invdiag[q]); v = bq; }
+            bq = shfl_cd(bq, q);
+            if (lane < q) v = csub(v, cmul(cconj(L[q][lane]), bq));
         }
-        double cb = 0.0;   // Re(c_S^H beta)
-        for (int q = 0; q < ns; ++q) {
-            const cplx c = cv(S[q]);
-            cb += c.x * bsel[q].x + c.y * bsel[q].y;
+        if (lane < ns) bsel[lane] = v;
+        __syncwarp();
+        double cb = 0.0;
+        if (lane < ns) {
+            const cd c = {cvec[2 * S[lane]], cvec[2 * S[lane] + 1]};
+            cb = fma(c.x, v.x, c.y * v.y);
         }
-        res2 = y2 - cb;
+        res2 = y2 - warp_sum(cb);
     }
-    for (int q = 0; q < ns; ++q) {
-        beta[2 * S[q]] = bsel[q].x;
-        beta[2 * S[q] + 1] = bsel[q].y;
+    if (live) {
+        beta[2 * lane] = 0.0;
+        beta[2 * lane + 1] = 0.0;
     }
-    for (int q = 0; q < K; ++q) sel[q] = (q < ns) ? S[q] : -1;
-    *nsel_out = ns;
+    __syncwarp();
+    if (lane < ns) {
+        beta[2 * S[lane]] = bsel[lane].x;
+        beta[2 * S[lane] + 1] = bsel[lane].y;
+    }
+    if (lane < K) sel[lane] = (lane < ns) ? S[lane] : -1;
+    if (lane == 0) *nsel_out = ns;
 }
 
 // 10. Phi_Y[i][c] = sum_t DY[(t+1)*k + i] G[t][c]
@@ -1002,9 +1215,8 @@ cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int 
     const size_t n_Hv = static_cast<size_t>(p) * p;
     const size_t n_vec = static_cast<size_t>(p);
     const size_t n_Z = static_cast<size_t>(p) * r;
-    const size_t n_work = static_cast<size_t>(r) * 6 * p;
     const size_t n_small = static_cast<size_t>(r) * r * 2;
-    size_t total = n_gram_part + n_R + n_Hv + 3 * n_vec + r + n_Z + n_work + 2 * n_Z + n_small * 3 + 2 * r + 64;
+    const size_t total = n_gram_part + n_R + n_Hv + 3 * n_vec + r + 3 * n_Z + 5 * n_small + 6 * r + 64;
     double* ws = nullptr;
     cdmd_status st = ensure_buffer(ctx, BUF_EIG, total * sizeof(double), reinterpret_cast<void**>(&ws));
     if (st != CDMD_OK) return st;
@@ -1016,13 +1228,16 @@ cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int 
     double* ee = dd + n_vec;
     double* lamT = ee + n_vec;
     double* Z = lamT + r;
-    double* work = Z + n_Z;
-    double* V = work + n_work;
+    double* V = Z + n_Z;
     double* B = V + n_Z;
     double* At = B + n_Z;
     double* W = At + n_small;
     double* M = W + n_small;
-    double* cvec = M + n_small;
+    double* WR = M + n_small;
+    double* lamR = WR + n_small;
+    double* cvec = lamR + 2 * r;
+    float* lam32 = reinterpret_cast<float*>(cvec + 2 * r);       // 2r floats
+    float* W32 = reinterpret_cast<float*>(cvec + 4 * r);         // 2r^2 floats (n_small/2 doubles)
 
     // 1. Gram
     gram_partial_kernel<<<dim3(ntiles, ntiles, splits), 256, 0, stream>>>(DY, k, n, kchunk, gpart);
@@ -1064,33 +1279,34 @@ cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int 
             break;
         }
     } else {
-        // p <= 2: A is already tridiagonal
         tiny_tridiag_kernel<<<1, 1, 0, stream>>>(R, n, p, dd, ee, htau);
         CDMD_CHECK_LAUNCH("tiny_tridiag_kernel");
     }
-    // 3. eigenpairs of T
+    // 3. eigenpairs of T, orthonormalisation, back-transform
     {
-        const size_t esm = 9 * static_cast<size_t>(p) * sizeof(double);
+        const size_t esm = 10 * static_cast<size_t>(p) * sizeof(double);
         CDMD_CHECK_CUDA(cudaFuncSetAttribute(tridiag_eigpair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(esm)));
         tridiag_eigpair_kernel<<<r, 32, esm, stream>>>(dd, ee, p, r, lamT, Z, ctx->d_status);
+        CDMD_CHECK_LAUNCH("tridiag_eigpair_kernel");
     }
-    CDMD_CHECK_LAUNCH("tridiag_eigpair_kernel");
-    orthonormalise_kernel<<<1, 256, 0, stream>>>(Z, p, r);
+    orthonormalise_kernel<<<1, 1024, 0, stream>>>(Z, p, r);
     CDMD_CHECK_LAUNCH("orthonormalise_kernel");
-    backtransform_kernel<<<r, 32, p * sizeof(double), stream>>>(Z, Hv, htau, lamT, R, n, p, r, V, B, sigma,
-                                                                 ctx->d_status);
+    backtransform_kernel<<<r, 32, p * sizeof(double), stream>>>(Z, Hv, htau, lamT, p, r, V, sigma, ctx->d_status);
     CDMD_CHECK_LAUNCH("backtransform_kernel");
     // 4. A~ and its eigen-decomposition
+    bmat_kernel<<<dim3((p + 7) / 8, r), 256, 0, stream>>>(R, V, n, p, B);
+    CDMD_CHECK_LAUNCH("bmat_kernel");
     atilde_kernel<<<r, 32, 0, stream>>>(V, B, sigma, p, r, At);
     CDMD_CHECK_LAUNCH("atilde_kernel");
-    {
-        const size_t esmem = static_cast<size_t>(kMaxR) * (kMaxR + 1) * (2 * sizeof(double) + 3 * sizeof(cplx));
-        CDMD_CHECK_CUDA(cudaFuncSetAttribute(eig_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(esmem)));
-        eig_small_kernel<<<1, 64, esmem, stream>>>(At, r, lambda, W, ctx->d_status);
-    }
-    CDMD_CHECK_LAUNCH("eig_small_kernel");
+    eig_f32_kernel<<<1, 32, 0, stream>>>(At, r, reinterpret_cast<float2*>(lam32), reinterpret_cast<float2*>(W32),
+                                         ctx->d_status);
+    CDMD_CHECK_LAUNCH("eig_f32_kernel");
+    eig_refine_kernel<<<r, 32, 0, stream>>>(At, r, reinterpret_cast<const float2*>(lam32),
+                                            reinterpret_cast<const float2*>(W32), lamR, WR, ctx->d_status);
+    CDMD_CHECK_LAUNCH("eig_refine_kernel");
+    eig_order_kernel<<<1, 32, 0, stream>>>(lamR, WR, r, lambda, W);
+    CDMD_CHECK_LAUNCH("eig_order_kernel");
     // 5. G, Gram-form quantities, selection
     gmat_kernel<<<(p * r + 127) / 128, 128, 0, stream>>>(V, sigma, W, p, r, G);
     CDMD_CHECK_LAUNCH("gmat_kernel");
