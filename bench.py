@@ -106,6 +106,15 @@ class ClockSampler:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
+            return
+        # nvidia-smi's start-up takes driver locks that can stall CUDA calls:
+        # wait for its first sample before the timed region begins
+        import select
+        self.first = ""
+        ready, _, _ = select.select([self.proc.stdout], [], [], 10.0)
+        if ready:
+            self.first = self.proc.stdout.readline()
+        time.sleep(0.3)
 
     def stop(self):
         if self.proc is None:
@@ -119,7 +128,7 @@ class ClockSampler:
             out, _ = self.proc.communicate()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in (getattr(self, "first", "") + out).strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -265,7 +274,6 @@ def run_ours(args, rank, world, local_rank):
         sampler = ClockSampler(gpu_index(local_rank)) if sample_clocks else None
         if sampler:
             sampler.start()
-            time.sleep(0.3)
         start.record(stream)
         for s in range(steps):
             step(prec, evs[s])

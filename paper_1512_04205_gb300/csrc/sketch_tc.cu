@@ -65,7 +65,9 @@ __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float&
     const float x = -1.3862943611198906f * __log2f(u);   // -2 ln u
     float rad;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rad) : "f"(x));
-    const float f = fmaf(__uint2float_rn(wb & 0x3fffffffu), 9.313225746154785e-10f, 4.656612873077393e-10f);
+    // f = (low 30 bits of wb + 1/2) 2^-30 from the top 23 of those bits: a float
+    // in [1, 2) built from the bits, minus 1, plus half a step (no I2F)
+    const float f = __uint_as_float(0x3F800000u | ((wb >> 7) & 0x7FFFFFu)) - (1.0f - 5.9604645e-08f);
     float s, c;
     __sincosf(1.5707963267948966f * f, &s, &c);
     const uint32_t qt = wb >> 30;
@@ -248,17 +250,17 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, int
                 const uint32_t row_t = static_cast<uint32_t>(4 * (q & 31));
                 const uint32_t gq = static_cast<uint32_t>((row_pair0 >> 2) + q);
                 float z[4][8];
+                const int64_t jg = j0 + 8 * g;
                 if (row_pair0 + 4 * q < k) {
+                    // pixels past m (last K step only) are drawn and then zeroed
 #pragma unroll
                     for (int p = 0; p < 8; ++p) {
-                        const int64_t j = j0 + 8 * g + p;
-                        if (j < m) {
-                            const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(j), gq, 0u, 0u), key);
-                            box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
-                            box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
-                        } else {
-                            z[0][p] = z[1][p] = z[2][p] = z[3][p] = 0.0f;
-                        }
+                        const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), key);
+                        box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
+                        box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
+                        const bool in = (jg + p) < m;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) z[e][p] = in ? z[e][p] : 0.0f;
                     }
                 } else {
 #pragma unroll

@@ -51,76 +51,103 @@ subtract_kernel(const uint8_t* __restrict__ D, int64_t m, int n, int64_t ldd,
     for (int idx = threadIdx.x; idx < n * NC; idx += kThreads) Ls[idx] = table[idx];
     __syncthreads();
 
+    constexpr int FB = 8;   // frames whose bytes are loaded ahead of the arithmetic
     const int lane = threadIdx.x & 31;
-    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
-    const int64_t base = warp_id * 32 * PX;
-    if (base >= m) return;   // warp-uniform
-
-    float2 a[PX][NC];
-#pragma unroll
-    for (int e = 0; e < PX; ++e) {
-        const int64_t j = base + lane + 32 * e;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            float2 v = make_float2(0.f, 0.f);
-            if (j < m && c < ncols) {
-                const float2 ph = Phi[j * ncols + c];
-                const float2 b = amp[c];
-                v = make_float2(ph.x * b.x - ph.y * b.y, ph.x * b.y + ph.y * b.x);
-            }
-            a[e][c] = v;
-        }
-    }
-    float bg_static[PX];
-    if (MODE == CDMD_BG_STATIC) {
-#pragma unroll
-        for (int e = 0; e < PX; ++e) {
-            float zr = 0.f, zi = 0.f;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                zr += a[e][c].x;
-                zi += a[e][c].y;
-            }
-            bg_static[e] = sqrtf(zr * zr + zi * zi);
-        }
-    }
-    const int64_t word0 = warp_id * PX;
-    for (int t = 0; t < n; ++t) {
-        const float2* lt = Ls + t * NC;
-        uint32_t words[PX];
+    const int64_t warps_total = static_cast<int64_t>(gridDim.x) * (kThreads / 32);
+    const int64_t tiles = (m + 32 * PX - 1) / (32 * PX);
+    for (int64_t tile = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5; tile < tiles;
+         tile += warps_total) {
+        const int64_t base = tile * 32 * PX;
+        float2 a[PX][NC];
 #pragma unroll
         for (int e = 0; e < PX; ++e) {
             const int64_t j = base + lane + 32 * e;
-            float bg;
-            if (MODE == CDMD_BG_STATIC) {
-                bg = bg_static[e];
-            } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float2 v = make_float2(0.f, 0.f);
+                if (j < m && c < ncols) {
+                    const float2 ph = Phi[j * ncols + c];
+                    const float2 b = amp[c];
+                    v = make_float2(ph.x * b.x - ph.y * b.y, ph.x * b.y + ph.y * b.x);
+                }
+                a[e][c] = v;
+            }
+        }
+        float bg_static[PX];
+        if (MODE == CDMD_BG_STATIC) {
+#pragma unroll
+            for (int e = 0; e < PX; ++e) {
                 float zr = 0.f, zi = 0.f;
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const float2 l = lt[c];
-                    zr = fmaf(a[e][c].x, l.x, zr);
-                    zr = fmaf(-a[e][c].y, l.y, zr);
-                    zi = fmaf(a[e][c].x, l.y, zi);
-                    zi = fmaf(a[e][c].y, l.x, zi);
+                    zr += a[e][c].x;
+                    zi += a[e][c].y;
                 }
-                bg = (MODE == CDMD_BG_MODULUS) ? sqrtf(zr * zr + zi * zi) : zr;
+                bg_static[e] = sqrtf(zr * zr + zi * zi);
             }
-            bool bit = false;
-            if (j < m) {
-                const float x = static_cast<float>(D[static_cast<int64_t>(t) * ldd + j]);
-                bit = fabsf(x - bg) > tau;
-                if (bg_out) bg_out[static_cast<int64_t>(t) * m + j] = bg;
-            }
-            words[e] = __ballot_sync(0xffffffffu, bit);
         }
-        if (lane < PX) {
-            uint32_t w = words[0];
+        const int64_t word0 = tile * PX;
+        for (int t0 = 0; t0 < n; t0 += FB) {
+            float xv[FB][PX];
 #pragma unroll
-            for (int e = 1; e < PX; ++e)
-                if (lane == e) w = words[e];
-            const int64_t wi = word0 + lane;
-            if (wi < words_per_frame) mask[static_cast<int64_t>(t) * words_per_frame + wi] = w;
+            for (int f = 0; f < FB; ++f)
+#pragma unroll
+                for (int e = 0; e < PX; ++e) {
+                    const int64_t j = base + lane + 32 * e;
+                    xv[f][e] = (t0 + f < n && j < m)
+                                   ? static_cast<float>(__ldg(D + static_cast<int64_t>(t0 + f) * ldd + j)) : 0.0f;
+                }
+#pragma unroll
+            for (int f = 0; f < FB; ++f) {
+                const int t = t0 + f;
+                if (t >= n) break;
+                const float2* lt = Ls + t * NC;
+                uint32_t words[PX];
+#pragma unroll
+                for (int e = 0; e < PX; ++e) {
+                    const int64_t j = base + lane + 32 * e;
+                    const float x = xv[f][e];
+                    bool bit;
+                    float bg = 0.0f;
+                    if (MODE == CDMD_BG_STATIC) {
+                        bg = bg_static[e];
+                        bit = fabsf(x - bg) > tau;
+                    } else {
+                        float zr = 0.f, zi = 0.f;
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            const float2 l = lt[c];
+                            zr = fmaf(a[e][c].x, l.x, zr);
+                            zr = fmaf(-a[e][c].y, l.y, zr);
+                            zi = fmaf(a[e][c].x, l.y, zi);
+                            zi = fmaf(a[e][c].y, l.x, zi);
+                        }
+                        if (MODE == CDMD_BG_REAL) {
+                            bg = zr;
+                            bit = fabsf(x - bg) > tau;
+                        } else if (bg_out != nullptr) {
+                            bg = sqrtf(zr * zr + zi * zi);
+                            bit = fabsf(x - bg) > tau;
+                        } else {
+                            // |x - |z|| > tau  <=>  |z|^2 > (x + tau)^2  or  (x - tau > 0 and |z|^2 < (x - tau)^2)
+                            const float q = fmaf(zr, zr, zi * zi);
+                            const float up = x + tau, dn = x - tau;
+                            bit = (q > up * up) || (dn > 0.0f && q < dn * dn);
+                        }
+                    }
+                    bit = bit && (j < m);
+                    if (bg_out != nullptr && j < m) bg_out[static_cast<int64_t>(t) * m + j] = bg;
+                    words[e] = __ballot_sync(0xffffffffu, bit);
+                }
+                if (lane < PX) {
+                    uint32_t w = words[0];
+#pragma unroll
+                    for (int e = 1; e < PX; ++e)
+                        if (lane == e) w = words[e];
+                    const int64_t wi = word0 + lane;
+                    if (wi < words_per_frame) mask[static_cast<int64_t>(t) * words_per_frame + wi] = w;
+                }
+            }
         }
     }
 }
@@ -130,7 +157,12 @@ cdmd_status launch_nc(cdmd_bgmode mode, const uint8_t* D, int64_t m, int n, int6
                       const float2* Phi, int ncols, const float2* table, const float2* amp,
                       float tau, uint32_t* mask, float* bg, cudaStream_t stream) {
     const int64_t warps = (m + 32 * PX - 1) / (32 * PX);
-    const int64_t blocks = (warps * 32 + kThreads - 1) / kThreads;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // persistent: a few CTAs per SM walk the pixel tiles (the lambda^t table
+    // is staged once per CTA)
+    const int64_t blocks = std::min<int64_t>((warps * 32 + kThreads - 1) / kThreads, static_cast<int64_t>(sms) * 3);
     const size_t smem = static_cast<size_t>(n) * NC * sizeof(float2);
     const int64_t wpf = (m + 31) / 32;
 #define CDMD_SUB_MODE(MV)                                                                         \
