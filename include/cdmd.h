@@ -135,6 +135,16 @@ cdmd_status cdmd_create(cdmd_ctx** ctx, int device);
  * the device to finish work that uses the workspace. */
 void cdmd_destroy(cdmd_ctx* ctx);
 
+/* Cap the grids of the full-data passes (sketch, lift, subtract) issued
+ * through this context at `max_sms` streaming multiprocessors' worth of CTAs
+ * (0 = the whole device; larger values are clamped to it).  The paper has no
+ * counterpart: Algorithm 1 treats one clip at a time.  The cap leaves SMs free
+ * so that the latency-bound small solves of another clip, issued through
+ * another context on another stream, run beside this context's passes.
+ * The cap changes results only through the split of the sketch's pixel sums
+ * (rounding order).  CDMD_ERR_INVALID_ARG for a NULL ctx or a negative cap. */
+cdmd_status cdmd_set_sm_limit(cdmd_ctx* ctx, int max_sms);
+
 /* Message of the last error returned on this host thread ("" if none). */
 const char* cdmd_last_error(void);
 

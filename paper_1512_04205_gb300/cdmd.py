@@ -33,7 +33,7 @@ SELECTORS = {"omp": 0, "lstsq": 1}
 EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_string", "cdmd_status_sync",
             "cdmd_measure_sparse_nnz", "cdmd_measure_build", "cdmd_sketch", "cdmd_sketch_gather",
             "cdmd_decompose", "cdmd_lift", "cdmd_subtract", "cdmd_run", "cdmd_run_host",
-            "cdmd_workspace_views", "cdmd_sketch_noalloc"]
+            "cdmd_workspace_views", "cdmd_sketch_noalloc", "cdmd_set_sm_limit"]
 
 
 class CdmdError(RuntimeError):
@@ -75,6 +75,7 @@ def load_library(path=LIB_PATH):
         "cdmd_last_error": [],
         "cdmd_status_string": [ctypes.c_int],
         "cdmd_status_sync": [vp, vp],
+        "cdmd_set_sm_limit": [vp, ctypes.c_int],
         "cdmd_measure_sparse_nnz": [vp, i64, ctypes.c_int, u64, dbl, ctypes.POINTER(i64), vp],
         "cdmd_measure_build": [vp, ctypes.POINTER(cdmd_measure), vp],
         "cdmd_sketch": [vp, vp, i64, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, u64, ctypes.c_int, vp, vp],
@@ -144,6 +145,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def cdmd_set_sm_limit(ctx, max_sms):
+    """Cap the full-data passes of this context at max_sms SMs (0 = all)."""
+    _check(ctx.lib.cdmd_set_sm_limit(ctx.handle, int(max_sms)))
 
 
 def cdmd_status_sync(ctx, stream=None):

@@ -108,7 +108,8 @@ cdmd_status cdmd_create(cdmd_ctx** ctx, int device) {
     DeviceGuard g(device);
     cdmd_ctx* c = new cdmd_ctx();
     c->device = device;
-    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    e = cudaDeviceGetAttribute(&c->device_sms, cudaDevAttrMultiProcessorCount, device);
+    c->num_sms = c->device_sms;
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -117,6 +118,14 @@ cdmd_status cdmd_create(cdmd_ctx** ctx, int device) {
         return cuda_fail(e, "cdmd_create");
     }
     *ctx = c;
+    return CDMD_OK;
+}
+
+cdmd_status cdmd_set_sm_limit(cdmd_ctx* ctx, int max_sms) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(max_sms >= 0, "max_sms = %d must be >= 0", max_sms);
+    ctx->num_sms = (max_sms == 0) ? ctx->device_sms : std::min(max_sms, ctx->device_sms);
     return CDMD_OK;
 }
 

@@ -146,7 +146,8 @@ enum BufferId {
 
 struct cdmd_ctx {
     int device = 0;
-    int num_sms = 0;
+    int device_sms = 0;    // SMs of the device
+    int num_sms = 0;       // SMs the full-data passes size their grids for (cdmd_set_sm_limit)
     int* d_status = nullptr;
     cdmd::Buffer buf[cdmd::BUF_COUNT];
     // views of the last cdmd_run

@@ -155,11 +155,8 @@ subtract_kernel(const uint8_t* __restrict__ D, int64_t m, int n, int64_t ldd,
 template <int NC, int PX>
 cdmd_status launch_nc(cdmd_bgmode mode, const uint8_t* D, int64_t m, int n, int64_t ldd,
                       const float2* Phi, int ncols, const float2* table, const float2* amp,
-                      float tau, uint32_t* mask, float* bg, cudaStream_t stream) {
+                      float tau, uint32_t* mask, float* bg, int sms, cudaStream_t stream) {
     const int64_t warps = (m + 32 * PX - 1) / (32 * PX);
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // persistent: a few CTAs per SM walk the pixel tiles (the lambda^t table
     // is staged once per CTA)
     const int64_t blocks = std::min<int64_t>((warps * 32 + kThreads - 1) / kThreads, static_cast<int64_t>(sms) * 3);
@@ -207,14 +204,14 @@ cdmd_status launch_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, i
     CDMD_CHECK_LAUNCH("subtract_table_kernel");
     const float2* ph = reinterpret_cast<const float2*>(Phi);
     switch (nc_pad) {
-        case 4: return launch_nc<4, 4>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, stream);
-        case 8: return launch_nc<8, 4>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, stream);
-        case 10: return launch_nc<10, 2>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, stream);
-        case 12: return launch_nc<12, 2>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, stream);
-        case 16: return launch_nc<16, 2>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, stream);
-        case 20: return launch_nc<20, 1>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, stream);
-        case 24: return launch_nc<24, 1>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, stream);
-        default: return launch_nc<32, 1>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, stream);
+        case 4: return launch_nc<4, 4>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, ctx->num_sms, stream);
+        case 8: return launch_nc<8, 4>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, ctx->num_sms, stream);
+        case 10: return launch_nc<10, 2>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, ctx->num_sms, stream);
+        case 12: return launch_nc<12, 2>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, ctx->num_sms, stream);
+        case 16: return launch_nc<16, 2>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, ctx->num_sms, stream);
+        case 20: return launch_nc<20, 1>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, ctx->num_sms, stream);
+        case 24: return launch_nc<24, 1>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, ctx->num_sms, stream);
+        default: return launch_nc<32, 1>(mode, D, m, n, ldd, ph, ncols, table, amp, tau, mask, bg, ctx->num_sms, stream);
     }
 }
 

@@ -141,3 +141,51 @@ def test_mixed_precision_pipeline_160x120(C, ctx, seed):
     mask2 = C.cdmd_run(ctx, D, C.make_params(k, r, K, tau, seed=cseed, prec="bf16x2"))
     C.cdmd_status_sync(ctx)
     assert np.array_equal(mask2.cpu().numpy(), mask.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x2"])
+def test_two_clips_in_flight_match_solo_runs(C, prec):
+    # Two contexts on two streams, each capped below the device's SM count, run
+    # two clips concurrently; every output equals that clip's solo run under
+    # the same cap bit for bit, and the cap itself moves eigenvalues only by
+    # the rounding of the sketch's pixel split.
+    clips = [videogen.make_clip(320, 240, 120, seed=20 + i) for i in range(2)]
+    Ds = [torch.from_numpy(c.frames).cuda() for c in clips]
+    k, r, K, tau, cseed = 300, 12, 8, 25.0, 77
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cap = max(1, sms - 16)
+
+    def run(ctx, D):
+        DY = C.cdmd_sketch(ctx, D, k, cseed, prec=prec)
+        dec = C.cdmd_decompose(ctx, DY, r, K)
+        Phi = C.cdmd_lift(ctx, D, dec["G"], cols=dec["sel"], ncols=K, prec=prec)
+        mask = C.cdmd_subtract(ctx, D, Phi, dec["beta"], dec["lam"], tau, cols=dec["sel"])
+        return mask, dec["lam"], DY
+
+    solo_ctx = C.Context(0)
+    C.cdmd_set_sm_limit(solo_ctx, cap)
+    solo = []
+    for D in Ds:
+        solo.append(run(solo_ctx, D))
+        C.cdmd_status_sync(solo_ctx)
+    ctxs = [C.Context(0), C.Context(0)]
+    for c in ctxs:
+        C.cdmd_set_sm_limit(c, cap)
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    streams[1].wait_stream(streams[0])
+    out = [None, None]
+    for rep in range(3):
+        for i in range(2):
+            with torch.cuda.stream(streams[i]):
+                out[i] = run(ctxs[i], Ds[i])
+    for i in range(2):
+        C.cdmd_status_sync(ctxs[i], streams[i])
+        for a, b in zip(out[i], solo[i]):
+            assert torch.equal(a, b)
+    # uncapped run: the same eigenvalues up to the sketch's rounding order
+    full_ctx = C.Context(0)
+    _, lam_full, _ = run(full_ctx, Ds[0])
+    C.cdmd_status_sync(full_ctx)
+    lam_full = torch.view_as_complex(lam_full).cpu().numpy()
+    lam_cap = torch.view_as_complex(solo[0][1]).cpu().numpy()
+    assert np.max(np.abs(lam_full - lam_cap) / np.abs(lam_cap)) < 1e-5
