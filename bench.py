@@ -40,9 +40,30 @@ METRIC = "cDMD 1080p frames/s"
 UNIT = "frames/s"
 
 
-def workload_name(prec):
+def workload_name(prec, selector="omp"):
     w = WORKLOAD
-    return f"cdmd_{w['width']}x{w['height']}_n{w['n']}_k{w['k']}_r{w['r']}_K{w['K']}_gaussian_{prec}"
+    return f"cdmd_{w['width']}x{w['height']}_n{w['n']}_k{w['k']}_r{w['r']}_K{w['K']}_gaussian_{prec}_{selector}"
+
+
+def fmeasure(pred, truth):
+    """F-measure of a boolean mask against the generator's ground truth."""
+    tp = float(np.count_nonzero(pred & truth))
+    fp = float(np.count_nonzero(pred & ~truth))
+    fn = float(np.count_nonzero(~pred & truth))
+    prec = tp / (tp + fp) if tp + fp > 0 else 0.0
+    rec = tp / (tp + fn) if tp + fn > 0 else 0.0
+    return 2 * prec * rec / (prec + rec) if prec + rec > 0 else 0.0
+
+
+def launches_per_step(selector, K):
+    """Kernels one pipeline step launches: sketch 2 (tiles + fixed-order
+    reduce); decompose 15 (Gram 2, tridiagonalisation 1, eigenpairs 1,
+    orthonormalise 1, back-transform 1, B 1, A~ 1, eig FP32 1, Newton 1,
+    FP64 QR fallback 1, order 1, G 1, Gram-form H 1, selection 1) + 2 for the
+    learned selection (scoring, least squares on its picks, then the OMP
+    launch that exits at once unless the picks were rejected); lift one per
+    16 modes; subtract 2 (lambda^t table + pass)."""
+    return 2 + 15 + (2 if selector == "mlp" else 0) + (K + 15) // 16 + 2
 
 
 def algorithmic_counts():
@@ -204,8 +225,8 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_clip * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name("f64_oracle"), "m": clip.m, "n": w["n"], "k": w["k"],
-                       "r": w["r"], "K": w["K"]},
+            "config": {"workload": workload_name(args.prec, args.selector), "m": clip.m, "n": w["n"], "k": w["k"],
+                       "r": w["r"], "K": w["K"], "implementation": "FP64 CPU oracle, OMP selection"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -223,6 +244,7 @@ def run_ours(args, rank, world, local_rank):
     import videogen
     from paper_1512_04205_gb300 import build
     from paper_1512_04205_gb300 import cdmd as C
+    from paper_1512_04205_gb300 import selector as SEL
 
     build.build()
     torch.cuda.set_device(local_rank)
@@ -236,6 +258,7 @@ def run_ours(args, rank, world, local_rank):
     m, n, k, r, K = clip.m, clip.n, w["k"], w["r"], w["K"]
     D = torch.from_numpy(clip.frames).to(dev)
     main_stream = torch.cuda.current_stream()
+    model = torch.from_numpy(SEL.load_model()[0]).to(dev) if args.selector == "mlp" else None
 
     class Lane:
         """One clip in flight: its own context (workspace), stream and outputs."""
@@ -247,12 +270,14 @@ def run_ours(args, rank, world, local_rank):
             self.dec = C.decompose_outputs(n, k, r, K, dev)
             self.Phi = torch.empty((m, K, 2), dtype=torch.float32, device=dev)
             self.mask = torch.empty((n, (m + 31) // 32), dtype=torch.int32, device=dev)
+            if model is not None:
+                C.cdmd_selector_load(self.ctx, model, stream=stream)
 
     lanes = [Lane(main_stream)] + [Lane(torch.cuda.Stream(device=dev)) for _ in range(max(0, args.inflight - 1))]
     ctx = lanes[0].ctx
     mask = lanes[0].mask
 
-    def step(prec, events=None, lane=None):
+    def step(prec, selector, events=None, lane=None):
         L = lane or lanes[0]
         st = L.stream
         with torch.cuda.stream(st):
@@ -261,7 +286,7 @@ def run_ours(args, rank, world, local_rank):
             C.cdmd_sketch(L.ctx, D, k, w["c_seed"], prec=prec, DY=L.DY)
             if events is not None:
                 events[1].record(st)
-            C.cdmd_decompose(L.ctx, L.DY, r, K, out=L.dec)
+            C.cdmd_decompose(L.ctx, L.DY, r, K, selector=selector, out=L.dec)
             if events is not None:
                 events[2].record(st)
             C.cdmd_lift(L.ctx, D, L.dec["G"], cols=L.dec["sel"], ncols=K, prec=prec, Phi=L.Phi)
@@ -279,9 +304,9 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(prec, steps, warmup, sample_clocks):
+    def timed(prec, selector, steps, warmup, sample_clocks):
         for _ in range(warmup):
-            step(prec)
+            step(prec, selector)
         C.cdmd_status_sync(ctx)
         barrier()
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
@@ -291,7 +316,7 @@ def run_ours(args, rank, world, local_rank):
             sampler.start()
         start.record(stream)
         for s in range(steps):
-            step(prec, evs[s])
+            step(prec, selector, evs[s])
         end.record(stream)
         torch.cuda.synchronize()
         clocks = sampler.stop() if sampler else None
@@ -305,12 +330,12 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         return total_ms, passes, clocks
 
-    def pipelined(prec, steps, warmup, sample_clocks):
+    def pipelined(prec, selector, steps, warmup, sample_clocks):
         """Whole-job throughput with len(lanes) clips in flight (one per stream)."""
         for L in lanes:
             C.cdmd_set_sm_limit(L.ctx, args.sm_limit)
         for i in range(warmup):
-            step(prec, lane=lanes[i % len(lanes)])
+            step(prec, selector, lane=lanes[i % len(lanes)])
         for L in lanes:
             C.cdmd_status_sync(L.ctx, L.stream)
         barrier()
@@ -322,7 +347,7 @@ def run_ours(args, rank, world, local_rank):
         for L in lanes[1:]:
             L.stream.wait_event(start)
         for i in range(steps):
-            step(prec, lane=lanes[i % len(lanes)])
+            step(prec, selector, lane=lanes[i % len(lanes)])
         for L in lanes[1:]:
             ev = torch.cuda.Event()
             ev.record(L.stream)
@@ -341,20 +366,25 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         return total_ms, clocks
 
+    # the headline form and the plain FP32 + OMP form it is compared with
+    forms = {"head": (args.prec, args.selector)}
+    if not args.no_plain and (args.prec, args.selector) != ("fp32", "omp"):
+        forms["plain"] = ("fp32", "omp")
     results = {}
-    precs = [args.prec] + ([] if args.prec == "fp32" or args.no_plain else ["fp32"])
-    for prec in precs:
-        total_ms, passes, clocks = timed(prec, args.steps, args.warmup, sample_clocks=(prec == args.prec))
-        results[prec] = dict(total_ms=total_ms, passes=passes, clocks=clocks,
-                             mask=C.unpack_mask(mask, m) if prec in ("fp32", args.prec) else None)
+    for label, (prec, selector) in forms.items():
+        total_ms, passes, clocks = timed(prec, selector, args.steps, args.warmup, sample_clocks=(label == "head"))
+        results[label] = dict(total_ms=total_ms, passes=passes, clocks=clocks, mask=C.unpack_mask(mask, m))
+    fallbacks = None
+    if args.selector == "mlp":
+        fallbacks = sum(C.cdmd_selector_fallbacks(L.ctx, reset=True, stream=L.stream) for L in lanes)
 
-    piped_ms, piped_clocks = (pipelined(args.prec, args.steps, args.warmup, True) if len(lanes) > 1
+    piped_ms, piped_clocks = (pipelined(args.prec, args.selector, args.steps, args.warmup, True) if len(lanes) > 1
                               else (None, None))
 
     # end to end through the public host-buffer call
     e2e = None
     if not args.no_e2e:
-        params = C.make_params(k, r, K, w["tau"], seed=w["c_seed"], prec=args.prec)
+        params = C.make_params(k, r, K, w["tau"], seed=w["c_seed"], prec=args.prec, selector=args.selector)
         host = torch.from_numpy(clip.frames).pin_memory()
         hmask = torch.empty((n, (m + 31) // 32), dtype=torch.int32).pin_memory()
         for _ in range(max(1, min(3, args.warmup))):
@@ -377,7 +407,7 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return 0
 
-    head = results[args.prec]
+    head = results["head"]
     steps = args.steps
     latency_value = world * n * steps / (head["total_ms"] * 1e-3)
     value = world * n * steps / (piped_ms * 1e-3) if piped_ms is not None else latency_value
@@ -406,7 +436,7 @@ def run_ours(args, rank, world, local_rank):
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16" if args.prec == "bf16x2" else "f32", "data": "synthetic",
-            "config": {"workload": workload_name(args.prec), "m": m, "n": n, "k": k, "r": r, "K": K,
+            "config": {"workload": workload_name(args.prec, args.selector), "selector": args.selector, "m": m, "n": n, "k": k, "r": r, "K": K,
                        "tau": w["tau"], "measurement": "gaussian (Philox4x32-10, in-kernel)",
                        "precision": ("sketch+lift BF16 hi+lo on tcgen05, FP32 accumulation; FP64 small solves"
                                      if args.prec == "bf16x2" else "sketch+lift FP32 FMA; FP64 small solves"),
@@ -418,20 +448,25 @@ def run_ours(args, rank, world, local_rank):
             "pass_roofline": {"lift_gbs": lift_gbs, "lift_frac_hbm": lift_gbs / hbm, "subtract_gbs": sub_gbs,
                               "subtract_frac_hbm": sub_gbs / hbm, "hbm_peak_gbs": hbm},
             "roofline": roof,
-            "gpu_launches": 16 * steps,
+            "gpu_launches": launches_per_step(args.selector, K) * steps,
             "e2e": e2e}
     if piped_clocks is not None:
         line["clocks"] = piped_clocks
     elif head["clocks"] is not None:
         line["clocks"] = head["clocks"]
-    if "fp32" in results and args.prec != "fp32":
-        plain = results["fp32"]
+    truth = clip.truth.T
+    line["accuracy"] = {"fmeasure_vs_truth": fmeasure(head["mask"], truth),
+                        "selector": args.selector, "selector_fallbacks": fallbacks,
+                        "selector_model": os.path.relpath(SEL.DEFAULT_MODEL, ROOT) if args.selector == "mlp" else None}
+    if "plain" in results:
+        plain = results["plain"]
         agree = plain["mask"] == head["mask"]
+        line["accuracy"]["plain_fp32_omp_fmeasure_vs_truth"] = fmeasure(plain["mask"], truth)
         line["plain_fp32"] = {"value": world * n * steps / (plain["total_ms"] * 1e-3),
                               "ms_per_step": plain["total_ms"] / steps,
                               "per_pass_ms": {nm: float(v) for nm, v in
                                               zip(["sketch", "decompose", "lift", "subtract"], plain["passes"])},
-                              "mask_agreement_vs_mixed": float(agree.mean())}
+                              "mask_agreement_vs_head": float(agree.mean())}
     if not args.no_cpu:
         fps, detail, _, _ = oracle_fps(clip, w["width"] * 8)
         line["cpu_baseline"] = {"value": fps, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
@@ -459,7 +494,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["bf16x2", "fp32"], default="fp32")
+    ap.add_argument("--prec", choices=["bf16x2", "fp32"], default="bf16x2")
+    ap.add_argument("--selector", choices=["mlp", "omp", "lstsq"], default="mlp",
+                    help="mode selection: learned (OMP fallback), OMP, or least squares on all modes")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")

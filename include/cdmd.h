@@ -102,8 +102,14 @@ typedef enum { CDMD_BG_MODULUS = 0, CDMD_BG_REAL = 1, CDMD_BG_STATIC = 2 } cdmd_
 /* Amplitudes / mode selection (Algorithm 1 step 9, Remark 3).
  *   OMP    orthogonal matching pursuit on the compressed modes Phi_Y with
  *          target y1 = DY[:,0], K picks.
- *   LSTSQ  least squares on all r compressed modes (OMP with K = r). */
-typedef enum { CDMD_SEL_OMP = 0, CDMD_SEL_LSTSQ = 1 } cdmd_selector;
+ *   LSTSQ  least squares on all r compressed modes (OMP with K = r).
+ *   MLP    learned selection (no counterpart in the paper, which uses sparse
+ *          coding, Section 2.3): the K modes of highest score under the model
+ *          loaded by cdmd_selector_load, amplitudes by least squares on them;
+ *          if the relative residual ||y1 - Phi_Y,S beta|| / ||y1|| exceeds the
+ *          model's tol, OMP runs instead (counted, see
+ *          cdmd_selector_fallbacks). */
+typedef enum { CDMD_SEL_OMP = 0, CDMD_SEL_LSTSQ = 1, CDMD_SEL_MLP = 2 } cdmd_selector;
 
 typedef struct cdmd_ctx cdmd_ctx;
 
@@ -262,6 +268,101 @@ cdmd_status cdmd_run_host(cdmd_ctx* ctx, const uint8_t* D_host, int64_t m, int n
 cdmd_status cdmd_workspace_views(cdmd_ctx* ctx, double** DY, double** sigma, double** lambda,
                                  double** G, double** beta, int32_t** sel, int32_t** nsel,
                                  float** Phi);
+
+/* ---- learned mode selector ------------------------------------------------
+ *
+ * The paper selects background modes by sparse coding (Section 2.3,
+ * Eq. sparsecoding; Remark 3 for the compressed modes).  These calls train
+ * and apply a small network that predicts that selection from four per-mode
+ * features (FP32, row-major r x 4):
+ *   f0 = max(log|lambda_j|, -30), f1 = |arg lambda_j|,
+ *   f2 = max(log(||phi_j|| / max_i ||phi_i||), -30),
+ *   f3 = |phi_j^H y1| / (||phi_j|| ||y1||),
+ * phi_j = column j of Phi_Y, y1 = DY[:,0] (Section 2.2 ties background modes
+ * to |lambda| near 1 and arg lambda near 0).  The network is
+ *   xh = (f - mu) / sd,  h = relu(W1 xh + b1) (64 units),  s = w2 . h + b2,
+ *   p = 1 / (1 + exp(-s)),
+ * trained with the mean binary cross-entropy against OMP labels and Adam.
+ *
+ * Model blob: CDMD_MLP_BLOB floats (device memory, caller-owned):
+ *   [0..3] mu, [4..7] sd, [8] tol, [9..11] zero,
+ *   then CDMD_MLP_PARAMS parameters: W1 (64 x 4 row-major), b1 (64), w2 (64),
+ *   b2 (1).  Gradients and Adam moments use the parameter layout. */
+#define CDMD_MLP_FEATURES 4
+#define CDMD_MLP_HIDDEN 64
+#define CDMD_MLP_PARAMS 385
+#define CDMD_MLP_HEADER 12
+#define CDMD_MLP_BLOB 397
+
+/* Copy a model blob (device) into the context for CDMD_SEL_MLP and reset the
+ * fallback count; the caller's blob may be freed after the copy completes on
+ * `stream`.  Inference rounds the network's matrix operands (xh, W1, h, w2)
+ * to bfloat16 and accumulates in FP32. */
+cdmd_status cdmd_selector_load(cdmd_ctx* ctx, const float* blob, void* stream);
+
+/* Features (r x 4) of the modes of the last cdmd_decompose on ctx, computed
+ * from its Gram quantities (valid until the next cdmd_decompose or cdmd_run
+ * on ctx); lambda is that call's lambda output.  If labels is not NULL,
+ * labels[j] = 1 when mode j appears among sel[0..K-1] (the call's sel
+ * output), else 0.  Device pointers; enqueued on `stream`.
+ * CDMD_ERR_INVALID_ARG if no decomposition with this r was run on ctx. */
+cdmd_status cdmd_selector_features(cdmd_ctx* ctx, const double* lambda, const int32_t* sel, int r, int K,
+                                   float* feats, float* labels, void* stream);
+
+/* OMP (Remark 3) on the compressed modes of the last cdmd_decompose on ctx
+ * against another target y_target (k doubles, device) instead of y1, e.g. the
+ * sketch of a clip's clean background frame when labelling training data:
+ * sel[0..K-1] receives the picks (-1 after the last).  DY, G and lambda are
+ * that call's input and outputs (k, n, r as there); 1 <= K <= r. */
+cdmd_status cdmd_selector_relabel(cdmd_ctx* ctx, const double* DY, int k, int n, const double* G,
+                                  const double* lambda, int r, const double* y_target, int K, int32_t* sel,
+                                  void* stream);
+
+/* Number of CDMD_SEL_MLP decompositions on ctx that fell back to OMP since
+ * the last load or reset.  Synchronises `stream`; reset != 0 zeroes it. */
+cdmd_status cdmd_selector_fallbacks(cdmd_ctx* ctx, int64_t* count, int reset, void* stream);
+
+/* Batch inference: logits s[N] and probabilities p[N] (either may be NULL)
+ * for N feature rows X (N x 4), with bf16 != 0 the BF16 operand rounding of
+ * the in-decompose selection, else FP32 throughout. */
+cdmd_status cdmd_mlp_forward(cdmd_ctx* ctx, const float* blob, const float* X, int64_t N, int bf16,
+                             float* s, float* p, void* stream);
+
+/* Mean loss and its gradient over N >= 1 rows (X: N x 4, Y: N labels in
+ * {0, 1}) at the blob's parameters, FP32 arithmetic with FP64 reduction of
+ * per-warp partial sums in a fixed order (deterministic).  grad:
+ * CDMD_MLP_PARAMS floats; loss: 1 float; device pointers. */
+cdmd_status cdmd_mlp_grad(cdmd_ctx* ctx, const float* blob, const float* X, const float* Y, int64_t N,
+                          float* grad, float* loss, void* stream);
+
+/* One Adam step (Kingma & Ba, Algorithm 1) on the blob's parameters from the
+ * gradient over N rows: m and v (CDMD_MLP_PARAMS floats each, zero before
+ * step 1) are updated in place; step >= 1 counts updates; loss (may be NULL)
+ * receives the loss before the update. */
+cdmd_status cdmd_mlp_train_step(cdmd_ctx* ctx, float* blob, float* m, float* v, int step, float lr, float beta1,
+                                float beta2, float eps, const float* X, const float* Y, int64_t N, float* loss,
+                                void* stream);
+
+/* ---- synthetic clips (selector training data) ----------------------------
+ *
+ * Renders a seeded synthetic clip on the device, shaped like the paper's
+ * surveillance workloads (Section 4: static textured scene, moving
+ * foreground, illumination change, sensor noise).  For frame t and pixel
+ * j = y * width + x (frame-major, D[t * ldd + j]):
+ *   v  = 128 + sum_w amp_w sin((x cos th_w + y sin th_w) 2 pi / period_w + phase_w)
+ *   v  = intensity_q for every object q (in order) whose frame-t rectangle
+ *        (|x + 1/2 - cx| <= w/2 and |y + 1/2 - cy| <= h/2) or ellipse
+ *        (ellipse != 0) contains the pixel centre
+ *   v *= 1 + drift (2 t / (n - 1) - 1)                        (n > 1)
+ *   v += noise_sigma z, z standard normal (Box-Muller on Philox4x32-10 words
+ *        0, 1 of counter (j, t, 4, 0) under key = seed)
+ *   D  = clamp(floor(v + 1/2), 0, 255)
+ * waves: nw x 4 floats [amp, period, theta, phase]; objects: n x nobj x 5
+ * floats [cx, cy, w, h, intensity] (state at frame t); device pointers.
+ * Requires width, height, n >= 1 and ldd >= width * height. */
+cdmd_status cdmd_synth_clip(cdmd_ctx* ctx, int width, int height, int n, const float* waves, int nw,
+                            const float* objects, int nobj, int ellipse, float drift, float noise_sigma,
+                            uint64_t seed, uint8_t* D, int64_t ldd, void* stream);
 
 /* ---- allocation-free sketch ---------------------------------------------
  *

@@ -22,7 +22,9 @@ keeps the sparse-coding solver as its fallback and judge:
   loss       mean binary cross-entropy of p against the OMP label of the mode,
              written as softplus(s) - y s.
   optimiser  Adam (Kingma & Ba, ICLR 2015, Algorithm 1).
-  selection  the K modes of largest p (equal p: lower index first); amplitudes
+  selection  the K modes of largest logit s (equivalently p; equal s: lower
+             index first; ranking by s avoids the ties a saturated sigmoid
+             would create); amplitudes
              by least squares on the selected compressed modes (Eq. b in the
              compressed form of Remark 3); if the relative residual
              ||y1 - Phi_Y,S beta|| / ||y1|| exceeds tol the OMP result is used.
@@ -168,31 +170,31 @@ def adam_step(theta, m, v, g, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 # ----------------------------------------------------------------------------
 
 
-def rank_modes(p):
-    """Mode indices by descending probability; equal values keep index order."""
-    p = np.asarray(p)
-    return np.array(sorted(range(len(p)), key=lambda j: (-p[j], j)), dtype=np.int64)
+def rank_modes(s):
+    """Mode indices by descending logit; equal values keep index order."""
+    s = np.asarray(s)
+    return np.array(sorted(range(len(s)), key=lambda j: (-s[j], j)), dtype=np.int64)
 
 
 def select(theta, mu, sd, tol, lam, PhiY, y1, K, bf16=True):
     """Learned selection of K background modes and their amplitudes.
 
-    Returns dict(sel, beta, fallback, residual, p): sel in pick order, beta the
+    Returns dict(sel, beta, fallback, residual, s, p): sel in pick order, beta the
     least-squares amplitudes on sel; fallback=True when the learned set's
     relative residual exceeded tol and OMP's (sel, beta) were returned.
     """
     PhiY = np.asarray(PhiY, dtype=np.complex128)
     y1 = np.asarray(y1, dtype=np.complex128)
     X = features(lam, PhiY, y1)
-    _, p = forward(theta, X, mu, sd, bf16=bf16)
+    s, p = forward(theta, X, mu, sd, bf16=bf16)
     r = PhiY.shape[1]
-    sel = rank_modes(p)[:min(K, r)]
+    sel = rank_modes(s)[:min(K, r)]
     beta = np.linalg.lstsq(PhiY[:, sel], y1, rcond=None)[0]
     res = np.linalg.norm(y1 - PhiY[:, sel] @ beta) / np.linalg.norm(y1)
     if res > tol:
         osel, obeta = O.omp(PhiY, y1, K, lam)
-        return dict(sel=osel, beta=obeta, fallback=True, residual=res, p=p)
-    return dict(sel=sel, beta=beta, fallback=False, residual=res, p=p)
+        return dict(sel=osel, beta=obeta, fallback=True, residual=res, s=s, p=p)
+    return dict(sel=sel, beta=beta, fallback=False, residual=res, s=s, p=p)
 
 
 def labels(r, sel):

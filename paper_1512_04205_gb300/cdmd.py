@@ -28,12 +28,15 @@ STATUS_NAMES = {0: "CDMD_OK", 1: "CDMD_ERR_INVALID_ARG", 2: "CDMD_ERR_CUDA", 3: 
 CTYPES = {"gaussian": 0, "rademacher": 1, "sparse": 2, "rowsample": 3}
 PRECS = {"fp32": 0, "bf16x2": 1}
 BGMODES = {"modulus": 0, "real": 1, "static": 2}
-SELECTORS = {"omp": 0, "lstsq": 1}
+SELECTORS = {"omp": 0, "lstsq": 1, "mlp": 2}
+MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS, MLP_HEADER, MLP_BLOB = 4, 64, 385, 12, 397
 
 EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_string", "cdmd_status_sync",
             "cdmd_measure_sparse_nnz", "cdmd_measure_build", "cdmd_sketch", "cdmd_sketch_gather",
             "cdmd_decompose", "cdmd_lift", "cdmd_subtract", "cdmd_run", "cdmd_run_host",
-            "cdmd_workspace_views", "cdmd_sketch_noalloc", "cdmd_set_sm_limit"]
+            "cdmd_workspace_views", "cdmd_sketch_noalloc", "cdmd_set_sm_limit", "cdmd_selector_load",
+            "cdmd_selector_features", "cdmd_selector_fallbacks", "cdmd_mlp_forward", "cdmd_mlp_grad",
+            "cdmd_mlp_train_step", "cdmd_synth_clip", "cdmd_selector_relabel"]
 
 
 class CdmdError(RuntimeError):
@@ -89,6 +92,15 @@ def load_library(path=LIB_PATH):
         "cdmd_run_host": [vp, vp, i64, ctypes.c_int, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_workspace_views": [vp] + [ctypes.POINTER(vp)] * 8,
         "cdmd_sketch_noalloc": [vp, i64, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, u64, vp, vp],
+        "cdmd_selector_load": [vp, vp, vp],
+        "cdmd_selector_relabel": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, vp],
+        "cdmd_synth_clip": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int,
+                            ctypes.c_int, flt, flt, u64, vp, i64, vp],
+        "cdmd_selector_features": [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp],
+        "cdmd_selector_fallbacks": [vp, ctypes.POINTER(i64), ctypes.c_int, vp],
+        "cdmd_mlp_forward": [vp, vp, vp, i64, ctypes.c_int, vp, vp, vp],
+        "cdmd_mlp_grad": [vp, vp, vp, vp, i64, vp, vp, vp],
+        "cdmd_mlp_train_step": [vp, vp, vp, vp, ctypes.c_int, flt, flt, flt, flt, vp, vp, i64, vp, vp],
     }
     for name, args in proto.items():
         fn = getattr(lib, name)
@@ -332,3 +344,87 @@ def unpack_mask(mask, m):
     words = np.asarray(mask.cpu().numpy() if hasattr(mask, "cpu") else mask).view(np.uint32)
     bits = np.unpackbits(words.view(np.uint8), axis=1, bitorder="little")
     return bits[:, :m].astype(bool).T
+
+
+# ---------------------------------------------------------------------------
+# learned mode selector
+# ---------------------------------------------------------------------------
+
+
+def cdmd_selector_load(ctx, blob, stream=None):
+    """Load a model blob (float32 device tensor of MLP_BLOB values) for selector='mlp'."""
+    assert blob.dtype.is_floating_point and blob.numel() == MLP_BLOB
+    _check(ctx.lib.cdmd_selector_load(ctx.handle, _ptr(blob), _stream(stream)))
+
+
+def cdmd_selector_features(ctx, lam, sel, r, K, labels=True, stream=None):
+    """Features (r, 4) and OMP labels (r,) of the last decomposition on ctx."""
+    import torch
+    feats = torch.empty((r, MLP_FEATURES), dtype=torch.float32, device=lam.device)
+    lab = torch.empty(r, dtype=torch.float32, device=lam.device) if labels else None
+    _check(ctx.lib.cdmd_selector_features(ctx.handle, _ptr(lam), _ptr(sel), int(r), int(K), _ptr(feats),
+                                          _ptr(lab), _stream(stream)))
+    return feats, lab
+
+
+def cdmd_selector_relabel(ctx, DY, dec, r, y_target, K, stream=None):
+    """OMP picks (K,) on the last decomposition's modes against y_target (k,)."""
+    import torch
+    n, k = DY.shape
+    sel = torch.empty(K, dtype=torch.int32, device=DY.device)
+    _check(ctx.lib.cdmd_selector_relabel(ctx.handle, _ptr(DY), int(k), int(n), _ptr(dec["G"]), _ptr(dec["lam"]),
+                                         int(r), _ptr(y_target), int(K), _ptr(sel), _stream(stream)))
+    return sel
+
+
+def cdmd_selector_fallbacks(ctx, reset=False, stream=None):
+    """Fallbacks to OMP taken by selector='mlp' since the last load/reset."""
+    c = ctypes.c_int64()
+    _check(ctx.lib.cdmd_selector_fallbacks(ctx.handle, ctypes.byref(c), int(bool(reset)), _stream(stream)))
+    return c.value
+
+
+def cdmd_mlp_forward(ctx, blob, X, bf16=True, stream=None):
+    """Logits and probabilities of N feature rows (device tensors)."""
+    import torch
+    N = X.shape[0]
+    s = torch.empty(N, dtype=torch.float32, device=X.device)
+    p = torch.empty(N, dtype=torch.float32, device=X.device)
+    _check(ctx.lib.cdmd_mlp_forward(ctx.handle, _ptr(blob), _ptr(X), int(N), int(bool(bf16)), _ptr(s), _ptr(p),
+                                    _stream(stream)))
+    return s, p
+
+
+def cdmd_mlp_grad(ctx, blob, X, Y, stream=None):
+    """Mean BCE loss and gradient over the rows (device tensors)."""
+    import torch
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(ctx.lib.cdmd_mlp_grad(ctx.handle, _ptr(blob), _ptr(X), _ptr(Y), int(X.shape[0]), _ptr(grad), _ptr(loss),
+                                 _stream(stream)))
+    return loss, grad
+
+
+def cdmd_mlp_train_step(ctx, blob, m, v, step, lr, X, Y, beta1=0.9, beta2=0.999, eps=1e-8, loss=None, stream=None):
+    """One Adam step in place on blob's parameters and the moments m, v."""
+    _check(ctx.lib.cdmd_mlp_train_step(ctx.handle, _ptr(blob), _ptr(m), _ptr(v), int(step), float(lr), float(beta1),
+                                       float(beta2), float(eps), _ptr(X), _ptr(Y), int(X.shape[0]), _ptr(loss),
+                                       _stream(stream)))
+
+
+def cdmd_synth_clip(ctx, spec, seed, D=None, stream=None):
+    """Render a clip described by a scene spec (videogen.clip_spec layout:
+    width, height, n, waves, objects, shape, drift, noise_sigma) on the
+    device; returns (n, width*height) uint8."""
+    import torch
+    W, H, n = spec["width"], spec["height"], spec["n"]
+    dev = torch.device("cuda", ctx.device)
+    if D is None:
+        D = torch.empty((n, W * H), dtype=torch.uint8, device=dev)
+    waves = torch.as_tensor(np.asarray(spec["waves"], dtype=np.float32)).to(dev)
+    objs = torch.as_tensor(np.asarray(spec["objects"], dtype=np.float32)).to(dev)
+    _check(ctx.lib.cdmd_synth_clip(ctx.handle, int(W), int(H), int(n), _ptr(waves), int(waves.shape[0]), _ptr(objs),
+                                   int(objs.shape[1]) if objs.ndim == 3 else 0, int(spec["shape"] == "ellipse"),
+                                   float(spec["drift"]), float(spec["noise_sigma"]), int(seed) & (2**64 - 1),
+                                   _ptr(D), int(D.stride(0)), _stream(stream)))
+    return D

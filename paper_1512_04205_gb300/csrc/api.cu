@@ -252,7 +252,10 @@ cdmd_status cdmd_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r,
     CDMD_REQUIRE(k >= 1, "k must be >= 1");
     CDMD_REQUIRE(r >= 1 && r <= 32 && r <= k && r <= n - 1, "r must be in [1, min(32, k, n-1)] (got %d)", r);
     CDMD_REQUIRE(K >= 1 && K <= r, "K must be in [1, r] (got %d)", K);
-    CDMD_REQUIRE(selector == CDMD_SEL_OMP || selector == CDMD_SEL_LSTSQ, "unknown selector %d", static_cast<int>(selector));
+    CDMD_REQUIRE(selector == CDMD_SEL_OMP || selector == CDMD_SEL_LSTSQ || selector == CDMD_SEL_MLP,
+                 "unknown selector %d", static_cast<int>(selector));
+    CDMD_REQUIRE(selector != CDMD_SEL_MLP || ctx->selector_loaded,
+                 "CDMD_SEL_MLP needs a model (cdmd_selector_load)");
     DeviceGuard g(ctx->device);
     return launch_decompose(ctx, DY, k, n, r, K, selector, sigma, lambda, G, PhiY, beta, sel, nsel,
                             static_cast<cudaStream_t>(stream));
@@ -378,6 +381,115 @@ cdmd_status cdmd_workspace_views(cdmd_ctx* ctx, double** DY, double** sigma, dou
     if (nsel) *nsel = ctx->run_nsel;
     if (Phi) *Phi = ctx->run_Phi;
     return CDMD_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// learned mode selector
+// ---------------------------------------------------------------------------
+
+cdmd_status cdmd_selector_load(cdmd_ctx* ctx, const float* blob, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(blob != nullptr, "blob is NULL");
+    DeviceGuard g(ctx->device);
+    void* buf = nullptr;
+    cdmd_status st = ensure_buffer(ctx, BUF_SELECTOR, kSelBytes, &buf);
+    if (st != CDMD_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CDMD_CHECK_CUDA(cudaMemcpyAsync(buf, blob, CDMD_MLP_BLOB * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CDMD_CHECK_CUDA(cudaMemsetAsync(static_cast<char*>(buf) + kSelOrderOff, 0, kSelBytes - kSelOrderOff, s));
+    ctx->selector_loaded = true;
+    return CDMD_OK;
+}
+
+cdmd_status cdmd_selector_features(cdmd_ctx* ctx, const double* lambda, const int32_t* sel, int r, int K,
+                                   float* feats, float* labels, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(lambda != nullptr && feats != nullptr, "lambda and feats are required");
+    CDMD_REQUIRE(ctx->last_M != nullptr && ctx->last_r == r, "no decomposition with r = %d on this context", r);
+    CDMD_REQUIRE(K >= 0 && K <= r, "K must be in [0, r] (got %d)", K);
+    CDMD_REQUIRE(labels == nullptr || sel != nullptr || K == 0, "labels need sel");
+    DeviceGuard g(ctx->device);
+    return launch_selector_features(ctx, lambda, sel, r, K, feats, labels, static_cast<cudaStream_t>(stream));
+}
+
+cdmd_status cdmd_selector_relabel(cdmd_ctx* ctx, const double* DY, int k, int n, const double* G,
+                                  const double* lambda, int r, const double* y_target, int K, int32_t* sel,
+                                  void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(DY && G && lambda && y_target && sel, "DY, G, lambda, y_target and sel are required");
+    CDMD_REQUIRE(ctx->last_M != nullptr && ctx->last_r == r, "no decomposition with r = %d on this context", r);
+    CDMD_REQUIRE(n >= 2 && n <= 512 && k >= 1, "bad sizes");
+    CDMD_REQUIRE(K >= 1 && K <= r, "K must be in [1, r] (got %d)", K);
+    DeviceGuard g(ctx->device);
+    return launch_selector_relabel(ctx, DY, k, n, G, lambda, r, y_target, K, sel, static_cast<cudaStream_t>(stream));
+}
+
+cdmd_status cdmd_selector_fallbacks(cdmd_ctx* ctx, int64_t* count, int reset, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && count != nullptr, "ctx and count are required");
+    CDMD_REQUIRE(ctx->selector_loaded, "no selector model loaded");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long v = 0;
+    CDMD_CHECK_CUDA(cudaMemcpyAsync(&v, selector_fallbacks(ctx), sizeof(v), cudaMemcpyDeviceToHost, s));
+    if (reset) CDMD_CHECK_CUDA(cudaMemsetAsync(selector_fallbacks(ctx), 0, sizeof(v), s));
+    CDMD_CHECK_CUDA(cudaStreamSynchronize(s));
+    *count = static_cast<int64_t>(v);
+    return CDMD_OK;
+}
+
+cdmd_status cdmd_mlp_forward(cdmd_ctx* ctx, const float* blob, const float* X, int64_t N, int bf16, float* s,
+                             float* p, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(blob != nullptr && (X != nullptr || N == 0), "blob and X are required");
+    CDMD_REQUIRE(N >= 0, "N must be >= 0");
+    DeviceGuard g(ctx->device);
+    return launch_mlp_forward(ctx, blob, X, N, bf16, s, p, static_cast<cudaStream_t>(stream));
+}
+
+cdmd_status cdmd_mlp_grad(cdmd_ctx* ctx, const float* blob, const float* X, const float* Y, int64_t N, float* grad,
+                          float* loss, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(blob && X && Y && grad, "blob, X, Y and grad are required");
+    CDMD_REQUIRE(N >= 1, "N must be >= 1");
+    DeviceGuard g(ctx->device);
+    return launch_mlp_train(ctx, 0, const_cast<float*>(blob), nullptr, nullptr, 1, 0.0f, 0.0f, 0.0f, 0.0f, X, Y, N,
+                            grad, loss, static_cast<cudaStream_t>(stream));
+}
+
+cdmd_status cdmd_mlp_train_step(cdmd_ctx* ctx, float* blob, float* m, float* v, int step, float lr, float beta1,
+                                float beta2, float eps, const float* X, const float* Y, int64_t N, float* loss,
+                                void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(blob && m && v && X && Y, "blob, m, v, X and Y are required");
+    CDMD_REQUIRE(N >= 1 && step >= 1, "N and step must be >= 1");
+    CDMD_REQUIRE(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f,
+                 "Adam needs 0 <= beta1, beta2 < 1 and eps > 0");
+    DeviceGuard g(ctx->device);
+    return launch_mlp_train(ctx, 1, blob, m, v, step, lr, beta1, beta2, eps, X, Y, N, nullptr, loss,
+                            static_cast<cudaStream_t>(stream));
+}
+
+cdmd_status cdmd_synth_clip(cdmd_ctx* ctx, int width, int height, int n, const float* waves, int nw,
+                            const float* objects, int nobj, int ellipse, float drift, float noise_sigma,
+                            uint64_t seed, uint8_t* D, int64_t ldd, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && D != nullptr, "ctx and D are required");
+    CDMD_REQUIRE(width >= 1 && height >= 1 && n >= 1, "width, height and n must be >= 1");
+    CDMD_REQUIRE(n <= 65535, "n must be <= 65535");
+    CDMD_REQUIRE(ldd >= static_cast<int64_t>(width) * height, "ldd must be >= width * height");
+    CDMD_REQUIRE(nw >= 0 && (nw == 0 || waves != nullptr), "waves missing");
+    CDMD_REQUIRE(nobj >= 0 && (nobj == 0 || objects != nullptr), "objects missing");
+    DeviceGuard g(ctx->device);
+    return launch_synth_clip(width, height, n, waves, nw, objects, nobj, ellipse, drift, noise_sigma, seed, D, ldd,
+                             static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

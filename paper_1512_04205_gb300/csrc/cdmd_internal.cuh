@@ -139,6 +139,9 @@ enum BufferId {
     BUF_RUN_VIDEO,            // cdmd_run_host device copy of the video
     BUF_RUN_MASK,
     BUF_SUBTRACT_TABLE,       // lambda^t table and amplitudes for pass (c)
+    BUF_SELECTOR,             // selector model blob, pick order, accept flag, fallback count
+    BUF_MLP_PARTS,            // selector training: per-warp partial gradients
+    BUF_RELABEL,              // selector training: OMP against a second target
     BUF_COUNT
 };
 
@@ -150,6 +153,12 @@ struct cdmd_ctx {
     int num_sms = 0;       // SMs the full-data passes size their grids for (cdmd_set_sm_limit)
     int* d_status = nullptr;
     cdmd::Buffer buf[cdmd::BUF_COUNT];
+    bool selector_loaded = false;
+    // Gram quantities of the last cdmd_decompose (decompose workspace)
+    const double* last_M = nullptr;
+    const double* last_cvec = nullptr;
+    const double* last_R = nullptr;
+    int last_r = 0;
     // views of the last cdmd_run
     double* run_DY = nullptr;
     double* run_sigma = nullptr;
@@ -162,6 +171,23 @@ struct cdmd_ctx {
 };
 
 namespace cdmd {
+
+// Selector buffer: model blob (FP32, 2 KB slot), pick order (32 int32),
+// accept flag (int), fallback count (uint64).
+constexpr size_t kSelOrderOff = 2048;
+constexpr size_t kSelAcceptOff = 2176;
+constexpr size_t kSelFallbackOff = 2184;
+constexpr size_t kSelBytes = 2304;
+inline float* selector_blob(cdmd_ctx* ctx) { return static_cast<float*>(ctx->buf[BUF_SELECTOR].ptr); }
+inline int32_t* selector_order(cdmd_ctx* ctx) {
+    return reinterpret_cast<int32_t*>(static_cast<char*>(ctx->buf[BUF_SELECTOR].ptr) + kSelOrderOff);
+}
+inline int* selector_accept(cdmd_ctx* ctx) {
+    return reinterpret_cast<int*>(static_cast<char*>(ctx->buf[BUF_SELECTOR].ptr) + kSelAcceptOff);
+}
+inline unsigned long long* selector_fallbacks(cdmd_ctx* ctx) {
+    return reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->buf[BUF_SELECTOR].ptr) + kSelFallbackOff);
+}
 
 // Grow-only workspace buffer (never shrinks; synchronises the device before
 // freeing an older, smaller allocation).
@@ -193,5 +219,20 @@ cdmd_status launch_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, i
                             const float* Phi, int ncols, const int32_t* cols, const double* beta,
                             const double* lambda, int r, float tau, cdmd_bgmode mode,
                             uint32_t* mask, float* bg, cudaStream_t stream);
+cdmd_status launch_synth_clip(int width, int height, int n, const float* waves, int nw, const float* objects,
+                              int nobj, int ellipse, float drift, float noise_sigma, uint64_t seed, uint8_t* D,
+                              int64_t ldd, cudaStream_t stream);
+cdmd_status launch_selector_features(cdmd_ctx* ctx, const double* lambda, const int32_t* sel, int r, int K,
+                                     float* feats, float* labels, cudaStream_t stream);
+cdmd_status launch_selector_relabel(cdmd_ctx* ctx, const double* DY, int k, int n, const double* G,
+                                    const double* lambda, int r, const double* y_target, int K, int32_t* sel,
+                                    cudaStream_t stream);
+cdmd_status launch_mlp_select(cdmd_ctx* ctx, const double* lambda, const double* M, const double* cvec,
+                              const double* R, int r, int K, cudaStream_t stream);
+cdmd_status launch_mlp_forward(cdmd_ctx* ctx, const float* blob, const float* X, int64_t N, int bf16,
+                               float* s, float* p, cudaStream_t stream);
+cdmd_status launch_mlp_train(cdmd_ctx* ctx, int apply, float* blob, float* m, float* v, int step, float lr,
+                             float beta1, float beta2, float eps, const float* X, const float* Y, int64_t N,
+                             float* grad, float* loss, cudaStream_t stream);
 
 }  // namespace cdmd

@@ -642,7 +642,7 @@ __device__ __forceinline__ cf fsqrtc(cf a) {
 
 __global__ void __launch_bounds__(32)
 eig_f32_kernel(const double* __restrict__ At, int r, float2* __restrict__ lam32, float2* __restrict__ W32,
-               int* status) {
+               int* fallback) {
     __shared__ float Hr[kMaxR][kMaxR + 1];
     __shared__ float Q[kMaxR][kMaxR + 1];
     __shared__ cf T[kMaxR][kMaxR + 1];
@@ -774,7 +774,8 @@ eig_f32_kernel(const double* __restrict__ At, int r, float2* __restrict__ lam32,
             __syncwarp();
         }
     }
-    if (failed && lane == 0) record_status(status, CDMD_ERR_NOT_CONVERGED);
+    // a failed FP32 iteration hands the whole problem to the FP64 QR fallback
+    if (lane == 0) *fallback = failed ? 1 : 0;
     __syncwarp();
     float tmax = 0.0f;
     for (int i = 0; i < r; ++i)
@@ -815,7 +816,7 @@ eig_f32_kernel(const double* __restrict__ At, int r, float2* __restrict__ lam32,
 
 __global__ void __launch_bounds__(32)
 eig_refine_kernel(const double* __restrict__ At, int r, const float2* __restrict__ lam32,
-                  const float2* __restrict__ W32, double* __restrict__ lamR, double* __restrict__ WR, int* status) {
+                  const float2* __restrict__ W32, double* __restrict__ lamR, double* __restrict__ WR, int* fallback) {
     __shared__ double A[kMaxR][kMaxR + 1];
     __shared__ cd Mx[kMaxR][kMaxR + 1];
     __shared__ cd wv[kMaxR];
@@ -909,7 +910,9 @@ eig_refine_kernel(const double* __restrict__ At, int r, const float2* __restrict
         done = (cabs2(dmu) <= 1e-28 * cabs2(mu)) && (dw <= 1e-26) && it > 0;
         __syncwarp();
     }
-    if (!done && lane == 0) record_status(status, CDMD_ERR_NOT_CONVERGED);
+    // no quadratic convergence (a cluster or a nearly defective pair): the
+    // FP64 QR fallback recomputes every eigenpair
+    if (!done && lane == 0) atomicExch(fallback, 1);
     if (lane == 0) {
         lamR[2 * j] = mu.x;
         lamR[2 * j + 1] = mu.y;
@@ -918,6 +921,235 @@ eig_refine_kernel(const double* __restrict__ At, int r, const float2* __restrict
         WR[2 * (static_cast<int64_t>(j) * r + lane)] = wv[lane].x;
         WR[2 * (static_cast<int64_t>(j) * r + lane) + 1] = wv[lane].y;
     }
+}
+
+// FP64 fallback of steps 6b/6c for the rare A~ on which the FP32 solve or
+// the Newton refinement did not converge (clustered or nearly defective
+// eigenvalues, e.g. a conjugate pair about to meet on the real axis), or whose
+// refined eigenvalues coincide.  One CTA: Householder Hessenberg reduction,
+// complex single-shift QR with Wilkinson shifts (exceptional shift every 11
+// iterations) to a complex Schur form T = Z^H H Z, eigenvectors of T by
+// back-substitution, W = Q Z X.  Returns at once when nothing was flagged.
+__device__ __forceinline__ double cabsd(cd a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ cd cdiv(cd a, cd b) {
+    const double sc = fabs(b.x) + fabs(b.y);
+    const cd as = {a.x / sc, a.y / sc}, bs = {b.x / sc, b.y / sc};
+    const double den = bs.x * bs.x + bs.y * bs.y;
+    return {(as.x * bs.x + as.y * bs.y) / den, (as.y * bs.x - as.x * bs.y) / den};
+}
+__device__ __forceinline__ cd csqrt_(cd a) {
+    const double m = cabsd(a);
+    if (m == 0.0) return {0.0, 0.0};
+    double re = sqrt(0.5 * (m + fabs(a.x)));
+    double im = 0.5 * a.y / re;
+    if (a.x < 0.0) {
+        const double t = re;
+        re = fabs(im);
+        im = (a.y >= 0.0) ? t : -t;
+    }
+    return {re, im};
+}
+
+constexpr int kQrThreads = 64;
+constexpr size_t kQrSmem = 2 * kMaxR * (kMaxR + 1) * sizeof(double) + 3 * kMaxR * (kMaxR + 1) * sizeof(cd);
+
+__global__ void __launch_bounds__(kQrThreads)
+eig_qr64_kernel(const double* __restrict__ At, int r, double* lamR, double* WR, int* fallback, int* status) {
+    extern __shared__ double qsm[];
+    typedef double RowD[kMaxR + 1];
+    typedef cd RowC[kMaxR + 1];
+    RowD* Hr = reinterpret_cast<RowD*>(qsm);
+    RowD* Q = Hr + kMaxR;
+    RowC* T = reinterpret_cast<RowC*>(Q + kMaxR);
+    RowC* Zs = T + kMaxR;
+    RowC* X = Zs + kMaxR;
+    __shared__ double hv[kMaxR];
+    __shared__ double scal[4];
+    __shared__ cd rot[2];
+    __shared__ int flag[2];
+    const int tid = threadIdx.x;
+    const int nt = blockDim.x;
+    if (tid == 0) {
+        int go = *fallback;
+        for (int i = 0; i < r && !go; ++i)
+            for (int q = i + 1; q < r && !go; ++q) {
+                const cd li = {lamR[2 * i], lamR[2 * i + 1]}, lq = {lamR[2 * q], lamR[2 * q + 1]};
+                const double tol = 1e-8 * fmax(1.0, cabsd(li));
+                if (!(cabs2(csub(li, lq)) > tol * tol)) go = 1;   // coincident (or NaN) eigenvalues
+            }
+        flag[1] = go;
+    }
+    __syncthreads();
+    if (!flag[1]) return;
+    for (int idx = tid; idx < r * r; idx += nt) {
+        const int i = idx % r, c = idx / r;
+        Hr[i][c] = At[static_cast<int64_t>(c) * r + i];
+        Q[i][c] = (i == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j + 2 < r; ++j) {
+        if (tid == 0) {
+            double nrm2 = 0.0;
+            for (int i = j + 1; i < r; ++i) nrm2 += Hr[i][j] * Hr[i][j];
+            const double nrm = sqrt(nrm2);
+            if (nrm == 0.0) {
+                scal[0] = 0.0;
+            } else {
+                for (int i = j + 1; i < r; ++i) hv[i] = Hr[i][j];
+                hv[j + 1] += (Hr[j + 1][j] >= 0.0 ? nrm : -nrm);
+                double vn = 0.0;
+                for (int i = j + 1; i < r; ++i) vn += hv[i] * hv[i];
+                scal[0] = vn > 0.0 ? 2.0 / vn : 0.0;
+            }
+        }
+        __syncthreads();
+        const double beta = scal[0];
+        if (beta != 0.0) {
+            for (int c = tid; c < r; c += nt) {
+                double sacc = 0.0;
+                for (int i = j + 1; i < r; ++i) sacc += hv[i] * Hr[i][c];
+                sacc *= beta;
+                for (int i = j + 1; i < r; ++i) Hr[i][c] -= sacc * hv[i];
+            }
+            __syncthreads();
+            for (int i = tid; i < r; i += nt) {
+                double sh = 0.0, sq = 0.0;
+                for (int c = j + 1; c < r; ++c) {
+                    sh += Hr[i][c] * hv[c];
+                    sq += Q[i][c] * hv[c];
+                }
+                sh *= beta;
+                sq *= beta;
+                for (int c = j + 1; c < r; ++c) {
+                    Hr[i][c] -= sh * hv[c];
+                    Q[i][c] -= sq * hv[c];
+                }
+            }
+            __syncthreads();
+            for (int i = j + 2 + tid; i < r; i += nt) Hr[i][j] = 0.0;
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < r * r; idx += nt) {
+        const int i = idx % r, c = idx / r;
+        T[i][c] = {Hr[i][c], 0.0};
+        Zs[i][c] = {(i == c) ? 1.0 : 0.0, 0.0};
+    }
+    __syncthreads();
+    int hi = r - 1, its = 0, total = 0;
+    bool failed = false;
+    while (hi > 0) {
+        if (tid == 0) {
+            int lo = hi;
+            while (lo > 0) {
+                const double sc = cabsd(T[lo - 1][lo - 1]) + cabsd(T[lo][lo]);
+                if (cabsd(T[lo][lo - 1]) <= kEps * sc) { T[lo][lo - 1] = {0.0, 0.0}; break; }
+                --lo;
+            }
+            flag[0] = lo;
+        }
+        __syncthreads();
+        const int lo = flag[0];
+        if (lo == hi) { --hi; its = 0; __syncthreads(); continue; }
+        ++its;
+        ++total;
+        if (its > 60 || total > 60 * r) { failed = true; break; }
+        if (tid == 0) {
+            const cd a = T[hi - 1][hi - 1], b = T[hi - 1][hi], c = T[hi][hi - 1], d = T[hi][hi];
+            cd mu;
+            if (its % 11 == 0) {
+                mu = {d.x + cabsd(c), d.y};
+            } else {
+                const cd half = {0.5 * (a.x - d.x), 0.5 * (a.y - d.y)};
+                const cd bc = cmul(b, c);
+                const cd disc = csqrt_(cadd(cmul(half, half), bc));
+                const cd s1 = cadd(half, disc), s2 = csub(half, disc);
+                cd mu1 = d, mu2 = d;
+                if (cabs2(s1) > 0.0) mu1 = csub(d, cdiv(bc, s1));
+                if (cabs2(s2) > 0.0) mu2 = csub(d, cdiv(bc, s2));
+                mu = (cabs2(csub(mu1, d)) <= cabs2(csub(mu2, d))) ? mu1 : mu2;
+            }
+            rot[1] = mu;
+        }
+        __syncthreads();
+        const cd mu = rot[1];
+        for (int q = lo; q < hi; ++q) {
+            if (tid == 0) {
+                cd x, y;
+                if (q == lo) { x = csub(T[lo][lo], mu); y = T[lo + 1][lo]; }
+                else { x = T[q][q - 1]; y = T[q + 1][q - 1]; }
+                const double rr = sqrt(cabs2(x) + cabs2(y));
+                if (rr == 0.0) { rot[0] = {1.0, 0.0}; scal[1] = 0.0; scal[2] = 0.0; }
+                else { rot[0] = {x.x / rr, x.y / rr}; scal[1] = y.x / rr; scal[2] = y.y / rr; }
+            }
+            __syncthreads();
+            const cd cg_ = rot[0];
+            const cd sg = {scal[1], scal[2]};
+            const int col0 = max(q - 1, 0);
+            for (int c = col0 + tid; c < r; c += nt) {
+                const cd t0 = T[q][c], t1 = T[q + 1][c];
+                T[q][c] = cadd(cmul(cconj(cg_), t0), cmul(cconj(sg), t1));
+                T[q + 1][c] = csub(cmul(cg_, t1), cmul(sg, t0));
+            }
+            __syncthreads();
+            const int row1 = min(q + 3, hi + 1);
+            for (int i = tid; i < r; i += nt) {
+                if (i < row1) {
+                    const cd t0 = T[i][q], t1 = T[i][q + 1];
+                    T[i][q] = cadd(cmul(t0, cg_), cmul(t1, sg));
+                    T[i][q + 1] = csub(cmul(t1, cconj(cg_)), cmul(t0, cconj(sg)));
+                }
+                const cd z0 = Zs[i][q], z1 = Zs[i][q + 1];
+                Zs[i][q] = cadd(cmul(z0, cg_), cmul(z1, sg));
+                Zs[i][q + 1] = csub(cmul(z1, cconj(cg_)), cmul(z0, cconj(sg)));
+            }
+            __syncthreads();
+            if (tid == 0 && q > lo) T[q + 1][q - 1] = {0.0, 0.0};
+            __syncthreads();
+        }
+    }
+    if (failed && tid == 0) record_status(status, CDMD_ERR_NOT_CONVERGED);
+    if (tid == 0) {
+        double tmax = 0.0;
+        for (int i = 0; i < r; ++i)
+            for (int c = i; c < r; ++c) tmax = fmax(tmax, cabsd(T[i][c]));
+        scal[3] = kEps * fmax(tmax, 1e-300);
+    }
+    __syncthreads();
+    const double small = scal[3];
+    for (int j = tid; j < r; j += nt) {
+        for (int i = 0; i < r; ++i) X[i][j] = {i == j ? 1.0 : 0.0, 0.0};
+        for (int i = j - 1; i >= 0; --i) {
+            cd acc = {0.0, 0.0};
+            for (int q = i + 1; q <= j; ++q) acc = cadd(acc, cmul(T[i][q], X[q][j]));
+            cd den = csub(T[i][i], T[j][j]);
+            if (cabsd(den) < small) den = {small, 0.0};
+            const cd v = cdiv(acc, den);
+            X[i][j] = {-v.x, -v.y};
+        }
+        lamR[2 * j] = T[j][j].x;
+        lamR[2 * j + 1] = T[j][j].y;
+    }
+    __syncthreads();
+    // W = Q (Z X); column j by one thread (X upper triangular)
+    for (int j = tid; j < r; j += nt) {
+        cd zx[kMaxR];
+        for (int q = 0; q < r; ++q) {
+            cd acc = {0.0, 0.0};
+            for (int u = 0; u <= j; ++u) acc = cadd(acc, cmul(Zs[q][u], X[u][j]));
+            zx[q] = acc;
+        }
+        for (int i = 0; i < r; ++i) {
+            double re = 0.0, im = 0.0;
+            for (int q = 0; q < r; ++q) {
+                re += Q[i][q] * zx[q].x;
+                im += Q[i][q] * zx[q].y;
+            }
+            WR[2 * (static_cast<int64_t>(j) * r + i)] = re;
+            WR[2 * (static_cast<int64_t>(j) * r + i) + 1] = im;
+        }
+    }
+    if (tid == 0) *fallback = 0;
 }
 
 __global__ void __launch_bounds__(32)
@@ -1084,7 +1316,19 @@ hmat_kernel(const double* __restrict__ R, const double* __restrict__ G, int n, i
 __global__ void __launch_bounds__(32)
 omp_kernel(const double* __restrict__ M, const double* __restrict__ cvec, const double* __restrict__ R,
            const double* __restrict__ lam, int r, int K, int lstsq, double* __restrict__ beta,
-           int32_t* __restrict__ sel, int32_t* __restrict__ nsel_out, int* status) {
+           int32_t* __restrict__ sel, int32_t* __restrict__ nsel_out, int* status,
+           const int32_t* __restrict__ order, const float* __restrict__ blob, int* accept,
+           unsigned long long* fallbacks) {
+    // Modes of operation:
+    //   order == nullptr, accept == nullptr   greedy OMP (or lstsq over all r)
+    //   order != nullptr                      least squares on the learned pick
+    //                                         order; accepted (outputs written,
+    //                                         *accept = 1) when the relative
+    //                                         residual is within the model's tol,
+    //                                         else *accept = 0 and one fallback
+    //                                         is counted
+    //   order == nullptr, accept != nullptr   greedy OMP unless *accept == 1
+    if (order == nullptr && accept != nullptr && *accept == 1) return;
     __shared__ cd L[kMaxR][kMaxR + 1];   // L[u][q], u >= q
     __shared__ double invdiag[kMaxR];
     __shared__ cd bsel[kMaxR];
@@ -1104,9 +1348,12 @@ omp_kernel(const double* __restrict__ M, const double* __restrict__ cvec, const 
     int ns = 0;
     double res2 = y2;
     for (int step = 0; step < kmax_steps; ++step) {
-        if (!lstsq && res2 <= 1e-24 * y2) break;
+        if (!lstsq && order == nullptr && res2 <= 1e-24 * y2) break;
         int best;
-        if (lstsq) {
+        if (order != nullptr) {
+            best = order[step];
+            if (best < 0 || best >= r) break;
+        } else if (lstsq) {
             best = step;
         } else {
             double score = -1.0;
@@ -1170,6 +1417,15 @@ omp_kernel(const double* __restrict__ M, const double* __restrict__ cvec, const 
         }
         res2 = y2 - warp_sum(cb);
     }
+    if (order != nullptr) {
+        const double tol = static_cast<double>(blob[8]);
+        const bool ok = tol >= 0.0 && res2 <= tol * tol * y2;   // a negative tol rejects every pick
+        if (lane == 0) {
+            *accept = ok ? 1 : 0;
+            if (!ok) atomicAdd(fallbacks, 1ull);
+        }
+        if (!ok) return;
+    }
     if (live) {
         beta[2 * lane] = 0.0;
         beta[2 * lane + 1] = 0.0;
@@ -1199,7 +1455,68 @@ __global__ void phiy_kernel(const double* __restrict__ DY, const double* __restr
     PhiY[2 * idx + 1] = im;
 }
 
+// OMP against another target y_t (k values) on the same decomposition:
+// cvec_t[c] = G[:,c]^H (Y'^T y_t), y2_t = ||y_t||^2.
+__global__ void __launch_bounds__(256)
+relabel_target_kernel(const double* __restrict__ DY, int k, int p, const double* __restrict__ G, int r,
+                      const double* __restrict__ yt, double* __restrict__ u, double* __restrict__ cvec_t,
+                      double* __restrict__ y2_t) {
+    // one CTA: first u = Y'^T y_t (warp per frame), then cvec_t, then ||y_t||^2
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = wid; t < p; t += nw) {
+        const double* col = DY + static_cast<int64_t>(t + 1) * k;
+        double acc = 0.0;
+        for (int i = lane; i < k; i += 32) acc = fma(col[i], yt[i], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) u[t] = acc;
+    }
+    __syncthreads();
+    for (int c = wid; c <= r; c += nw) {
+        double re = 0.0, im = 0.0;
+        if (c < r) {
+            const double* gc = G + 2 * static_cast<int64_t>(c) * p;
+            for (int t = lane; t < p; t += 32) {
+                re = fma(gc[2 * t], u[t], re);
+                im = fma(-gc[2 * t + 1], u[t], im);
+            }
+        } else {
+            for (int i = lane; i < k; i += 32) re = fma(yt[i], yt[i], re);
+        }
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (lane == 0) {
+            if (c < r) {
+                cvec_t[2 * c] = re;
+                cvec_t[2 * c + 1] = im;
+            } else {
+                *y2_t = re;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+cdmd_status launch_selector_relabel(cdmd_ctx* ctx, const double* DY, int k, int n, const double* G,
+                                    const double* lambda, int r, const double* y_target, int K, int32_t* sel,
+                                    cudaStream_t stream) {
+    const int p = n - 1;
+    void* buf = nullptr;
+    const size_t doubles = static_cast<size_t>(p) + 4 * r + 8;
+    cdmd_status st = ensure_buffer(ctx, BUF_RELABEL, doubles * sizeof(double) + 64, &buf);
+    if (st != CDMD_OK) return st;
+    double* u = static_cast<double*>(buf);
+    double* cvec_t = u + p;
+    double* beta_t = cvec_t + 2 * r;
+    double* y2_t = beta_t + 2 * r;
+    int32_t* nsel_t = reinterpret_cast<int32_t*>(y2_t + 1);
+    relabel_target_kernel<<<1, 256, 0, stream>>>(DY, k, p, G, r, y_target, u, cvec_t, y2_t);
+    CDMD_CHECK_LAUNCH("relabel_target_kernel");
+    omp_kernel<<<1, 32, 0, stream>>>(ctx->last_M, cvec_t, y2_t, lambda, r, K, 0, beta_t, sel, nsel_t,
+                                     ctx->d_status, nullptr, nullptr, nullptr, nullptr);
+    CDMD_CHECK_LAUNCH("omp_kernel");
+    return CDMD_OK;
+}
 
 cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r, int K,
                              cdmd_selector selector, double* sigma, double* lambda, double* G,
@@ -1217,9 +1534,11 @@ cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int 
     const size_t n_Z = static_cast<size_t>(p) * r;
     const size_t n_small = static_cast<size_t>(r) * r * 2;
     const size_t total = n_gram_part + n_R + n_Hv + 3 * n_vec + r + 3 * n_Z + 5 * n_small + 6 * r + 64;
+    // + one slot for the eigen-solver's fallback flag
     double* ws = nullptr;
-    cdmd_status st = ensure_buffer(ctx, BUF_EIG, total * sizeof(double), reinterpret_cast<void**>(&ws));
+    cdmd_status st = ensure_buffer(ctx, BUF_EIG, (total + 1) * sizeof(double), reinterpret_cast<void**>(&ws));
     if (st != CDMD_OK) return st;
+    int* eig_flag = reinterpret_cast<int*>(ws + total);   // written by eig_f32_kernel before any read
     double* gpart = ws;
     double* R = gpart + n_gram_part;
     double* Hv = R + n_R;
@@ -1300,11 +1619,15 @@ cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int 
     atilde_kernel<<<r, 32, 0, stream>>>(V, B, sigma, p, r, At);
     CDMD_CHECK_LAUNCH("atilde_kernel");
     eig_f32_kernel<<<1, 32, 0, stream>>>(At, r, reinterpret_cast<float2*>(lam32), reinterpret_cast<float2*>(W32),
-                                         ctx->d_status);
+                                         eig_flag);
     CDMD_CHECK_LAUNCH("eig_f32_kernel");
     eig_refine_kernel<<<r, 32, 0, stream>>>(At, r, reinterpret_cast<const float2*>(lam32),
-                                            reinterpret_cast<const float2*>(W32), lamR, WR, ctx->d_status);
+                                            reinterpret_cast<const float2*>(W32), lamR, WR, eig_flag);
     CDMD_CHECK_LAUNCH("eig_refine_kernel");
+    CDMD_CHECK_CUDA(cudaFuncSetAttribute(eig_qr64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kQrSmem)));
+    eig_qr64_kernel<<<1, kQrThreads, kQrSmem, stream>>>(At, r, lamR, WR, eig_flag, ctx->d_status);
+    CDMD_CHECK_LAUNCH("eig_qr64_kernel");
     eig_order_kernel<<<1, 32, 0, stream>>>(lamR, WR, r, lambda, W);
     CDMD_CHECK_LAUNCH("eig_order_kernel");
     // 5. G, Gram-form quantities, selection
@@ -1312,8 +1635,24 @@ cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int 
     CDMD_CHECK_LAUNCH("gmat_kernel");
     hmat_kernel<<<r, 128, 2 * p * sizeof(double), stream>>>(R, G, n, p, r, M, cvec);
     CDMD_CHECK_LAUNCH("hmat_kernel");
-    omp_kernel<<<1, 32, 0, stream>>>(M, cvec, R, lambda, r, K, selector == CDMD_SEL_LSTSQ ? 1 : 0, beta, sel,
-                                     nsel, ctx->d_status);
+    ctx->last_M = M;
+    ctx->last_cvec = cvec;
+    ctx->last_R = R;
+    ctx->last_r = r;
+    if (selector == CDMD_SEL_MLP) {
+        // learned pick order -> least squares on it -> OMP only if rejected
+        st = launch_mlp_select(ctx, lambda, M, cvec, R, r, K, stream);
+        if (st != CDMD_OK) return st;
+        omp_kernel<<<1, 32, 0, stream>>>(M, cvec, R, lambda, r, K, 0, beta, sel, nsel, ctx->d_status,
+                                         selector_order(ctx), selector_blob(ctx), selector_accept(ctx),
+                                         selector_fallbacks(ctx));
+        CDMD_CHECK_LAUNCH("omp_kernel");
+        omp_kernel<<<1, 32, 0, stream>>>(M, cvec, R, lambda, r, K, 0, beta, sel, nsel, ctx->d_status, nullptr,
+                                         nullptr, selector_accept(ctx), nullptr);
+    } else {
+        omp_kernel<<<1, 32, 0, stream>>>(M, cvec, R, lambda, r, K, selector == CDMD_SEL_LSTSQ ? 1 : 0, beta, sel,
+                                         nsel, ctx->d_status, nullptr, nullptr, nullptr, nullptr);
+    }
     CDMD_CHECK_LAUNCH("omp_kernel");
     if (PhiY != nullptr) {
         const int64_t tot = static_cast<int64_t>(k) * r;

@@ -189,3 +189,23 @@ def test_two_clips_in_flight_match_solo_runs(C, prec):
     lam_full = torch.view_as_complex(lam_full).cpu().numpy()
     lam_cap = torch.view_as_complex(solo[0][1]).cpu().numpy()
     assert np.max(np.abs(lam_full - lam_cap) / np.abs(lam_cap)) < 1e-5
+
+
+@pytest.mark.parametrize("seed,r", [(1009227, 10), (1015594, 10), (1016388, 23)])
+def test_near_defective_eigenvalues_match_oracle(C, ctx, seed, r):
+    # Clips whose A~ has a conjugate pair about to meet on the real axis (or
+    # two nearly equal real eigenvalues): the FP32 solve + Newton refinement
+    # does not converge there and the FP64 QR fallback takes over.
+    from paper_1512_04205_gb300 import selector as SEL
+    spec, r_draw, cseed = SEL.clip_setup(seed, **SEL.TRAIN)
+    assert r_draw == r
+    D = C.cdmd_synth_clip(ctx, spec, seed)
+    k = min(1000, 4 * spec["n"])
+    DY = C.cdmd_sketch(ctx, D, k, cseed)
+    dec = C.cdmd_decompose(ctx, DY, r, 10)
+    C.cdmd_status_sync(ctx)
+    lam = torch.view_as_complex(dec["lam"]).cpu().numpy()
+    ref = O.decompose(DY.cpu().numpy().T, r, 10)
+    idx = [int(np.argmin(np.abs(lam - x))) for x in ref["lam"]]
+    assert len(set(idx)) == r
+    assert np.max(np.abs(lam[idx] - ref["lam"]) / np.abs(ref["lam"])) < 1e-7

@@ -26,7 +26,7 @@ the transpose of the paper's m x n video matrix.
 """
 import numpy as np
 
-__all__ = ["make_clip", "Clip", "CONFIGS"]
+__all__ = ["make_clip", "clip_spec", "Clip", "CONFIGS"]
 
 
 class Clip:
@@ -53,14 +53,22 @@ class Clip:
         return self.frames.T.astype(np.float64)
 
 
-def _background(rng, W, H, n_sinusoids):
-    y, x = np.mgrid[0:H, 0:W].astype(np.float32)
-    bg = np.full((H, W), 128.0, dtype=np.float32)
+def _wave_params(rng, W, n_sinusoids):
+    """(amplitude, period, orientation, phase) of each background plane wave."""
+    waves = []
     for _ in range(n_sinusoids):
         amp = rng.uniform(5.0, 25.0)
         period = rng.uniform(8.0, max(8.0, W / 2.0))
         theta = rng.uniform(0.0, np.pi)
         phase = rng.uniform(0.0, 2.0 * np.pi)
+        waves.append((amp, period, theta, phase))
+    return np.array(waves, dtype=np.float64).reshape(-1, 4)
+
+
+def _render_background(waves, W, H):
+    y, x = np.mgrid[0:H, 0:W].astype(np.float32)
+    bg = np.full((H, W), 128.0, dtype=np.float32)
+    for amp, period, theta, phase in waves:
         arg = (x * np.cos(theta) + y * np.sin(theta)) * (2.0 * np.pi / period) + phase
         bg += np.float32(amp) * np.sin(arg).astype(np.float32)
     return bg
@@ -116,23 +124,49 @@ def _cover(obj, W, H, shape):
     return inside, (y0, y1, x0, x1)
 
 
+def _trajectories(objs, n, W, H):
+    """Object states (cx, cy, w, h, intensity) at frames 0..n-1 (n x objects x 5)."""
+    objs = [list(o) for o in objs]
+    out = np.zeros((n, len(objs), 5))
+    for t in range(n):
+        for q, obj in enumerate(objs):
+            out[t, q] = obj[:5]
+            _step(obj, W, H)
+    return out
+
+
+def clip_spec(width, height, n, seed, n_sinusoids=6, n_objects=3, shape="rectangle", drift=0.0,
+              noise_sigma=3.0):
+    """The scene parameters make_clip draws for `seed`: plane waves
+    (n_sinusoids x [amplitude, period, orientation, phase]) and object states
+    per frame (n x n_objects x [cx, cy, w, h, intensity]).  A renderer that
+    draws its own noise can rebuild the clip's scene from them."""
+    rng = np.random.default_rng(seed)
+    W, H = int(width), int(height)
+    waves = _wave_params(rng, W, n_sinusoids)
+    objs = _objects(rng, W, H, n_objects)
+    return dict(width=W, height=H, n=int(n), waves=waves, objects=_trajectories(objs, n, W, H), shape=shape,
+                drift=float(drift), noise_sigma=float(noise_sigma))
+
+
 def make_clip(width, height, n, seed, n_sinusoids=6, n_objects=3,
               shape="rectangle", drift=0.0, noise_sigma=3.0):
     """Generate one clip; see the module docstring for the recipe."""
     rng = np.random.default_rng(seed)
     W, H = int(width), int(height)
-    bg = _background(rng, W, H, n_sinusoids)
+    waves = _wave_params(rng, W, n_sinusoids)
+    bg = _render_background(waves, W, H)
     objs = _objects(rng, W, H, n_objects)
+    states = _trajectories(objs, n, W, H)
     frames = np.empty((n, H * W), dtype=np.uint8)
     truth = np.zeros((n, H * W), dtype=bool)
     for t in range(n):
         scene = bg.copy()
         tmask = np.zeros((H, W), dtype=bool)
-        for obj in objs:
-            inside, (y0, y1, x0, x1) = _cover(obj, W, H, shape)
-            scene[y0:y1, x0:x1][inside] = obj[4]
+        for state in states[t]:
+            inside, (y0, y1, x0, x1) = _cover(state, W, H, shape)
+            scene[y0:y1, x0:x1][inside] = state[4]
             tmask[y0:y1, x0:x1] |= inside
-            _step(obj, W, H)
         if drift != 0.0 and n > 1:
             scene *= np.float32(1.0 + drift * (2.0 * t / (n - 1) - 1.0))
         if noise_sigma > 0.0:
