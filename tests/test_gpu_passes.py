@@ -331,3 +331,65 @@ def test_lift_bf16x2(C, ctx, w, h, n, r, modes):
         else:
             err = np.linalg.norm(Phi[:, q] - ref[:, s]) / np.linalg.norm(ref[:, s])
             assert err <= 5e-5, (q, s, err)
+
+
+def _conjugate_structured_modes(m, seed):
+    # real eigenvalues with real modes and amplitudes, conjugate pairs with
+    # conjugate modes and amplitudes, and one complex mode without partner
+    rng = np.random.default_rng(seed)
+    th = [0.3, 0.7, 1.1]
+    lam = np.array([0.99, 0.95 * np.exp(1j * th[0]), 0.95 * np.exp(-1j * th[0]), 0.9 * np.exp(1j * th[1]),
+                    0.9 * np.exp(-1j * th[1]), 0.8 * np.exp(1j * th[2]), 0.7])
+    Phi = np.zeros((m, 7), dtype=complex)
+    beta = np.zeros(7, dtype=complex)
+    Phi[:, 0] = rng.normal(size=m)
+    Phi[:, 6] = rng.normal(size=m)
+    beta[0], beta[6] = 60.0, -8.0
+    for lead in (1, 3):
+        Phi[:, lead] = rng.normal(size=m) + 1j * rng.normal(size=m)
+        Phi[:, lead + 1] = Phi[:, lead].conj()
+        beta[lead] = rng.normal() * 10 + 1j * rng.normal() * 10
+        beta[lead + 1] = beta[lead].conjugate()
+    Phi[:, 5] = rng.normal(size=m) + 1j * rng.normal(size=m)
+    beta[5] = 5.0 - 3.0j
+    return lam, Phi, beta
+
+
+@pytest.mark.parametrize("mode", ["modulus", "real", "static"])
+@pytest.mark.parametrize("cols,perturb", [([0, 1, 2, 3, 4, 6], False),     # conjugate-closed: real terms
+                                          ([0, 1, 2, 5, 3, 4], False),     # a lone complex mode
+                                          ([0, 2, 1, 6], True)])           # pair amplitudes not conjugate
+@pytest.mark.parametrize("pad", [0, 31])          # ldd = m (plain loads) or 16-byte aligned rows (tensor loads)
+def test_subtract_real_terms_and_complex_path(C, ctx, mode, cols, perturb, pad):
+    W, H, n = 61, 37, 45
+    m = W * H
+    lam, Phi, beta = _conjugate_structured_modes(m, 31)
+    if perturb:
+        beta = beta.copy()
+        beta[2] = beta[1].conjugate() * (1 + 1e-3)
+    frames = np.random.default_rng(32).integers(0, 256, size=(n, m), dtype=np.uint8)
+    if pad:
+        padded = np.full((n, m + pad), 255, dtype=np.uint8)      # bytes past m must be ignored
+        padded[:, :m] = frames
+        Dv = _dev(padded)[:, :m]
+    else:
+        Dv = _dev(frames)
+    cols = np.array(cols, dtype=np.int32)
+    Phi_sel = Phi[:, cols].astype(np.complex64)
+    mask, bg = C.cdmd_subtract(ctx, Dv, _dev(np.stack([Phi_sel.real, Phi_sel.imag], axis=-1)),
+                               _dev(np.stack([beta.real, beta.imag], axis=-1)),
+                               _dev(np.stack([lam.real, lam.imag], axis=-1)), 25.0,
+                               cols=_dev(cols), mode=mode, want_bg=True)
+    C.cdmd_status_sync(ctx)
+    ref_bg = O.background(Phi_sel.astype(np.complex128), beta[cols], lam[cols], n, mode)
+    bg = bg.cpu().numpy().T
+    assert np.abs(bg - ref_bg).max() <= 2e-5 * np.abs(ref_bg).max()
+    D = frames.T.astype(np.float64)
+    margin = np.abs(np.abs(D - ref_bg) - 25.0) > 0.01
+    assert np.array_equal(C.unpack_mask(mask, m)[margin], O.foreground_mask(D, ref_bg, 25.0)[margin])
+    # the mask without a background output takes the same decisions
+    mask2 = C.cdmd_subtract(ctx, Dv, _dev(np.stack([Phi_sel.real, Phi_sel.imag], axis=-1)),
+                            _dev(np.stack([beta.real, beta.imag], axis=-1)),
+                            _dev(np.stack([lam.real, lam.imag], axis=-1)), 25.0, cols=_dev(cols), mode=mode)
+    C.cdmd_status_sync(ctx)
+    assert np.array_equal(C.unpack_mask(mask2, m)[margin], O.foreground_mask(D, ref_bg, 25.0)[margin])
