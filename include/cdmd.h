@@ -180,8 +180,9 @@ cdmd_status cdmd_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, void* stream);
 /* Dense Gaussian / Rademacher C generated in-kernel from `seed` (never
  * stored).  D: m x n frames (n >= 2), ldd >= m.  DY: k x n doubles
  * (column-major, ld = k), overwritten.  prec selects FP32 CUDA-core or
- * BF16 hi+lo tensor-core arithmetic (BF16X2 needs n <= 256 and is defined for
- * Gaussian C; Rademacher entries are exact in BF16). */
+ * BF16 hi+lo tensor-core arithmetic (BF16X2 is defined for Gaussian C, needs
+ * a 16-byte aligned D with ldd % 16 == 0, and sketches clips longer than 256
+ * frames in 256-frame pieces, the product being linear in the frames). */
 cdmd_status cdmd_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                         cdmd_ctype ctype, int k, uint64_t seed, cdmd_prec prec,
                         double* DY, void* stream);
@@ -217,7 +218,8 @@ cdmd_status cdmd_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r,
 /* Phi[j*ncols + c] = sum_{t=0}^{n-2} D[(t+1)*ldd + j] * G[:, cols[c]] for the
  * ncols modes listed in `cols` (device int32, NULL = modes 0..ncols-1; a
  * negative entry yields a zero column).  G: (n-1) x r complex double.
- * Phi: m x ncols complex float, pixel-major.  ncols <= 64. */
+ * Phi: m x ncols complex float, pixel-major.  ncols <= 64.  BF16X2 needs a
+ * 16-byte aligned D, ldd % 16 == 0 and n <= 256 (else CDMD_ERR_UNSUPPORTED). */
 cdmd_status cdmd_lift(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                       const double* G, int r, const int32_t* cols, int ncols,
                       cdmd_prec prec, float* Phi, void* stream);
@@ -252,7 +254,9 @@ typedef struct {
 /* Sketch -> decompose -> lift of the selected modes -> subtract, on device
  * buffers, enqueued on `stream`; intermediates live in the context's
  * workspace and stay valid until the next call on the context (see
- * cdmd_workspace_views).  mask as described above. */
+ * cdmd_workspace_views).  mask as described above.  With BF16X2, clips longer
+ * than 256 frames take the FP32 lift (the tensor-core lift holds all n-1
+ * frames of a pixel tile in one operand). */
 cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                      const cdmd_params* p, uint32_t* mask, void* stream);
 
@@ -268,6 +272,87 @@ cdmd_status cdmd_run_host(cdmd_ctx* ctx, const uint8_t* D_host, int64_t m, int n
 cdmd_status cdmd_workspace_views(cdmd_ctx* ctx, double** DY, double** sigma, double** lambda,
                                  double** G, double** beta, int32_t** sel, int32_t** nsel,
                                  float** Phi);
+
+/* ---- batches of clips -------------------------------------------------------
+ *
+ * The paper processes long videos as independent 200-frame batches
+ * (Section 4.1); a batch here is many clips of uneven resolution and length
+ * run through one plan.  cdmd_batch_create validates the clips, allocates
+ * every per-clip buffer and workspace once, picks the execution knobs (see
+ * cdmd_batch_tuning) by timing candidates on the batch itself when asked,
+ * and captures the whole batch into one CUDA graph; cdmd_batch_run replays
+ * it.  Every clip gets the same results as a cdmd_run with the same
+ * parameters up to the rounding order of the sketch's split sums.
+ *
+ * A clip: device video D (frame-major, n frames of m pixels, row stride
+ * ldd), its sketch size k, rank r, K selected modes, measurement seed, and
+ * the device mask it receives (n x ceil(m/32) words, as for cdmd_subtract).
+ * The caller owns D and mask and keeps them alive, at fixed addresses, for
+ * the life of the batch; the graph reads and writes them on every run. */
+typedef struct {
+    const uint8_t* D;
+    int64_t m;
+    int32_t n;
+    int64_t ldd;
+    int32_t k, r, K;
+    uint64_t seed;
+    uint32_t* mask;
+} cdmd_clip;
+
+/* flags */
+#define CDMD_BATCH_GRAPH 1      /* capture the batch into a CUDA graph (else eager launches) */
+#define CDMD_BATCH_AUTOTUNE 2   /* time candidate knobs on the batch and keep the fastest    */
+#define CDMD_BATCH_GROUPED 4    /* the subtract pass of all clips, and with BF16X2 their sketch,
+                                   as one grouped launch each (else per-clip launches); dropped
+                                   silently for clips it does not cover (unaligned D or ldd,
+                                   more than 12 modes)                                        */
+
+typedef struct {
+    cdmd_prec prec;
+    cdmd_selector selector;
+    cdmd_bgmode bgmode;
+    float tau;
+    int32_t lanes;                /* streams (each with its own workspace); 0 = default 8      */
+    int32_t flags;
+    const float* selector_blob;   /* device model blob for CDMD_SEL_MLP, else NULL             */
+} cdmd_batch_params;
+
+typedef struct cdmd_batch cdmd_batch;
+
+/* Plan a batch of nclips clips on `device`; work done while planning (a warm-up
+ * run, autotuning runs, the capture) is enqueued on `stream` and waited for.
+ * Requirements per clip as for cdmd_run (Gaussian C); with BF16X2, D must be
+ * 16-byte aligned with ldd % 16 == 0.  CDMD_ERR_INVALID_ARG names the first
+ * offending clip. */
+cdmd_status cdmd_batch_create(cdmd_batch** batch, int device, const cdmd_clip* clips, int nclips,
+                              const cdmd_batch_params* params, void* stream);
+
+/* Run the whole batch on `stream` (asynchronous; graph replay if captured). */
+cdmd_status cdmd_batch_run(cdmd_batch* batch, void* stream);
+
+/* Synchronise `stream`, then return and clear the first numerical status
+ * recorded by any clip of the batch (CDMD_OK if none). */
+cdmd_status cdmd_batch_status_sync(cdmd_batch* batch, void* stream);
+
+/* Device pointers to clip `clip`'s results of the last run: DY (k x n),
+ * lambda (2r), beta (2r), sel (K), Phi (m x ncols complex float); any output
+ * pointer may be NULL. */
+cdmd_status cdmd_batch_views(cdmd_batch* batch, int clip, double** DY, double** lambda, double** beta,
+                             int32_t** sel, float** Phi);
+
+/* The knobs the plan runs with: lanes (streams), the SM cap of each lane's
+ * full-data passes (0 = none), the sketch work-item size (64-pixel steps per
+ * CTA) and the subtract work-item size (pixel tiles per CTA) of the grouped
+ * launches, and the measured time of one run in milliseconds (0 if not
+ * autotuned). */
+cdmd_status cdmd_batch_tuning(cdmd_batch* batch, int32_t* lanes, int32_t* sm_limit, int32_t* sketch_steps,
+                              int32_t* subtract_tiles, float* run_ms);
+
+void cdmd_batch_destroy(cdmd_batch* batch);
+
+/* Copy `bytes` between any two host or device addresses, ordered on
+ * `stream` (a convenience for bindings reading the views above). */
+cdmd_status cdmd_copy(void* dst, const void* src, size_t bytes, void* stream);
 
 /* ---- learned mode selector ------------------------------------------------
  *

@@ -36,7 +36,10 @@ EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_strin
             "cdmd_decompose", "cdmd_lift", "cdmd_subtract", "cdmd_run", "cdmd_run_host",
             "cdmd_workspace_views", "cdmd_sketch_noalloc", "cdmd_set_sm_limit", "cdmd_selector_load",
             "cdmd_selector_features", "cdmd_selector_fallbacks", "cdmd_mlp_forward", "cdmd_mlp_grad",
-            "cdmd_mlp_train_step", "cdmd_synth_clip", "cdmd_selector_relabel"]
+            "cdmd_mlp_train_step", "cdmd_synth_clip", "cdmd_selector_relabel", "cdmd_batch_create",
+            "cdmd_batch_run", "cdmd_batch_status_sync", "cdmd_batch_views", "cdmd_batch_tuning",
+            "cdmd_batch_destroy", "cdmd_copy"]
+BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_GROUPED = 1, 2, 4
 
 
 class CdmdError(RuntimeError):
@@ -50,6 +53,17 @@ class cdmd_measure(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("density", ctypes.c_double),
                 ("col_ptr", ctypes.c_void_p), ("row_idx", ctypes.c_void_p),
                 ("nnz_capacity", ctypes.c_int64), ("rows", ctypes.c_void_p)]
+
+
+class cdmd_clip(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int32), ("ldd", ctypes.c_int64),
+                ("k", ctypes.c_int32), ("r", ctypes.c_int32), ("K", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("mask", ctypes.c_void_p)]
+
+
+class cdmd_batch_params(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("selector", ctypes.c_int), ("bgmode", ctypes.c_int), ("tau", ctypes.c_float),
+                ("lanes", ctypes.c_int32), ("flags", ctypes.c_int32), ("selector_blob", ctypes.c_void_p)]
 
 
 class cdmd_params(ctypes.Structure):
@@ -93,6 +107,14 @@ def load_library(path=LIB_PATH):
         "cdmd_workspace_views": [vp] + [ctypes.POINTER(vp)] * 8,
         "cdmd_sketch_noalloc": [vp, i64, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, u64, vp, vp],
         "cdmd_selector_load": [vp, vp, vp],
+        "cdmd_batch_create": [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.c_int, vp, vp],
+        "cdmd_batch_run": [vp, vp],
+        "cdmd_batch_status_sync": [vp, vp],
+        "cdmd_batch_views": [vp, ctypes.c_int] + [ctypes.POINTER(vp)] * 5,
+        "cdmd_batch_tuning": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                              ctypes.POINTER(flt)],
+        "cdmd_batch_destroy": [vp],
+        "cdmd_copy": [vp, vp, ctypes.c_size_t, vp],
         "cdmd_selector_relabel": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, vp],
         "cdmd_synth_clip": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int,
                             ctypes.c_int, flt, flt, u64, vp, i64, vp],
@@ -107,6 +129,7 @@ def load_library(path=LIB_PATH):
         fn.argtypes = args
         fn.restype = ctypes.c_int
     lib.cdmd_destroy.restype = None
+    lib.cdmd_batch_destroy.restype = None
     lib.cdmd_last_error.restype = ctypes.c_char_p
     lib.cdmd_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -428,3 +451,84 @@ def cdmd_synth_clip(ctx, spec, seed, D=None, stream=None):
                                    float(spec["drift"]), float(spec["noise_sigma"]), int(seed) & (2**64 - 1),
                                    _ptr(D), int(D.stride(0)), _stream(stream)))
     return D
+
+
+# ---------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------
+
+
+class Batch:
+    """A planned batch of clips (see cdmd_batch_create).
+
+    clips: list of dicts with D (CUDA uint8 (n, m) tensor, unit pixel
+    stride), k, r, K, seed.  Masks are allocated here (self.masks[i],
+    (n, ceil(m/32)) int32).  The tensors must stay alive and unmoved while
+    the batch exists; this object keeps references to them."""
+
+    def __init__(self, clips, tau, prec="fp32", selector="omp", bgmode="modulus", lanes=0, graph=True,
+                 autotune=False, grouped=True, selector_blob=None, device=0, stream=None):
+        import torch
+        self.lib = load_library()
+        self.handle = ctypes.c_void_p()
+        self.videos = [c["D"] for c in clips]
+        self.masks = []
+        arr = (cdmd_clip * len(clips))()
+        for i, c in enumerate(clips):
+            n, m, ldd = _video(c["D"])
+            mask = torch.empty((n, (m + 31) // 32), dtype=torch.int32, device=c["D"].device)
+            self.masks.append(mask)
+            arr[i] = cdmd_clip(c["D"].data_ptr(), m, n, ldd, int(c["k"]), int(c["r"]), int(c["K"]),
+                               int(c["seed"]) & (2**64 - 1), mask.data_ptr())
+        self.meta = [dict(m=int(c["D"].shape[1]), n=int(c["D"].shape[0]), k=int(c["k"]), r=int(c["r"]),
+                          K=int(c["K"])) for c in clips]
+        self.selector = selector
+        flags = (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0) | (BATCH_GROUPED if grouped else 0)
+        self.blob = selector_blob
+        p = cdmd_batch_params(PRECS[prec], SELECTORS[selector], BGMODES[bgmode], float(tau), int(lanes), flags,
+                              _ptr(selector_blob))
+        _check(self.lib.cdmd_batch_create(ctypes.byref(self.handle), int(device), arr, len(clips), ctypes.byref(p),
+                                          _stream(stream)))
+
+    def run(self, stream=None):
+        _check(self.lib.cdmd_batch_run(self.handle, _stream(stream)))
+
+    def status_sync(self, stream=None):
+        _check(self.lib.cdmd_batch_status_sync(self.handle, _stream(stream)))
+
+    def tuning(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        ms = ctypes.c_float()
+        _check(self.lib.cdmd_batch_tuning(self.handle, *[ctypes.byref(x) for x in v], ctypes.byref(ms)))
+        return dict(lanes=v[0].value, sm_limit=v[1].value, sketch_steps=v[2].value, subtract_tiles=v[3].value,
+                    run_ms=ms.value)
+
+    def views(self, i, stream=None):
+        """Host copies of clip i's DY (n, k), lambda (r,), beta (r,), sel (K,)."""
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        _check(self.lib.cdmd_batch_views(self.handle, int(i), *[ctypes.byref(q) for q in ptrs]))
+        md = self.meta[i]
+
+        def fetch(ptr, shape, dtype):
+            out = np.empty(shape, dtype=dtype)
+            _check(self.lib.cdmd_copy(out.ctypes.data_as(ctypes.c_void_p), ptr, out.nbytes, _stream(stream)))
+            return out
+        import torch
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        DY = fetch(ptrs[0], (md["n"], md["k"]), np.float64)
+        lam = fetch(ptrs[1], (md["r"], 2), np.float64)
+        beta = fetch(ptrs[2], (md["r"], 2), np.float64)
+        sel = fetch(ptrs[3], (md["K"],), np.int32)
+        torch.cuda.synchronize()
+        return dict(DY=DY, lam=lam[:, 0] + 1j * lam[:, 1], beta=beta[:, 0] + 1j * beta[:, 1], sel=sel)
+
+    def close(self):
+        if self.handle:
+            self.lib.cdmd_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -215,7 +215,6 @@ cdmd_status cdmd_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (prec == CDMD_PREC_FP32) return launch_sketch_fp32(ctx, D, m, n, ldd, ctype, k, seed, DY, s);
     if (prec == CDMD_PREC_BF16X2) {
-        CDMD_REQUIRE(n <= 256, "BF16X2 sketch needs n <= 256 (got %d)", n);
         return launch_sketch_tc(ctx, D, m, n, ldd, ctype, k, seed, DY, s);
     }
     return fail(CDMD_ERR_INVALID_ARG, "unknown precision %d", static_cast<int>(prec));
@@ -337,7 +336,9 @@ cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t 
     // OMP: lift and subtract only the selected modes (sel, -1 padded);
     // LSTSQ: every mode carries an amplitude, so all r are used.
     const int32_t* cols = (p->selector == CDMD_SEL_LSTSQ) ? nullptr : sel;
-    st = cdmd_lift(ctx, D, m, n, ldd, Gm, r, cols, ncols, p->prec, Phi, stream);
+    // the tensor-core lift covers n <= 256 frames; longer clips lift in FP32
+    const cdmd_prec lift_prec = (p->prec == CDMD_PREC_BF16X2 && n > 256) ? CDMD_PREC_FP32 : p->prec;
+    st = cdmd_lift(ctx, D, m, n, ldd, Gm, r, cols, ncols, lift_prec, Phi, stream);
     if (st != CDMD_OK) return st;
     return cdmd_subtract(ctx, D, m, n, ldd, Phi, ncols, cols, beta, lambda, r, p->tau, p->bgmode, mask, nullptr,
                          stream);

@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 
 #include "tc_common.cuh"
+#include "batch_internal.cuh"
 
 namespace cdmd {
 
@@ -61,6 +62,7 @@ constexpr int kStages = 2;
 constexpr int kKStep = 64;                  // pixels per K step (one 128-byte BF16 row)
 constexpr int kTileBytes = 128 * 128;       // 128 rows x 128 bytes
 constexpr uint32_t kTmemCols = 512;
+constexpr int kMaxFrames = 256;             // frames per launch: MMA N and TMA box height limits
 
 // Fast Box-Muller pair (MUFU lg2 / sqrt / sin / cos), same definition as the
 // accurate form: U(w) = (w + 1/2) 2^-32, angle split into quarter turns.
@@ -101,12 +103,12 @@ __host__ __device__ inline SmemLayout smem_layout(int n) {
     return L;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, int k, uint2 key,
-                 int64_t steps_per_split, int64_t total_steps, float* __restrict__ part, int* status) {
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    // the runtime aligns dynamic shared memory to at least 16 bytes; round up
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+// One CTA's share of C D: rows pair*256 .. pair*256+255 of C over the
+// 64-pixel K steps step0 .. step0+nsteps-1, written to part[t * k + row]
+// (this split's partial sums).  Used by the per-clip and the grouped launch.
+__device__ __forceinline__ void sketch_tc_body(const CUtensorMap* tmap, int64_t m, int n, int k, uint2 key, int pair,
+                                               int64_t step0, int64_t nsteps, float* __restrict__ part, int* status,
+                                               uint8_t* smem) {
     const SmemLayout L = smem_layout(n);
     const int npad = (n + 15) / 16 * 16;
     uint8_t* A = smem + L.a_off;
@@ -125,11 +127,6 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, int
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const int pair = blockIdx.x;
-    const int split = blockIdx.y;
-    const int64_t step0 = static_cast<int64_t>(split) * steps_per_split;
-    int64_t nsteps = total_steps - step0;
-    if (nsteps > steps_per_split) nsteps = steps_per_split;
     if (nsteps < 0) nsteps = 0;
     const uint32_t b_stride = (L.b_stage_bytes + 1023u) / 1024u * 1024u;
 
@@ -167,7 +164,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, int
                 const uint32_t u = static_cast<uint32_t>(ks / kStages);
                 if (u >= 1 && !tc::mbar_wait(&d_free[s], (u - 1) & 1u, abort_flag, status)) break;
                 tc::mbar_arrive_expect_tx(&tma_full[s], static_cast<uint32_t>(n) * kKStep);
-                tc::tma_load_2d(Dst + s * L.dst_stage_bytes, &tmap, static_cast<int>((step0 + ks) * kKStep), 0,
+                tc::tma_load_2d(Dst + s * L.dst_stage_bytes, tmap, static_cast<int>((step0 + ks) * kKStep), 0,
                                 &tma_full[s]);
             }
             // drain: the last load of each stage must have landed before exit
@@ -310,7 +307,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, int
 #pragma unroll
                             for (int q = 0; q < 16; ++q) {
                                 const int t = c0 + q;
-                                if (t < n) part[(static_cast<int64_t>(split) * n + t) * k + row] = __uint_as_float(v[q]);
+                                if (t < n) part[static_cast<int64_t>(t) * k + row] = __uint_as_float(v[q]);
                             }
                         }
                     }
@@ -326,6 +323,50 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, int
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem_base, kTmemCols);
     }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, int k, uint2 key,
+                 int64_t steps_per_split, int64_t total_steps, float* __restrict__ part, int* status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // the runtime aligns dynamic shared memory to at least 16 bytes; round up
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    const int split = blockIdx.y;
+    const int64_t step0 = static_cast<int64_t>(split) * steps_per_split;
+    int64_t nsteps = total_steps - step0;
+    if (nsteps > steps_per_split) nsteps = steps_per_split;
+    sketch_tc_body(&tmap, m, n, k, key, blockIdx.x, step0, nsteps, part + static_cast<int64_t>(split) * n * k, status,
+                   smem);
+}
+
+// Grouped launch: CTA b runs work item items[b] (any clip, frame chunk,
+// row pair and pixel range); the tensor maps live in global memory.
+__global__ void __launch_bounds__(kThreads, 1)
+sketch_tc_grouped_kernel(const SketchItem* __restrict__ items, int* status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    const SketchItem it = items[blockIdx.x];
+    sketch_tc_body(it.tmap, it.m, it.n, it.k, it.key, it.pair, it.step0, it.nsteps, it.part, status, smem);
+}
+
+// Grouped fixed-order reduce: element idx of the concatenated outputs belongs
+// to chunk c with prefix[c] <= idx < prefix[c+1].
+__global__ void sketch_reduce_grouped_kernel(const ReduceChunk* __restrict__ chunks, const int64_t* __restrict__ prefix,
+                                             int nchunks, int64_t total, int* status) {
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int lo = 0, hi = nchunks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    const ReduceChunk c = chunks[lo];
+    const int64_t e = idx - prefix[lo];
+    double s = 0.0;
+    for (int sp = 0; sp < c.splits; ++sp) s += static_cast<double>(c.part[static_cast<int64_t>(sp) * c.elems + e]);
+    if (!isfinite(s)) record_status(status, CDMD_ERR_NONFINITE);
+    c.DY[e] = s;
 }
 
 // DY[t*k + i] = sum_s part[(s*n + t)*k + i], FP64, fixed order.
@@ -348,6 +389,16 @@ cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, 
         return fail(CDMD_ERR_UNSUPPORTED, "BF16X2 sketch is built for the Gaussian measurement matrix");
     if ((reinterpret_cast<uintptr_t>(D) & 15) != 0 || (ldd & 15) != 0)
         return fail(CDMD_ERR_INVALID_ARG, "BF16X2 sketch needs a 16-byte aligned video and ldd %% 16 == 0");
+    if (n > kMaxFrames) {
+        // the sketch is linear in the frames: DY[t0:t1] = C D[:, t0:t1]
+        for (int t0 = 0; t0 < n; t0 += kMaxFrames) {
+            const int nc = std::min(kMaxFrames, n - t0);
+            cdmd_status st = launch_sketch_tc(ctx, D + static_cast<int64_t>(t0) * ldd, m, nc, ldd, ctype, k, seed,
+                                              DY + static_cast<int64_t>(t0) * k, stream);
+            if (st != CDMD_OK) return st;
+        }
+        return CDMD_OK;
+    }
     CUtensorMap tmap;
     cdmd_status st = make_video_tmap(&tmap, D, m, n, ldd, kKStep, n);
     if (st != CDMD_OK) return st;
@@ -372,6 +423,24 @@ cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, 
     sketch_tc_reduce_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, stream>>>(
         part, static_cast<int>(splits), k, n, DY, ctx->d_status);
     CDMD_CHECK_LAUNCH("sketch_tc_reduce_kernel");
+    return CDMD_OK;
+}
+
+}  // namespace cdmd
+
+namespace cdmd {
+
+size_t sketch_tc_smem_bytes(int n) { return smem_layout(n).total + 1024; }
+
+cdmd_status launch_sketch_grouped(const SketchItem* items, int nitems, size_t smem, const ReduceChunk* chunks,
+                                  const int64_t* prefix, int nchunks, int64_t total, int* status, cudaStream_t stream) {
+    CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem)));
+    sketch_tc_grouped_kernel<<<static_cast<unsigned>(nitems), kThreads, smem, stream>>>(items, status);
+    CDMD_CHECK_LAUNCH("sketch_tc_grouped_kernel");
+    sketch_reduce_grouped_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, stream>>>(chunks, prefix, nchunks,
+                                                                                                total, status);
+    CDMD_CHECK_LAUNCH("sketch_reduce_grouped_kernel");
     return CDMD_OK;
 }
 

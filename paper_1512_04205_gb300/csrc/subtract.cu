@@ -18,6 +18,7 @@
 // exactly mask word base/32 + e of frame t.
 #include "cdmd_internal.cuh"
 #include "tc_common.cuh"
+#include "batch_internal.cuh"
 
 namespace cdmd {
 namespace {
@@ -57,9 +58,9 @@ __host__ __device__ inline Table table_views(void* base, int n, int nc_pad) {
     return t;
 }
 
-__global__ void __launch_bounds__(32)
-subtract_table_kernel(const int32_t* __restrict__ cols, int ncols, int nc_pad, const double* __restrict__ beta,
-                      const double* __restrict__ lambda, int r, int n, Table tb) {
+__device__ __forceinline__ void build_table(const int32_t* __restrict__ cols, int ncols, int nc_pad,
+                                            const double* __restrict__ beta, const double* __restrict__ lambda, int r,
+                                            int n, const Table& tb) {
     const int c = threadIdx.x;
     int s = -1;
     if (c < ncols) s = cols ? cols[c] : c;
@@ -123,6 +124,19 @@ subtract_table_kernel(const int32_t* __restrict__ cols, int ncols, int nc_pad, c
         pr = nr;
         pi = ni;
     }
+}
+
+__global__ void __launch_bounds__(32)
+subtract_table_kernel(const int32_t* __restrict__ cols, int ncols, int nc_pad, const double* __restrict__ beta,
+                      const double* __restrict__ lambda, int r, int n, Table tb) {
+    build_table(cols, ncols, nc_pad, beta, lambda, r, n, tb);
+}
+
+// Grouped: one warp per clip, tables with the common column stride nc.
+__global__ void __launch_bounds__(32)
+subtract_table_grouped_kernel(const SubtractClip* __restrict__ clips, int nc) {
+    const SubtractClip c = clips[blockIdx.x];
+    build_table(c.cols, c.ncols, nc, c.beta, c.lambda, c.r, c.n, table_views(c.table, c.n, nc));
 }
 
 // One pixel tile for every frame.  REAL: accumulate real terms only (the
@@ -322,12 +336,13 @@ __host__ __device__ inline size_t tma_smem_bytes(int n, int nc) {
 // Consumer side: every chunk of every tile of this CTA.
 template <int NT, int MODE, bool REAL, int LSTRIDE>
 __device__ __forceinline__ void tma_consume(const uint8_t* stages, uint64_t* full, uint64_t* empty, volatile int* abort,
-                                            int* status, int64_t my_tiles, int nch, int64_t m, int n,
+                                            int* status, int64_t tile0, int64_t tstride, int64_t my_tiles, int nch,
+                                            int64_t m, int n,
                                             const float2* __restrict__ Phi, int ncols, const Table& tb, int nterms,
                                             const float2* Ls, float tau, uint32_t* __restrict__ mask,
                                             int64_t words_per_frame, float* __restrict__ bg_out, int warp, int lane) {
     for (int64_t ti = 0; ti < my_tiles; ++ti) {
-        const int64_t tile = blockIdx.x + ti * gridDim.x;
+        const int64_t tile = tile0 + ti * tstride;
         const int64_t j0 = tile * kTmaTile + warp * kTmaWarpPx + kTmaPxl * lane;
         float2 a[kTmaPxl][NT];
 #pragma unroll
@@ -433,11 +448,11 @@ __device__ __forceinline__ void tma_consume(const uint8_t* stages, uint64_t* ful
 }
 
 template <int NC, int MODE>
-__global__ void __launch_bounds__(kTmaThreads, 1)   // 16 warps x 128 registers fill the 64K register file
-subtract_tma_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, const float2* __restrict__ Phi,
-                    int ncols, Table tb, float tau, uint32_t* __restrict__ mask, int64_t words_per_frame,
-                    float* __restrict__ bg_out, int* status) {
-    extern __shared__ __align__(1024) uint8_t smem[];
+__device__ __forceinline__ void subtract_tma_body(const CUtensorMap* tmap, int64_t m, int n,
+                                                  const float2* __restrict__ Phi, int ncols, const Table& tb, float tau,
+                                                  uint32_t* __restrict__ mask, int64_t words_per_frame,
+                                                  float* __restrict__ bg_out, int* status, int64_t tile0,
+                                                  int64_t tstride, int64_t my_tiles, uint8_t* smem) {
     uint8_t* stages = smem;
     float2* Ls = reinterpret_cast<float2*>(smem + tma_ls_offset());
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + tma_bar_offset(n, NC));
@@ -458,9 +473,7 @@ subtract_tma_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, 
         tc::fence_mbar_init();
     }
     __syncthreads();
-    const int64_t tiles = (m + kTmaTile - 1) / kTmaTile;
     const int nch = (n + kTmaFB - 1) / kTmaFB;
-    const int64_t my_tiles = (static_cast<int64_t>(blockIdx.x) < tiles) ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t total = my_tiles * nch;
     if (warp == kTmaConsumers) {
         if (lane == 0) {
@@ -470,12 +483,12 @@ subtract_tma_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, 
                 const int64_t u = g / kTmaStages;
                 if (u >= 1 && !tc::mbar_wait(&empty[s], static_cast<uint32_t>(u - 1) & 1u, abort, status)) break;
                 if (*abort) break;
-                const int64_t tile = blockIdx.x + (g / nch) * gridDim.x;
+                const int64_t tile = tile0 + (g / nch) * tstride;
                 const int t0 = static_cast<int>(g % nch) * kTmaFB;
                 tc::mbar_arrive_expect_tx(&full[s], kChunkBytes);
 #pragma unroll
                 for (int q = 0; q < kTmaTile / kTmaBox; ++q)
-                    tc::tma_load_2d(stages + static_cast<size_t>(s) * kChunkBytes + q * (kTmaFB * kTmaBox), &tmap,
+                    tc::tma_load_2d(stages + static_cast<size_t>(s) * kChunkBytes + q * (kTmaFB * kTmaBox), tmap,
                                     static_cast<int>(tile * kTmaTile + q * kTmaBox), t0, &full[s]);
             }
             *issued_sm = static_cast<int>(g);
@@ -486,19 +499,19 @@ subtract_tma_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, 
         constexpr int N1 = (NC + 1) / 2, N2 = N1 + 1, N3 = N1 + 2;
         const int nterms = tb.hdr[0];
         if (nterms <= N1)
-            tma_consume<N1, MODE, true, NC>(stages, full, empty, abort, status, my_tiles, nch, m, n, Phi, ncols, tb,
+            tma_consume<N1, MODE, true, NC>(stages, full, empty, abort, status, tile0, tstride, my_tiles, nch, m, n, Phi, ncols, tb,
                                             nterms, Ls, tau, mask, words_per_frame, bg_out, warp, lane);
         else if (nterms <= N2)
-            tma_consume<N2, MODE, true, NC>(stages, full, empty, abort, status, my_tiles, nch, m, n, Phi, ncols, tb,
+            tma_consume<N2, MODE, true, NC>(stages, full, empty, abort, status, tile0, tstride, my_tiles, nch, m, n, Phi, ncols, tb,
                                             nterms, Ls, tau, mask, words_per_frame, bg_out, warp, lane);
         else if (nterms <= N3)
-            tma_consume<N3, MODE, true, NC>(stages, full, empty, abort, status, my_tiles, nch, m, n, Phi, ncols, tb,
+            tma_consume<N3, MODE, true, NC>(stages, full, empty, abort, status, tile0, tstride, my_tiles, nch, m, n, Phi, ncols, tb,
                                             nterms, Ls, tau, mask, words_per_frame, bg_out, warp, lane);
         else
-            tma_consume<NC, MODE, true, NC>(stages, full, empty, abort, status, my_tiles, nch, m, n, Phi, ncols, tb,
+            tma_consume<NC, MODE, true, NC>(stages, full, empty, abort, status, tile0, tstride, my_tiles, nch, m, n, Phi, ncols, tb,
                                             nterms, Ls, tau, mask, words_per_frame, bg_out, warp, lane);
     } else {
-        tma_consume<NC, MODE, false, NC>(stages, full, empty, abort, status, my_tiles, nch, m, n, Phi, ncols, tb, NC,
+        tma_consume<NC, MODE, false, NC>(stages, full, empty, abort, status, tile0, tstride, my_tiles, nch, m, n, Phi, ncols, tb, NC,
                                          Ls, tau, mask, words_per_frame, bg_out, warp, lane);
     }
     __syncthreads();
@@ -509,6 +522,31 @@ subtract_tma_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, 
         for (int64_t g = (issued > kTmaStages ? issued - kTmaStages : 0); g < issued; ++g)
             tc::mbar_wait(&full[g % kTmaStages], static_cast<uint32_t>(g / kTmaStages) & 1u, &never, status);
     }
+}
+
+template <int NC, int MODE>
+__global__ void __launch_bounds__(kTmaThreads, 1)   // 16 warps x 128 registers fill the 64K register file
+subtract_tma_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, const float2* __restrict__ Phi,
+                    int ncols, Table tb, float tau, uint32_t* __restrict__ mask, int64_t words_per_frame,
+                    float* __restrict__ bg_out, int* status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int64_t tiles = (m + kTmaTile - 1) / kTmaTile;
+    const int64_t my_tiles = (static_cast<int64_t>(blockIdx.x) < tiles) ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    subtract_tma_body<NC, MODE>(&tmap, m, n, Phi, ncols, tb, tau, mask, words_per_frame, bg_out, status, blockIdx.x,
+                                gridDim.x, my_tiles, smem);
+}
+
+// Grouped: CTA b runs item items[b], consecutive tiles of one clip.
+template <int NC, int MODE>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+subtract_tma_grouped_kernel(const SubtractClip* __restrict__ clips, const SubtractItem* __restrict__ items,
+                            float tau, int* status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const SubtractItem it = items[blockIdx.x];
+    const SubtractClip c = clips[it.clip];
+    subtract_tma_body<NC, MODE>(c.tmap, c.m, c.n, reinterpret_cast<const float2*>(c.Phi), c.ncols,
+                                table_views(c.table, c.n, NC), tau, c.mask, c.words_per_frame, nullptr, status,
+                                it.tile0, 1, it.ntiles, smem);
 }
 
 template <int NC>
@@ -608,6 +646,47 @@ cdmd_status launch_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, i
         case 24: return launch_nc<24, 1>(mode, D, m, n, ldd, ph, ncols, tb, tau, mask, bg, ctx->num_sms, stream);
         default: return launch_nc<32, 1>(mode, D, m, n, ldd, ph, ncols, tb, tau, mask, bg, ctx->num_sms, stream);
     }
+}
+
+}  // namespace cdmd
+
+namespace cdmd {
+
+size_t subtract_table_bytes_nc(int n, int nc) { return table_bytes(n, nc); }
+size_t subtract_tma_smem(int n, int nc) { return tma_smem_bytes(n, nc); }
+int subtract_tile_pixels() { return kTmaTile; }
+
+cdmd_status make_subtract_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, int n, int64_t ldd) {
+    return make_video_tmap(map, D, m, n, ldd, kTmaBox, kTmaFB);
+}
+
+cdmd_status launch_subtract_grouped(const SubtractClip* clips, int nclips, const SubtractItem* items, int nitems,
+                                    int nc, int max_n, cdmd_bgmode mode, float tau, int* status, cudaStream_t stream) {
+    subtract_table_grouped_kernel<<<static_cast<unsigned>(nclips), 32, 0, stream>>>(clips, nc);
+    CDMD_CHECK_LAUNCH("subtract_table_grouped_kernel");
+    const size_t smem = tma_smem_bytes(max_n, nc);
+#define CDMD_SUBG(NCV, MV)                                                                                   \
+    {                                                                                                        \
+        auto kern = subtract_tma_grouped_kernel<NCV, MV>;                                                    \
+        CDMD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                             static_cast<int>(smem)));                                       \
+        kern<<<static_cast<unsigned>(nitems), kTmaThreads, smem, stream>>>(clips, items, tau, status);       \
+    }
+#define CDMD_SUBG_NC(MV)                                \
+    switch (nc) {                                       \
+        case 4: CDMD_SUBG(4, MV) break;                 \
+        case 8: CDMD_SUBG(8, MV) break;                 \
+        case 10: CDMD_SUBG(10, MV) break;               \
+        case 12: CDMD_SUBG(12, MV) break;               \
+        default: return fail(CDMD_ERR_INVALID_ARG, "grouped subtract: column stride %d", nc); \
+    }
+    if (mode == CDMD_BG_MODULUS) { CDMD_SUBG_NC(CDMD_BG_MODULUS) }
+    else if (mode == CDMD_BG_REAL) { CDMD_SUBG_NC(CDMD_BG_REAL) }
+    else { CDMD_SUBG_NC(CDMD_BG_STATIC) }
+#undef CDMD_SUBG_NC
+#undef CDMD_SUBG
+    CDMD_CHECK_LAUNCH("subtract_tma_grouped_kernel");
+    return CDMD_OK;
 }
 
 }  // namespace cdmd

@@ -277,6 +277,7 @@ def test_subtract_matches_oracle(C, ctx, mode):
 # ----------------------------------------------------- sketch, tensor cores
 
 @pytest.mark.parametrize("w,h,n,k", [(160, 120, 100, 200), (97, 61, 37, 203), (64, 33, 256, 300),
+                                     (48, 32, 300, 120), (40, 24, 257, 64),
                                      (300, 40, 16, 513)])
 def test_sketch_bf16x2_gaussian(C, ctx, w, h, n, k):
     # BF16 hi+lo C (2^-16 relative per entry), fast MUFU Box-Muller, FP32
