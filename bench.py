@@ -235,6 +235,75 @@ def run_reference(args, rank):
 
 
 # ----------------------------------------------------------------------------
+# batch of clips of uneven size (grouped launches, captured graph, autotuned)
+# ----------------------------------------------------------------------------
+
+BATCH = dict(clips=64, sizes=[(320, 240), (640, 480), (1280, 720), (1920, 1080)], n_lo=50, n_hi=300, r_lo=10,
+             r_hi=30, K=10, tau=25.0, seed=4242)
+
+
+def run_batch_measure(C, SEL, torch, dev, args, model):
+    """64 seeded clips (resolution, length and rank drawn per clip, k =
+    min(1000, 4n)) rendered on the device, planned as one batch (grouped
+    launches, graph, autotuner) and timed over replays; the same clips one
+    after another through cdmd_run for comparison."""
+    import videogen
+    rng = np.random.default_rng(BATCH["seed"])
+    clips, frames_total = [], 0
+    ctx = C.Context(dev.index or 0)
+    for i in range(BATCH["clips"]):
+        w, h = BATCH["sizes"][int(rng.integers(0, len(BATCH["sizes"])))]
+        n = int(rng.integers(BATCH["n_lo"], BATCH["n_hi"] + 1))
+        r = int(rng.integers(BATCH["r_lo"], BATCH["r_hi"] + 1))
+        spec = videogen.clip_spec(w, h, n, BATCH["seed"] * 1000 + i, drift=float(rng.uniform(0, 0.1)))
+        D = C.cdmd_synth_clip(ctx, spec, BATCH["seed"] * 1000 + i)
+        clips.append(dict(D=D, k=min(1000, 4 * n), r=r, K=min(BATCH["K"], r), seed=77 + i))
+        frames_total += n
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch = C.Batch(clips, BATCH["tau"], prec=args.prec, selector=args.selector, autotune=True, grouped=True,
+                    graph=True, lanes=8, selector_blob=model)
+    plan_s = time.perf_counter() - t0
+    tune = batch.tuning()
+    reps = max(3, min(args.steps, 10))
+    batch.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        batch.run()
+    e1.record()
+    torch.cuda.synchronize()
+    batch.status_sync()
+    ms = e0.elapsed_time(e1) / reps
+    # the same clips one after another through the single-clip call
+    if model is not None:
+        C.cdmd_selector_load(ctx, model)
+    params = [C.make_params(c["k"], c["r"], c["K"], BATCH["tau"], seed=c["seed"], prec=args.prec,
+                            selector=args.selector) for c in clips]
+    for c, p in zip(clips, params):
+        C.cdmd_run(ctx, c["D"], p)
+    torch.cuda.synchronize()
+    e0.record()
+    for c, p in zip(clips, params):
+        C.cdmd_run(ctx, c["D"], p)
+    e1.record()
+    torch.cuda.synchronize()
+    C.cdmd_status_sync(ctx)
+    seq_ms = e0.elapsed_time(e1)
+    pix_frames = sum(int(c["D"].shape[0]) * int(c["D"].shape[1]) for c in clips)
+    batch.close()
+    return {"clips": len(clips), "frames": frames_total, "pixel_frames": pix_frames,
+            "value": frames_total / (ms * 1e-3), "unit": "frames/s", "ms_per_batch": ms,
+            "gpixel_frames_per_s": pix_frames / (ms * 1e-3) / 1e9,
+            "sequential_cdmd_run": {"value": frames_total / (seq_ms * 1e-3), "ms_per_batch": seq_ms},
+            "tuning": tune, "plan_s": plan_s,
+            "config": {"sizes": BATCH["sizes"], "n": [BATCH["n_lo"], BATCH["n_hi"]], "k": "min(1000, 4n)",
+                       "r": [BATCH["r_lo"], BATCH["r_hi"]], "K": BATCH["K"], "launch": "grouped sketch + subtract, "
+                       "per-clip small solves and lifts on lanes, one CUDA graph"}}
+
+
+# ----------------------------------------------------------------------------
 # GPU path
 # ----------------------------------------------------------------------------
 
@@ -428,6 +497,8 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": int(n * ((m + 31) // 32) * 4), "steps": e2e_steps,
                "host_threads": len(lanes), "api": "cdmd_run_host (pinned host video in, host mask out)"}
 
+    batch_line = run_batch_measure(C, SEL, torch, dev, args, model) if args.batch else None
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -493,6 +564,8 @@ def run_ours(args, rank, world, local_rank):
                               "per_pass_ms": {nm: float(v) for nm, v in
                                               zip(["sketch", "decompose", "lift", "subtract"], plain["passes"])},
                               "mask_agreement_vs_head": float(agree.mean())}
+    if batch_line is not None:
+        line["batch"] = batch_line
     if not args.no_cpu:
         fps, detail, _, _ = oracle_fps(clip, w["width"] * 8)
         line["cpu_baseline"] = {"value": fps, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
@@ -527,6 +600,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--inflight", type=int, default=8, help="clips in flight per GPU (streams)")
+    ap.add_argument("--batch", action="store_true",
+                    help="also measure a batch of 64 clips of mixed size (grouped launches, graph, autotuner)")
     ap.add_argument("--size", default=None,
                     help="WxH of a smaller clip for profiling captures (default: the 1920x1080 workload)")
     ap.add_argument("--sm-limit", type=int, default=136,

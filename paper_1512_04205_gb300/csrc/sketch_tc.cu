@@ -95,7 +95,9 @@ __host__ __device__ inline SmemLayout smem_layout(int n) {
     L.a_off = 0;
     L.b_stage_bytes = static_cast<uint32_t>(npad) * 128u;
     L.b_off = L.a_off + kStages * 4 * kTileBytes;
-    L.dst_stage_bytes = static_cast<uint32_t>(n) * kKStep;
+    // tensor copies need a 128-byte aligned shared-memory destination: pad
+    // the staging stride (n * 64 bytes is only 64-byte aligned for odd n)
+    L.dst_stage_bytes = (static_cast<uint32_t>(n) * kKStep + 127u) / 128u * 128u;
     L.dst_off = L.b_off + kStages * ((L.b_stage_bytes + 1023u) / 1024u * 1024u);
     L.bar_off = (L.dst_off + kStages * L.dst_stage_bytes + 127u) / 128u * 128u;
     L.misc_off = L.bar_off + (5 * kStages + 1) * 8;

@@ -25,7 +25,8 @@ def C():
 # (width, height, n, k, r, K): uneven sizes, a clip longer than 256 frames,
 # a pixel count that is not a multiple of the 960-pixel subtract tile
 SHAPES = [(320, 240, 100, 400, 14, 8), (160, 120, 60, 240, 10, 6), (64, 48, 300, 300, 12, 10),
-          (208, 96, 80, 320, 16, 10), (640, 480, 50, 200, 10, 4), (112, 80, 150, 600, 20, 10)]
+          (208, 96, 80, 320, 16, 10), (640, 480, 50, 200, 10, 4), (112, 80, 150, 600, 20, 10),
+          (320, 192, 161, 644, 18, 10), (256, 128, 287, 1000, 27, 10)]     # odd n, several K steps per item
 
 
 def _clips(device="cuda"):
@@ -53,10 +54,12 @@ def _compare(C, batch, clips, ctx, prec, selector):
         # pixels sitting on the threshold
         assert np.mean(a != b) <= 2e-4, (i, np.mean(a != b))
         v = batch.views(i)
-        # the sketch matches the per-clip sketch up to FP32 summation order
+        # the sketch matches the per-clip sketch up to the order of its FP32
+        # partial sums (the batch sums longer pixel ranges per partial)
         DYt = C.cdmd_sketch(ctx, c["D"], c["k"], c["seed"], prec=prec)
         DY = DYt.cpu().numpy()
-        assert np.abs(v["DY"] - DY).max() <= 1e-5 * np.abs(DY).max()
+        assert np.abs(v["DY"] - DY).max() <= 5e-5 * np.abs(DY).max()
+        assert np.linalg.norm(v["DY"] - DY) <= 1e-5 * np.linalg.norm(DY)
         # and so do the eigenvalues of the decomposition
         dec = C.cdmd_decompose(ctx, DYt, c["r"], c["K"], selector=selector)
         C.cdmd_status_sync(ctx)

@@ -278,6 +278,7 @@ def test_subtract_matches_oracle(C, ctx, mode):
 
 @pytest.mark.parametrize("w,h,n,k", [(160, 120, 100, 200), (97, 61, 37, 203), (64, 33, 256, 300),
                                      (48, 32, 300, 120), (40, 24, 257, 64),
+                                     (256, 160, 37, 100), (384, 160, 255, 200),   # odd n, several K steps per CTA
                                      (300, 40, 16, 513)])
 def test_sketch_bf16x2_gaussian(C, ctx, w, h, n, k):
     # BF16 hi+lo C (2^-16 relative per entry), fast MUFU Box-Muller, FP32
