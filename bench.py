@@ -45,6 +45,27 @@ def workload_name(prec, selector="omp"):
     return f"cdmd_{w['width']}x{w['height']}_n{w['n']}_k{w['k']}_r{w['r']}_K{w['K']}_gaussian_{prec}_{selector}"
 
 
+def clip_seed(rank):
+    """Each rank sketches its own clip (clips are independent): weak scaling,
+    no collective on the data path."""
+    return WORKLOAD["clip_seed"] + rank
+
+
+def max_over_ranks(x, dist, device):
+    """The slowest rank's time (the job's time); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(frames_per_rank, world, seconds):
+    """Frames of all ranks over the max-over-ranks time."""
+    return world * frames_per_rank / seconds
+
+
 def fmeasure(pred, truth):
     """F-measure of a boolean mask against the generator's ground truth."""
     tp = float(np.count_nonzero(pred & truth))
@@ -323,7 +344,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     w = WORKLOAD
-    clip = videogen.make_clip(w["width"], w["height"], w["n"], seed=w["clip_seed"] + rank, drift=w["drift"])
+    clip = videogen.make_clip(w["width"], w["height"], w["n"], seed=clip_seed(rank), drift=w["drift"])
     m, n, k, r, K = clip.m, clip.n, w["k"], w["r"], w["K"]
     D = torch.from_numpy(clip.frames).to(dev)
     main_stream = torch.cuda.current_stream()
@@ -392,10 +413,7 @@ def run_ours(args, rank, world, local_rank):
         C.cdmd_status_sync(ctx)
         total_ms = start.elapsed_time(end)
         passes = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs]).mean(axis=0)
-        if dist is not None:
-            t = torch.tensor([total_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
         barrier()
         return total_ms, passes, clocks
 
@@ -428,10 +446,7 @@ def run_ours(args, rank, world, local_rank):
             C.cdmd_status_sync(L.ctx, L.stream)
             C.cdmd_set_sm_limit(L.ctx, 0)
         total_ms = start.elapsed_time(end)
-        if dist is not None:
-            t = torch.tensor([total_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
         barrier()
         return total_ms, clocks
 
@@ -489,10 +504,7 @@ def run_ours(args, rank, world, local_rank):
         dt = time.perf_counter() - t0
         for L in lanes:
             C.cdmd_set_sm_limit(L.ctx, 0)
-        if dist is not None:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dist, dev)
         e2e = {"value": world * n * e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(m * n),
                "d2h_bytes_per_step": int(n * ((m + 31) // 32) * 4), "steps": e2e_steps,
                "host_threads": len(lanes), "api": "cdmd_run_host (pinned host video in, host mask out)"}
@@ -506,8 +518,8 @@ def run_ours(args, rank, world, local_rank):
 
     head = results["head"]
     steps = args.steps
-    latency_value = world * n * steps / (head["total_ms"] * 1e-3)
-    value = world * n * steps / (piped_ms * 1e-3) if piped_ms is not None else latency_value
+    latency_value = job_throughput(n * steps, world, head["total_ms"] * 1e-3)
+    value = job_throughput(n * steps, world, piped_ms * 1e-3) if piped_ms is not None else latency_value
     counts = algorithmic_counts()
     peaks, peak_src = load_peaks()
     sketch_ms = float(head["passes"][0])
