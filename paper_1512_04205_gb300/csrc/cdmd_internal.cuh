@@ -62,6 +62,32 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 key) {
     return c;
 }
 
+// The same generator with its ten round keys computed once by the caller
+// (key + i * (0x9E3779B9, 0xBB67AE85)); for loops that draw many counters
+// under one key.
+struct PhiloxKeys {
+    uint32_t x[10], y[10];
+};
+__device__ __forceinline__ PhiloxKeys philox_round_keys(uint2 key) {
+    PhiloxKeys k;
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        k.x[rnd] = key.x + static_cast<uint32_t>(rnd) * 0x9E3779B9u;
+        k.y[rnd] = key.y + static_cast<uint32_t>(rnd) * 0xBB67AE85u;
+    }
+    return k;
+}
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& k) {
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+        const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+        c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k.x[rnd], static_cast<uint32_t>(p1),
+                       static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k.y[rnd], static_cast<uint32_t>(p0));
+    }
+    return c;
+}
+
 __host__ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
     return make_uint2(static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
 }

@@ -65,23 +65,22 @@ constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxFrames = 256;             // frames per launch: MMA N and TMA box height limits
 
 // Fast Box-Muller pair (MUFU lg2 / sqrt / sin / cos), same definition as the
-// accurate form: U(w) = (w + 1/2) 2^-32, angle split into quarter turns.
+// accurate form: U(w) = (w + 1/2) 2^-32 for the radius; the angle 2 pi U(wb)
+// is taken from the top 23 bits of wb, f = (wb >> 9 + 1/2) 2^-23 built as a
+// float in [1, 2) from the bits minus 1 (no integer conversion), and handed
+// to the hardware sine / cosine whole.  The angle differs from 2 pi U(wb) by
+// at most pi 2^-23, and the MUFU sine / cosine by about 2^-21 absolute, far
+// below the BF16 hi + lo split of C.
 __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float& zc, float& zs) {
     const float u = fmaf(__uint2float_rn(wa), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float x = -1.3862943611198906f * __log2f(u);   // -2 ln u
     float rad;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rad) : "f"(x));
-    // f = (low 30 bits of wb + 1/2) 2^-30 from the top 23 of those bits: a float
-    // in [1, 2) built from the bits, minus 1, plus half a step (no I2F)
-    const float f = __uint_as_float(0x3F800000u | ((wb >> 7) & 0x7FFFFFu)) - (1.0f - 5.9604645e-08f);
+    const float f = __uint_as_float(0x3F800000u | (wb >> 9)) - (1.0f - 5.9604645e-08f);
     float s, c;
-    __sincosf(1.5707963267948966f * f, &s, &c);
-    const uint32_t qt = wb >> 30;
-    float cs = (qt & 1u) ? -s : c;
-    float sn = (qt & 1u) ? c : s;
-    if (qt & 2u) { cs = -cs; sn = -sn; }
-    zc = rad * cs;
-    zs = rad * sn;
+    __sincosf(6.283185307179586f * f, &s, &c);
+    zc = rad * c;
+    zs = rad * s;
 }
 
 struct SmemLayout {
@@ -238,6 +237,7 @@ __device__ __forceinline__ void sketch_tc_body(const CUtensorMap* tmap, int64_t 
         // ---------------- C generators (256 threads) ----------------
         const int gt = tid - 128;
         const int row_pair0 = pair * 256;
+        const PhiloxKeys rk = philox_round_keys(key);   // the same for every draw of this CTA
         for (int64_t ks = 0; ks < nsteps; ++ks) {
             const int s = static_cast<int>(ks % kStages);
             const uint32_t u = static_cast<uint32_t>(ks / kStages);
@@ -254,11 +254,18 @@ __device__ __forceinline__ void sketch_tc_body(const CUtensorMap* tmap, int64_t 
                 const uint32_t gq = static_cast<uint32_t>((row_pair0 >> 2) + q);
                 float z[4][8];
                 const int64_t jg = j0 + 8 * g;
-                if (row_pair0 + 4 * q < k) {
+                if (row_pair0 + 4 * q < k && jg + 8 <= m) {
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) {
+                        const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), rk);
+                        box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
+                        box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
+                    }
+                } else if (row_pair0 + 4 * q < k) {
                     // pixels past m (last K step only) are drawn and then zeroed
 #pragma unroll
                     for (int p = 0; p < 8; ++p) {
-                        const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), key);
+                        const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), rk);
                         box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
                         box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
                         const bool in = (jg + p) < m;

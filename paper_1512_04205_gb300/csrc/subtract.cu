@@ -299,9 +299,8 @@ subtract_kernel(const uint8_t* __restrict__ D, int64_t m, int n, int64_t ldd,
 // ring of shared-memory stages with 2-D tensor loads (out-of-range pixels and
 // frames read as zero), so 90 KB per SM are in flight independently of the
 // consumers' registers.  Consumer warp w owns pixels 64w .. 64w + 63 of
-// the CTA tile, lane l the two adjacent pixels 2l, 2l + 1; the two
-// per-sub-position ballots are interleaved into the mask words (bit
-// 2(l mod 16) + e of word l/16 of the warp's two).  Waits are bounded: after
+// the CTA tile, lane l the pixels 64w + l and 64w + l + 32, so each of the
+// two ballots of a frame is one mask word.  Waits are bounded: after
 // 2 s the kernel records CDMD_ERR_TIMEOUT, stops, and waits (again bounded)
 // for its own loads in flight before it exits.
 constexpr int kTmaPxl = 2;                          // adjacent pixels per lane
@@ -313,17 +312,10 @@ constexpr int kTmaTile = kTmaWarpPx * kTmaConsumers;   // pixels per CTA tile (9
 constexpr int kTmaBox = 192;                        // pixels per tensor load (3 warps; box width <= 256)
 static_assert(kTmaTile % kTmaBox == 0 && kTmaBox % kTmaWarpPx == 0 && kTmaTile % 32 == 0, "tile layout");
 static_assert(kTmaBox % 16 == 0, "tensor-load x offsets must be multiples of 16 bytes");
+static_assert(kTmaPxl == 2, "a lane owns pixels l and l + 32 of its warp's 64");
 constexpr int kTmaStages = 6;
 constexpr int kChunkBytes = kTmaFB * kTmaTile;
 
-__device__ __forceinline__ uint32_t spread2(uint32_t b) {   // bit i -> bit 2i (i < 16)
-    uint32_t x = b & 0xFFFFu;
-    x = (x | (x << 8)) & 0x00FF00FFu;
-    x = (x | (x << 4)) & 0x0F0F0F0Fu;
-    x = (x | (x << 2)) & 0x33333333u;
-    x = (x | (x << 1)) & 0x55555555u;
-    return x;
-}
 
 __host__ __device__ inline size_t tma_ls_offset() { return static_cast<size_t>(kTmaStages) * kChunkBytes; }
 __host__ __device__ inline size_t tma_bar_offset(int n, int nc) {
@@ -343,11 +335,13 @@ __device__ __forceinline__ void tma_consume(const uint8_t* stages, uint64_t* ful
                                             int64_t words_per_frame, float* __restrict__ bg_out, int warp, int lane) {
     for (int64_t ti = 0; ti < my_tiles; ++ti) {
         const int64_t tile = tile0 + ti * tstride;
-        const int64_t j0 = tile * kTmaTile + warp * kTmaWarpPx + kTmaPxl * lane;
+        // lane l owns pixels j0 + l and j0 + l + 32 of the warp's 64, so each
+        // ballot is one mask word as it stands
+        const int64_t j0 = tile * kTmaTile + warp * kTmaWarpPx + lane;
         float2 a[kTmaPxl][NT];
 #pragma unroll
         for (int e = 0; e < kTmaPxl; ++e) {
-            const int64_t j = j0 + e;
+            const int64_t j = j0 + 32 * e;
 #pragma unroll
             for (int c = 0; c < NT; ++c) {
                 float2 v = make_float2(0.f, 0.f);
@@ -379,33 +373,36 @@ __device__ __forceinline__ void tma_consume(const uint8_t* stages, uint64_t* ful
             if (!tc::mbar_wait(&full[s], static_cast<uint32_t>(g / kTmaStages) & 1u, abort, status)) return;
             constexpr int kWarpsPerBox = kTmaBox / kTmaWarpPx;
             const uint8_t* buf = stages + static_cast<size_t>(s) * kChunkBytes +
-                                 (warp / kWarpsPerBox) * (kTmaFB * kTmaBox) + (warp % kWarpsPerBox) * kTmaWarpPx +
-                                 kTmaPxl * lane;
+                                 (warp / kWarpsPerBox) * (kTmaFB * kTmaBox) + (warp % kWarpsPerBox) * kTmaWarpPx + lane;
             const int t0 = ch * kTmaFB;
 #pragma unroll 2
             for (int f = 0; f < kTmaFB; ++f) {
                 const int t = t0 + f;
                 if (t >= n) break;
-                const uint32_t xw = *reinterpret_cast<const uint16_t*>(buf + f * kTmaBox);
                 const float2* lt = Ls + t * LSTRIDE;
                 uint32_t bal[kTmaPxl];
 #pragma unroll
                 for (int e = 0; e < kTmaPxl; ++e) {
-                    const int64_t j = j0 + e;
-                    const float x = static_cast<float>((xw >> (8 * e)) & 0xFFu);
+                    const int64_t j = j0 + 32 * e;
+                    // the byte as a float: 2^23 + b built from the bits, minus 2^23 (exact)
+                    const uint32_t b = buf[f * kTmaBox + 32 * e];
+                    const float x = __uint_as_float(0x4B000000u | b) - 8388608.0f;
                     bool bit;
                     float bg = 0.0f;
                     if (MODE == CDMD_BG_STATIC) {
                         bg = bg_static[e];
                         bit = fabsf(x - bg) > tau;
                     } else if (REAL) {
-                        float zr = 0.f;
+                        // two partial sums (even / odd terms) halve the FMA dependency chain
+                        float z0 = 0.f, z1 = 0.f;
 #pragma unroll
                         for (int c = 0; c < NT; ++c) {
                             const float2 l = lt[c];
-                            zr = fmaf(a[e][c].x, l.x, zr);
-                            zr = fmaf(-a[e][c].y, l.y, zr);
+                            float& z = (c & 1) ? z1 : z0;
+                            z = fmaf(a[e][c].x, l.x, z);
+                            z = fmaf(-a[e][c].y, l.y, z);
                         }
+                        const float zr = z0 + z1;
                         bg = (MODE == CDMD_BG_REAL) ? zr : fabsf(zr);
                         bit = fabsf(x - bg) > tau;
                     } else {
@@ -435,8 +432,7 @@ __device__ __forceinline__ void tma_consume(const uint8_t* stages, uint64_t* ful
                     bal[e] = __ballot_sync(0xffffffffu, bit);
                 }
                 if (lane < kTmaPxl) {
-                    const int sh = 16 * lane;
-                    const uint32_t w = spread2(bal[0] >> sh) | (spread2(bal[1] >> sh) << 1);
+                    const uint32_t w = (lane == 0) ? bal[0] : bal[1];
                     const int64_t wi = tile * (kTmaTile / 32) + warp * kTmaPxl + lane;
                     if (wi < words_per_frame) mask[static_cast<int64_t>(t) * words_per_frame + wi] = w;
                 }
