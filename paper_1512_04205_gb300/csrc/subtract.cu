@@ -375,11 +375,26 @@ __device__ __forceinline__ void tma_consume(const uint8_t* stages, uint64_t* ful
             const uint8_t* buf = stages + static_cast<size_t>(s) * kChunkBytes +
                                  (warp / kWarpsPerBox) * (kTmaFB * kTmaBox) + (warp % kWarpsPerBox) * kTmaWarpPx + lane;
             const int t0 = ch * kTmaFB;
-#pragma unroll 2
+            // the chunk's 16 frames x 2 mask words: lane 2f + e keeps word e
+            // of frame f and every lane stores one word after the chunk
+            static_assert(2 * kTmaFB == 32 && kTmaPxl == 2, "one mask word per lane per chunk");
+            uint32_t keep = 0;
+#pragma unroll 4
             for (int f = 0; f < kTmaFB; ++f) {
                 const int t = t0 + f;
                 if (t >= n) break;
+                // this frame's lambda^t row, two terms per 16-byte load (rows
+                // start 16-byte aligned: LSTRIDE is even)
+                static_assert(LSTRIDE % 2 == 0, "lambda^t rows must hold an even number of columns");
                 const float2* lt = Ls + t * LSTRIDE;
+                float2 lv[NT];
+#pragma unroll
+                for (int c = 0; c + 1 < NT; c += 2) {
+                    const float4 q = *reinterpret_cast<const float4*>(lt + c);
+                    lv[c] = make_float2(q.x, q.y);
+                    lv[c + 1] = make_float2(q.z, q.w);
+                }
+                if (NT & 1) lv[NT - 1] = lt[NT - 1];
                 uint32_t bal[kTmaPxl];
 #pragma unroll
                 for (int e = 0; e < kTmaPxl; ++e) {
@@ -397,7 +412,7 @@ __device__ __forceinline__ void tma_consume(const uint8_t* stages, uint64_t* ful
                         float z0 = 0.f, z1 = 0.f;
 #pragma unroll
                         for (int c = 0; c < NT; ++c) {
-                            const float2 l = lt[c];
+                            const float2 l = lv[c];
                             float& z = (c & 1) ? z1 : z0;
                             z = fmaf(a[e][c].x, l.x, z);
                             z = fmaf(-a[e][c].y, l.y, z);
@@ -409,7 +424,7 @@ __device__ __forceinline__ void tma_consume(const uint8_t* stages, uint64_t* ful
                         float zr = 0.f, zi = 0.f;
 #pragma unroll
                         for (int c = 0; c < NT; ++c) {
-                            const float2 l = lt[c];
+                            const float2 l = lv[c];
                             zr = fmaf(a[e][c].x, l.x, zr);
                             zr = fmaf(-a[e][c].y, l.y, zr);
                             zi = fmaf(a[e][c].x, l.y, zi);
@@ -431,11 +446,13 @@ __device__ __forceinline__ void tma_consume(const uint8_t* stages, uint64_t* ful
                     if (bg_out != nullptr && j < m) bg_out[static_cast<int64_t>(t) * m + j] = bg;
                     bal[e] = __ballot_sync(0xffffffffu, bit);
                 }
-                if (lane < kTmaPxl) {
-                    const uint32_t w = (lane == 0) ? bal[0] : bal[1];
-                    const int64_t wi = tile * (kTmaTile / 32) + warp * kTmaPxl + lane;
-                    if (wi < words_per_frame) mask[static_cast<int64_t>(t) * words_per_frame + wi] = w;
-                }
+                if (lane == 2 * f) keep = bal[0];
+                if (lane == 2 * f + 1) keep = bal[1];
+            }
+            {
+                const int t = t0 + (lane >> 1);
+                const int64_t wi = tile * (kTmaTile / 32) + warp * kTmaPxl + (lane & 1);
+                if (t < n && wi < words_per_frame) mask[static_cast<int64_t>(t) * words_per_frame + wi] = keep;
             }
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&empty[s]);
