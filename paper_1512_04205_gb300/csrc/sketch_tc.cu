@@ -65,22 +65,28 @@ constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxFrames = 256;             // frames per launch: MMA N and TMA box height limits
 
 // Fast Box-Muller pair (MUFU lg2 / sqrt / sin / cos), same definition as the
-// accurate form: U(w) = (w + 1/2) 2^-32 for the radius; the angle 2 pi U(wb)
-// is taken from the top 23 bits of wb, f = (wb >> 9 + 1/2) 2^-23 built as a
-// float in [1, 2) from the bits minus 1 (no integer conversion), and handed
-// to the hardware sine / cosine whole.  The angle differs from 2 pi U(wb) by
-// at most pi 2^-23, and the MUFU sine / cosine by about 2^-21 absolute, far
-// below the BF16 hi + lo split of C.
+// accurate form: U(w) = (w + 1/2) 2^-32, angle split into quarter turns: the
+// top two bits of wb pick the quadrant and the hardware sine / cosine see only
+// the remainder (pi/2) f, f in (0, 1) from the next 23 bits (a float in
+// [1, 2) built from the bits, minus 1, plus half a step; no I2F).  The
+// quadrant map sends the approximation error of cos and sin to +c, -s, -c,
+// +s in turn, so its mean cancels; handed the whole angle, the hardware
+// functions leave a bias of ~5e-7 per draw that a sketch over 2 M pixels of
+// mean ~128 grey levels turns into ~1e-4 relative.
 __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float& zc, float& zs) {
     const float u = fmaf(__uint2float_rn(wa), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float x = -1.3862943611198906f * __log2f(u);   // -2 ln u
     float rad;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rad) : "f"(x));
-    const float f = __uint_as_float(0x3F800000u | (wb >> 9)) - (1.0f - 5.9604645e-08f);
+    const float f = __uint_as_float(0x3F800000u | ((wb >> 7) & 0x7FFFFFu)) - (1.0f - 5.9604645e-08f);
     float s, c;
-    __sincosf(6.283185307179586f * f, &s, &c);
-    zc = rad * c;
-    zs = rad * s;
+    __sincosf(1.5707963267948966f * f, &s, &c);
+    const uint32_t qt = wb >> 30;
+    float cs = (qt & 1u) ? -s : c;
+    float sn = (qt & 1u) ? c : s;
+    if (qt & 2u) { cs = -cs; sn = -sn; }
+    zc = rad * cs;
+    zs = rad * sn;
 }
 
 struct SmemLayout {
