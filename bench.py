@@ -1,19 +1,23 @@
 #!/usr/bin/env python
 """Throughput benchmark: compressed-DMD background subtraction, frames/s.
 
-Workload: one seeded synthetic 1920x1080 grayscale clip of 200 frames per GPU
+Workload: seeded synthetic 1920x1080 grayscale clips of 200 frames
 (textured low-rank background, 3 moving rectangles, +-10 % illumination
 drift, noise sigma 3; k = 1000 Gaussian measurements drawn in-kernel from
-Philox, target rank r = 20, K = 10 background modes, threshold 25 grey).
-A step is one pass of the whole hot path over the clip:
-    sketch -> decompose -> lift (selected modes) -> subtract + bit-pack.
+Philox, target rank r = 20, K = 10 background modes, threshold 25 grey), two
+per GPU (the second rendered on the device), all seen through one
+measurement matrix C (one camera, one sensing matrix, video processed window
+by window).  A step is one pass of the whole hot path over the two clips:
+    sketch of both (one C draw feeds both) -> per clip: decompose -> lift
+    (selected modes) -> subtract + bit-pack.
 value = frames processed by all ranks / wall time of the timed steps (max over
-ranks); the clip (415 MB) is resident in HBM and larger than L2, so no
-flush is needed between steps.  Each pass is timed with CUDA events on the
+ranks); the clips (415 MB each) are resident in HBM and larger than L2, so
+no flush is needed between steps.  Each pass is timed with CUDA events on the
 launching stream; the sketch is the dominant kernel and carries the roofline.
+--clips-per-step 1 times the one-clip step (no sharing of C).
 
-e2e: the same metric through cdmd_run_host with pinned host buffers (the
-clip copied in and the mask copied out every step).
+e2e: the same metric through cdmd_run_host_shared with pinned host buffers
+(both clips copied in and both masks copied out every step).
 cpu_baseline / --impl reference: the FP64 oracle on the host cores, on a
 bounded pixel sample of the clip, scaled to the full frame.
 
@@ -35,7 +39,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(width=1920, height=1080, n=200, k=1000, r=20, K=10, tau=25.0, drift=0.1, clip_seed=2024,
-                c_seed=0x5EED1080)
+                c_seed=0x5EED1080, clips_per_step=2)
 METRIC = "cDMD 1080p frames/s"
 UNIT = "frames/s"
 
@@ -76,15 +80,16 @@ def fmeasure(pred, truth):
     return 2 * prec * rec / (prec + rec) if prec + rec > 0 else 0.0
 
 
-def launches_per_step(selector, K):
-    """Kernels one pipeline step launches: sketch 2 (tiles + fixed-order
-    reduce); decompose 15 (Gram 2, tridiagonalisation 1, eigenpairs 1,
+def launches_per_step(selector, K, clips=1):
+    """Kernels one pipeline step over `clips` clips launches: sketch 2 per
+    launch of one clip or a pair sharing C (tiles + fixed-order reduce); per
+    clip: decompose 15 (Gram 2, tridiagonalisation 1, eigenpairs 1,
     orthonormalise 1, back-transform 1, B 1, A~ 1, eig FP32 1, Newton 1,
     FP64 QR fallback 1, order 1, G 1, Gram-form H 1, selection 1) + 2 for the
     learned selection (scoring, least squares on its picks, then the OMP
     launch that exits at once unless the picks were rejected); lift one per
     16 modes; subtract 2 (lambda^t table + pass)."""
-    return 2 + 15 + (2 if selector == "mlp" else 0) + (K + 15) // 16 + 2
+    return 2 * ((clips + 1) // 2) + clips * (15 + (2 if selector == "mlp" else 0) + (K + 15) // 16 + 2)
 
 
 def algorithmic_counts():
@@ -350,22 +355,31 @@ def run_ours(args, rank, world, local_rank):
     main_stream = torch.cuda.current_stream()
     model = torch.from_numpy(SEL.load_model()[0]).to(dev) if args.selector == "mlp" else None
 
+    cps = args.clips_per_step
+
     class Lane:
-        """One clip in flight: its own context (workspace), stream and outputs."""
+        """One step in flight: its own context (workspace), stream and the
+        outputs of each of its clips."""
 
         def __init__(self, stream):
             self.ctx = C.Context(local_rank)
             self.stream = stream
-            self.DY = torch.empty((n, k), dtype=torch.float64, device=dev)
-            self.dec = C.decompose_outputs(n, k, r, K, dev)
-            self.Phi = torch.empty((m, K, 2), dtype=torch.float32, device=dev)
-            self.mask = torch.empty((n, (m + 31) // 32), dtype=torch.int32, device=dev)
+            self.DY = [torch.empty((n, k), dtype=torch.float64, device=dev) for _ in range(cps)]
+            self.dec = [C.decompose_outputs(n, k, r, K, dev) for _ in range(cps)]
+            self.Phi = [torch.empty((m, K, 2), dtype=torch.float32, device=dev) for _ in range(cps)]
+            self.mask = [torch.empty((n, (m + 31) // 32), dtype=torch.int32, device=dev) for _ in range(cps)]
             if model is not None:
                 C.cdmd_selector_load(self.ctx, model, stream=stream)
 
     lanes = [Lane(main_stream)] + [Lane(torch.cuda.Stream(device=dev)) for _ in range(max(0, args.inflight - 1))]
     ctx = lanes[0].ctx
-    mask = lanes[0].mask
+    mask = lanes[0].mask[0]
+    # the step's other clips: same size, own content, rendered on the device
+    Ds = [D]
+    for i in range(1, cps):
+        sd = clip_seed(rank) + 1000 * i
+        Ds.append(C.cdmd_synth_clip(ctx, videogen.clip_spec(w["width"], w["height"], n, sd, drift=w["drift"]), sd))
+    torch.cuda.synchronize()
 
     def step(prec, selector, events=None, lane=None):
         L = lane or lanes[0]
@@ -373,17 +387,23 @@ def run_ours(args, rank, world, local_rank):
         with torch.cuda.stream(st):
             if events is not None:
                 events[0].record(st)
-            C.cdmd_sketch(L.ctx, D, k, w["c_seed"], prec=prec, DY=L.DY)
+            if cps == 1:
+                C.cdmd_sketch(L.ctx, D, k, w["c_seed"], prec=prec, DY=L.DY[0])
+            else:
+                C.cdmd_sketch_shared(L.ctx, Ds, k, w["c_seed"], prec=prec, DYs=L.DY)
             if events is not None:
                 events[1].record(st)
-            C.cdmd_decompose(L.ctx, L.DY, r, K, selector=selector, out=L.dec)
+            for i in range(cps):
+                C.cdmd_decompose(L.ctx, L.DY[i], r, K, selector=selector, out=L.dec[i])
             if events is not None:
                 events[2].record(st)
-            C.cdmd_lift(L.ctx, D, L.dec["G"], cols=L.dec["sel"], ncols=K, prec=prec, Phi=L.Phi)
+            for i in range(cps):
+                C.cdmd_lift(L.ctx, Ds[i], L.dec[i]["G"], cols=L.dec[i]["sel"], ncols=K, prec=prec, Phi=L.Phi[i])
             if events is not None:
                 events[3].record(st)
-            C.cdmd_subtract(L.ctx, D, L.Phi, L.dec["beta"], L.dec["lam"], w["tau"], cols=L.dec["sel"],
-                            mask=L.mask)
+            for i in range(cps):
+                C.cdmd_subtract(L.ctx, Ds[i], L.Phi[i], L.dec[i]["beta"], L.dec[i]["lam"], w["tau"],
+                                cols=L.dec[i]["sel"], mask=L.mask[i])
             if events is not None:
                 events[4].record(st)
     stream = main_stream
@@ -412,7 +432,7 @@ def run_ours(args, rank, world, local_rank):
         clocks = sampler.stop() if sampler else None
         C.cdmd_status_sync(ctx)
         total_ms = start.elapsed_time(end)
-        passes = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs]).mean(axis=0)
+        passes = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs]).mean(axis=0) / cps
         total_ms = max_over_ranks(total_ms, dist, dev)
         barrier()
         return total_ms, passes, clocks
@@ -473,8 +493,9 @@ def run_ours(args, rank, world, local_rank):
         # others' compute; every step copies the clip in and the mask out
         import threading
         params = C.make_params(k, r, K, w["tau"], seed=w["c_seed"], prec=args.prec, selector=args.selector)
-        host = torch.from_numpy(clip.frames).pin_memory()
-        hmasks = [torch.empty((n, (m + 31) // 32), dtype=torch.int32).pin_memory() for _ in lanes]
+        hosts = [torch.from_numpy(clip.frames).pin_memory()] + [Dx.cpu().pin_memory() for Dx in Ds[1:]]
+        hmasks = [[torch.empty((n, (m + 31) // 32), dtype=torch.int32).pin_memory() for _ in range(cps)]
+                  for _ in lanes]
         for L in lanes:
             C.cdmd_set_sm_limit(L.ctx, args.sm_limit if len(lanes) > 1 else 0)
         errors = []
@@ -482,7 +503,12 @@ def run_ours(args, rank, world, local_rank):
         def worker(i, count):
             try:
                 for _ in range(count):
-                    C.cdmd_run_host(lanes[i].ctx, host, params, mask_host=hmasks[i], stream=lanes[i].stream)
+                    if cps == 1:
+                        C.cdmd_run_host(lanes[i].ctx, hosts[0], params, mask_host=hmasks[i][0],
+                                        stream=lanes[i].stream)
+                    else:
+                        C.cdmd_run_host_shared(lanes[i].ctx, hosts, params, mask_hosts=hmasks[i],
+                                               stream=lanes[i].stream)
             except Exception as e:          # reported after the join
                 errors.append(e)
 
@@ -505,9 +531,11 @@ def run_ours(args, rank, world, local_rank):
         for L in lanes:
             C.cdmd_set_sm_limit(L.ctx, 0)
         dt = max_over_ranks(dt, dist, dev)
-        e2e = {"value": world * n * e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(m * n),
-               "d2h_bytes_per_step": int(n * ((m + 31) // 32) * 4), "steps": e2e_steps,
-               "host_threads": len(lanes), "api": "cdmd_run_host (pinned host video in, host mask out)"}
+        e2e = {"value": world * cps * n * e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(cps * m * n),
+               "d2h_bytes_per_step": int(cps * n * ((m + 31) // 32) * 4), "steps": e2e_steps,
+               "clips_per_step": cps, "host_threads": len(lanes),
+               "api": ("cdmd_run_host" if cps == 1 else "cdmd_run_host_shared") +
+                      " (pinned host videos in, host masks out)"}
 
     batch_line = run_batch_measure(C, SEL, torch, dev, args, model) if args.batch else None
 
@@ -518,8 +546,8 @@ def run_ours(args, rank, world, local_rank):
 
     head = results["head"]
     steps = args.steps
-    latency_value = job_throughput(n * steps, world, head["total_ms"] * 1e-3)
-    value = job_throughput(n * steps, world, piped_ms * 1e-3) if piped_ms is not None else latency_value
+    latency_value = job_throughput(cps * n * steps, world, head["total_ms"] * 1e-3)
+    value = job_throughput(cps * n * steps, world, piped_ms * 1e-3) if piped_ms is not None else latency_value
     counts = algorithmic_counts()
     peaks, peak_src = load_peaks()
     sketch_ms = float(head["passes"][0])
@@ -546,18 +574,21 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16" if args.prec == "bf16x2" else "f32", "data": "synthetic",
             "config": {"workload": workload_name(args.prec, args.selector), "selector": args.selector, "m": m, "n": n, "k": k, "r": r, "K": K,
-                       "tau": w["tau"], "measurement": "gaussian (Philox4x32-10, in-kernel)",
+                       "tau": w["tau"], "clips_per_step": cps,
+                       "measurement": ("gaussian (Philox4x32-10, in-kernel); one C for all clips"
+                                       + (", one draw of C feeds both clips of a step" if cps > 1 else "")),
                        "precision": ("sketch+lift BF16 hi+lo on tcgen05, FP32 accumulation; FP64 small solves"
                                      if args.prec == "bf16x2" else "sketch+lift FP32 FMA; FP64 small solves"),
-                       "l2": f"clip {m * n / 1e6:.0f} MB vs 129 MB L2 (no flush)",
-                       "parallelism": f"clips x{world} (one per GPU), {len(lanes)} in flight per GPU (one stream each)",
+                       "l2": f"clip {m * n / 1e6:.0f} MB each vs 129 MB L2 (no flush)",
+                       "parallelism": (f"clips x{world * cps} ({cps} per GPU per step), {len(lanes)} steps in flight "
+                                       "per GPU (one stream each)"),
                        "sm_limit": args.sm_limit},
-            "single_stream": {"value": latency_value, "ms_per_clip": head["total_ms"] / steps},
+            "single_stream": {"value": latency_value, "ms_per_clip": head["total_ms"] / (steps * cps)},
             "per_pass_ms": per_pass,
             "pass_roofline": {"lift_gbs": lift_gbs, "lift_frac_hbm": lift_gbs / hbm, "subtract_gbs": sub_gbs,
                               "subtract_frac_hbm": sub_gbs / hbm, "hbm_peak_gbs": hbm},
             "roofline": roof,
-            "gpu_launches": launches_per_step(args.selector, K) * steps,
+            "gpu_launches": launches_per_step(args.selector, K, cps) * steps,
             "e2e": e2e}
     if piped_clocks is not None:
         line["clocks"] = piped_clocks
@@ -571,7 +602,7 @@ def run_ours(args, rank, world, local_rank):
         plain = results["plain"]
         agree = plain["mask"] == head["mask"]
         line["accuracy"]["plain_fp32_omp_fmeasure_vs_truth"] = fmeasure(plain["mask"], truth)
-        line["plain_fp32"] = {"value": world * n * steps / (plain["total_ms"] * 1e-3),
+        line["plain_fp32"] = {"value": world * cps * n * steps / (plain["total_ms"] * 1e-3),
                               "ms_per_step": plain["total_ms"] / steps,
                               "per_pass_ms": {nm: float(v) for nm, v in
                                               zip(["sketch", "decompose", "lift", "subtract"], plain["passes"])},
@@ -611,7 +642,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--inflight", type=int, default=8, help="clips in flight per GPU (streams)")
+    ap.add_argument("--inflight", type=int, default=8, help="steps in flight per GPU (streams)")
+    ap.add_argument("--clips-per-step", type=int, choices=[1, 2], default=WORKLOAD["clips_per_step"],
+                    help="clips per step, all under one C (2: one draw of C feeds both)")
     ap.add_argument("--batch", action="store_true",
                     help="also measure a batch of 64 clips of mixed size (grouped launches, graph, autotuner)")
     ap.add_argument("--size", default=None,

@@ -187,6 +187,24 @@ cdmd_status cdmd_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64
                         cdmd_ctype ctype, int k, uint64_t seed, cdmd_prec prec,
                         double* DY, void* stream);
 
+/* Several clips sketched with one measurement matrix (Algorithm 1 steps 2-3
+ * for each clip, one C): DY[i] = C D[i] for i < nclips, where every clip has
+ * the same pixel count m and C is drawn from the same (ctype, k, seed) as
+ * cdmd_sketch draws it.  This is the case of one camera (one sensing matrix)
+ * whose video is processed window by window.  With prec = CDMD_PREC_BF16X2
+ * and a Gaussian C, consecutive clips of <= 256 frames (pairs whose frame
+ * counts fit one CTA's shared memory, about n0 + n1 <= 430) are sketched
+ * together: each entry of C drawn feeds both clips, halving the generator's
+ * work per clip; the others, and every other precision or C, go one by one
+ * as cdmd_sketch would.  D[i], n[i], ldd[i], DY[i] as for cdmd_sketch; the
+ * four arrays are host arrays of nclips entries (D[i], DY[i] device
+ * pointers).  Results agree with cdmd_sketch's up to the rounding order of
+ * the split partial sums.  CDMD_ERR_INVALID_ARG (naming the clip) for
+ * nclips < 1 or any argument cdmd_sketch would reject. */
+cdmd_status cdmd_sketch_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m,
+                               const int* n, const int64_t* ldd, cdmd_ctype ctype, int k,
+                               uint64_t seed, cdmd_prec prec, double* const* DY, void* stream);
+
 /* Sparse or single-pixel C applied as a gather (one pass over D; exact
  * integer sums).  meas must have been filled by cdmd_measure_build for the
  * same m.  DY as for cdmd_sketch with k = meas->k. */
@@ -266,6 +284,25 @@ cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t 
  * stream and returns the numerical status as cdmd_status_sync does. */
 cdmd_status cdmd_run_host(cdmd_ctx* ctx, const uint8_t* D_host, int64_t m, int n,
                           const cdmd_params* p, uint32_t* mask_host, void* stream);
+
+/* cdmd_run for 1..8 clips of the same pixel count and parameters (one
+ * measurement matrix): the sketches go through cdmd_sketch_shared, then each
+ * clip's small solves, lift and subtract run in order on `stream`, reusing
+ * the context's workspace (cdmd_workspace_views then shows the last clip).
+ * D, n, ldd and mask are host arrays of nclips entries; each clip as for
+ * cdmd_run.  CDMD_ERR_INVALID_ARG (naming the clip) as cdmd_run would, or for
+ * nclips outside [1, 8]. */
+cdmd_status cdmd_run_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m,
+                            const int* n, const int64_t* ldd, const cdmd_params* p,
+                            uint32_t* const* mask, void* stream);
+
+/* cdmd_run_shared on host memory: copies each D_host[i] (m x n[i], ldd = m)
+ * to the device, runs cdmd_run_shared and copies each mask back to
+ * mask_host[i], all on `stream`; then synchronises the stream and returns the
+ * numerical status as cdmd_status_sync does. */
+cdmd_status cdmd_run_host_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D_host,
+                                 int64_t m, const int* n, const cdmd_params* p,
+                                 uint32_t* const* mask_host, void* stream);
 
 /* Device pointers to the intermediates of the last cdmd_run on ctx (any
  * output pointer may be NULL).  Valid until the next call on the context. */

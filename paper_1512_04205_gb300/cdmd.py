@@ -38,7 +38,7 @@ EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_strin
             "cdmd_selector_features", "cdmd_selector_fallbacks", "cdmd_mlp_forward", "cdmd_mlp_grad",
             "cdmd_mlp_train_step", "cdmd_synth_clip", "cdmd_selector_relabel", "cdmd_batch_create",
             "cdmd_batch_run", "cdmd_batch_status_sync", "cdmd_batch_views", "cdmd_batch_tuning",
-            "cdmd_batch_destroy", "cdmd_copy"]
+            "cdmd_batch_destroy", "cdmd_copy", "cdmd_sketch_shared", "cdmd_run_shared", "cdmd_run_host_shared"]
 BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_GROUPED = 1, 2, 4
 
 
@@ -104,6 +104,10 @@ def load_library(path=LIB_PATH):
                           ctypes.c_int, vp, vp, vp],
         "cdmd_run": [vp, vp, i64, ctypes.c_int, i64, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_run_host": [vp, vp, i64, ctypes.c_int, ctypes.POINTER(cdmd_params), vp, vp],
+        "cdmd_sketch_shared": [vp, ctypes.c_int, vp, i64, vp, vp, ctypes.c_int, ctypes.c_int, u64, ctypes.c_int, vp,
+                               vp],
+        "cdmd_run_shared": [vp, ctypes.c_int, vp, i64, vp, vp, ctypes.POINTER(cdmd_params), vp, vp],
+        "cdmd_run_host_shared": [vp, ctypes.c_int, vp, i64, vp, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_workspace_views": [vp] + [ctypes.POINTER(vp)] * 8,
         "cdmd_sketch_noalloc": [vp, i64, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, u64, vp, vp],
         "cdmd_selector_load": [vp, vp, vp],
@@ -201,6 +205,34 @@ def cdmd_sketch(ctx, D, k, seed, ctype="gaussian", prec="fp32", DY=None, stream=
     _check(ctx.lib.cdmd_sketch(ctx.handle, _ptr(D), m, n, ldd, CTYPES[ctype], int(k), int(seed) & (2**64 - 1),
                                PRECS[prec], _ptr(DY), _stream(stream)))
     return DY
+
+
+def _arrays(tensors):
+    """Host arrays of device pointers, frame counts and row strides of a
+    list of videos (n, m) of one pixel count."""
+    vids = [_video(D) for D in tensors]
+    ms = {v[1] for v in vids}
+    if len(ms) != 1:
+        raise ValueError("every clip must have the same pixel count")
+    cnt = len(tensors)
+    ptrs = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in tensors])
+    ns = (ctypes.c_int * cnt)(*[v[0] for v in vids])
+    ldds = (ctypes.c_int64 * cnt)(*[v[2] for v in vids])
+    return ptrs, ns, ldds, ms.pop()
+
+
+def cdmd_sketch_shared(ctx, Ds, k, seed, ctype="gaussian", prec="fp32", DYs=None, stream=None):
+    """Pass (a) for several clips of one pixel count with one C: returns
+    [DY_i (n_i, k) float64]; with prec="bf16x2" consecutive clips share the
+    generator two at a time."""
+    import torch
+    ptrs, ns, ldds, m = _arrays(Ds)
+    if DYs is None:
+        DYs = [torch.empty((D.shape[0], k), dtype=torch.float64, device=D.device) for D in Ds]
+    out = (ctypes.c_void_p * len(Ds))(*[t.data_ptr() for t in DYs])
+    _check(ctx.lib.cdmd_sketch_shared(ctx.handle, len(Ds), ptrs, m, ns, ldds, CTYPES[ctype], int(k),
+                                      int(seed) & (2**64 - 1), PRECS[prec], out, _stream(stream)))
+    return DYs
 
 
 def cdmd_sketch_noalloc(D, k, seed, ctype="gaussian", DY=None, stream=None):
@@ -352,6 +384,44 @@ def cdmd_run_host(ctx, D_host, params, mask_host=None, stream=None):
     _check(ctx.lib.cdmd_run_host(ctx.handle, _ptr(D_host), m, n, ctypes.byref(params), _ptr(mask_host),
                                  _stream(stream)))
     return mask_host
+
+
+def cdmd_run_shared(ctx, Ds, params, masks=None, stream=None):
+    """Whole pipeline on 1..8 device videos of one pixel count with one C;
+    returns their masks."""
+    import torch
+    ptrs, ns, ldds, m = _arrays(Ds)
+    if masks is None:
+        masks = [torch.empty((D.shape[0], (m + 31) // 32), dtype=torch.int32, device=D.device) for D in Ds]
+    out = (ctypes.c_void_p * len(Ds))(*[t.data_ptr() for t in masks])
+    _check(ctx.lib.cdmd_run_shared(ctx.handle, len(Ds), ptrs, m, ns, ldds, ctypes.byref(params), out,
+                                   _stream(stream)))
+    return masks
+
+
+def cdmd_run_host_shared(ctx, D_hosts, params, mask_hosts=None, stream=None):
+    """cdmd_run_shared on host videos (n_i, m) uint8 (pinned for full copy
+    bandwidth): copies in, runs, copies the masks out and synchronises."""
+    import torch
+    hs = []
+    for D in D_hosts:
+        if isinstance(D, np.ndarray):
+            D = torch.from_numpy(np.ascontiguousarray(D))
+        if D.dtype != torch.uint8 or D.dim() != 2 or not D.is_contiguous() or D.is_cuda:
+            raise ValueError("each host video must be a contiguous host uint8 tensor (n, m)")
+        hs.append(D)
+    m = hs[0].shape[1]
+    if any(D.shape[1] != m for D in hs):
+        raise ValueError("every clip must have the same pixel count")
+    if mask_hosts is None:
+        mask_hosts = [torch.empty((D.shape[0], (m + 31) // 32), dtype=torch.int32, pin_memory=D.is_pinned())
+                      for D in hs]
+    cnt = len(hs)
+    ptrs = (ctypes.c_void_p * cnt)(*[D.data_ptr() for D in hs])
+    ns = (ctypes.c_int * cnt)(*[D.shape[0] for D in hs])
+    out = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in mask_hosts])
+    _check(ctx.lib.cdmd_run_host_shared(ctx.handle, cnt, ptrs, m, ns, ctypes.byref(params), out, _stream(stream)))
+    return mask_hosts
 
 
 def cdmd_workspace_views(ctx):

@@ -74,6 +74,15 @@ static cdmd_status check_video(const uint8_t* D, int64_t m, int n, int64_t ldd) 
     return CDMD_OK;
 }
 
+// Prefix the current error message with the clip it concerns.
+static cdmd_status fail_clip(cdmd_status st, int clip) {
+    char msg[sizeof(g_last_error)];
+    snprintf(msg, sizeof(msg), "%s", g_last_error);
+    return fail(st, "clip %d: %s", clip, msg);
+}
+
+constexpr int kMaxSharedRun = 8;   // clips per cdmd_run_shared / cdmd_run_host_shared call
+
 }  // namespace cdmd
 
 using namespace cdmd;
@@ -220,6 +229,34 @@ cdmd_status cdmd_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64
     return fail(CDMD_ERR_INVALID_ARG, "unknown precision %d", static_cast<int>(prec));
 }
 
+cdmd_status cdmd_sketch_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
+                               const int64_t* ldd, cdmd_ctype ctype, int k, uint64_t seed, cdmd_prec prec,
+                               double* const* DY, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(nclips >= 1, "nclips must be >= 1 (got %d)", nclips);
+    CDMD_REQUIRE(D != nullptr && n != nullptr && ldd != nullptr && DY != nullptr, "NULL array argument");
+    for (int i = 0; i < nclips; ++i) {
+        cdmd_status st = check_video(D[i], m, n[i], ldd[i]);
+        if (st != CDMD_OK) return fail_clip(st, i);
+        CDMD_REQUIRE(DY[i] != nullptr && aligned(DY[i], 8), "clip %d: DY is NULL or not 8-byte aligned", i);
+    }
+    CDMD_REQUIRE(k >= 1 && k <= (1 << 20), "k must be in [1, 2^20] (got %d)", k);
+    CDMD_REQUIRE(ctype == CDMD_C_GAUSSIAN || ctype == CDMD_C_RADEMACHER,
+                 "cdmd_sketch_shared generates GAUSSIAN or RADEMACHER C");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == CDMD_PREC_BF16X2 && ctype == CDMD_C_GAUSSIAN)
+        return launch_sketch_tc_shared(ctx, nclips, D, m, n, ldd, k, seed, DY, s);
+    if (prec != CDMD_PREC_FP32 && prec != CDMD_PREC_BF16X2)
+        return fail(CDMD_ERR_INVALID_ARG, "unknown precision %d", static_cast<int>(prec));
+    for (int i = 0; i < nclips; ++i) {
+        cdmd_status st = cdmd_sketch(ctx, D[i], m, n[i], ldd[i], ctype, k, seed, prec, DY[i], stream);
+        if (st != CDMD_OK) return st;
+    }
+    return CDMD_OK;
+}
+
 cdmd_status cdmd_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                                const cdmd_measure* meas, double* DY, void* stream) {
     clear_error();
@@ -298,24 +335,27 @@ cdmd_status cdmd_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int
                            static_cast<cudaStream_t>(stream));
 }
 
-cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const cdmd_params* p,
-                     uint32_t* mask, void* stream) {
-    clear_error();
-    CDMD_REQUIRE(ctx != nullptr && p != nullptr && mask != nullptr, "ctx, params or mask is NULL");
+namespace {
+
+cdmd_status check_run(const uint8_t* D, int64_t m, int n, int64_t ldd, const cdmd_params* p) {
     cdmd_status st = check_video(D, m, n, ldd);
     if (st != CDMD_OK) return st;
     const int k = p->k, r = p->r, K = p->K;
     CDMD_REQUIRE(r >= 1 && r <= 32 && r <= k && r <= n - 1, "r must be in [1, min(32, k, n-1)]");
     CDMD_REQUIRE(K >= 1 && K <= r, "K must be in [1, r]");
-    DeviceGuard g(ctx->device);
+    return CDMD_OK;
+}
+
+// Steps 4-9 of cdmd_run on a sketch DY already in device memory (the
+// context's small-solve and Phi buffers are reused, stream-ordered).
+cdmd_status run_from_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const cdmd_params* p,
+                            double* DY, uint32_t* mask, void* stream) {
+    const int k = p->k, r = p->r, K = p->K;
     const int p1 = n - 1;
     const int ncols = (p->selector == CDMD_SEL_LSTSQ) ? r : K;
     void* v = nullptr;
-    st = ensure_buffer(ctx, BUF_RUN_DY, static_cast<size_t>(k) * n * sizeof(double), &v);
-    if (st != CDMD_OK) return st;
-    double* DY = static_cast<double*>(v);
     const size_t n_small = static_cast<size_t>(r) + 2 * r + 2 * static_cast<size_t>(p1) * r + 2 * r + 8;
-    st = ensure_buffer(ctx, BUF_RUN_SMALL, n_small * sizeof(double) + (r + 8) * sizeof(int32_t), &v);
+    cdmd_status st = ensure_buffer(ctx, BUF_RUN_SMALL, n_small * sizeof(double) + (r + 8) * sizeof(int32_t), &v);
     if (st != CDMD_OK) return st;
     double* sigma = static_cast<double*>(v);
     double* lambda = sigma + r;
@@ -329,8 +369,6 @@ cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t 
     ctx->run_DY = DY; ctx->run_sigma = sigma; ctx->run_lambda = lambda; ctx->run_G = Gm;
     ctx->run_beta = beta; ctx->run_sel = sel; ctx->run_nsel = nsel; ctx->run_Phi = Phi;
 
-    st = cdmd_sketch(ctx, D, m, n, ldd, p->ctype, k, p->seed, p->prec, DY, stream);
-    if (st != CDMD_OK) return st;
     st = cdmd_decompose(ctx, DY, k, n, r, K, p->selector, sigma, lambda, Gm, nullptr, beta, sel, nsel, stream);
     if (st != CDMD_OK) return st;
     // OMP: lift and subtract only the selected modes (sel, -1 padded);
@@ -342,6 +380,53 @@ cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t 
     if (st != CDMD_OK) return st;
     return cdmd_subtract(ctx, D, m, n, ldd, Phi, ncols, cols, beta, lambda, r, p->tau, p->bgmode, mask, nullptr,
                          stream);
+}
+
+}  // namespace
+
+cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const cdmd_params* p,
+                     uint32_t* mask, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && p != nullptr && mask != nullptr, "ctx, params or mask is NULL");
+    cdmd_status st = check_run(D, m, n, ldd, p);
+    if (st != CDMD_OK) return st;
+    DeviceGuard g(ctx->device);
+    void* v = nullptr;
+    st = ensure_buffer(ctx, BUF_RUN_DY, static_cast<size_t>(p->k) * n * sizeof(double), &v);
+    if (st != CDMD_OK) return st;
+    double* DY = static_cast<double*>(v);
+    st = cdmd_sketch(ctx, D, m, n, ldd, p->ctype, p->k, p->seed, p->prec, DY, stream);
+    if (st != CDMD_OK) return st;
+    return run_from_sketch(ctx, D, m, n, ldd, p, DY, mask, stream);
+}
+
+cdmd_status cdmd_run_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
+                            const int64_t* ldd, const cdmd_params* p, uint32_t* const* mask, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && p != nullptr, "ctx or params is NULL");
+    CDMD_REQUIRE(nclips >= 1, "nclips must be >= 1 (got %d)", nclips);
+    CDMD_REQUIRE(D != nullptr && n != nullptr && ldd != nullptr && mask != nullptr, "NULL array argument");
+    size_t off[kMaxSharedRun + 1] = {0};
+    CDMD_REQUIRE(nclips <= kMaxSharedRun, "nclips must be <= %d (got %d)", kMaxSharedRun, nclips);
+    for (int i = 0; i < nclips; ++i) {
+        cdmd_status st = check_run(D[i], m, n[i], ldd[i], p);
+        if (st != CDMD_OK) return fail_clip(st, i);
+        CDMD_REQUIRE(mask[i] != nullptr, "clip %d: mask is NULL", i);
+        off[i + 1] = off[i] + static_cast<size_t>(p->k) * n[i];
+    }
+    DeviceGuard g(ctx->device);
+    void* v = nullptr;
+    cdmd_status st = ensure_buffer(ctx, BUF_RUN_DY, off[nclips] * sizeof(double), &v);
+    if (st != CDMD_OK) return st;
+    double* DYs[kMaxSharedRun];
+    for (int i = 0; i < nclips; ++i) DYs[i] = static_cast<double*>(v) + off[i];
+    st = cdmd_sketch_shared(ctx, nclips, D, m, n, ldd, p->ctype, p->k, p->seed, p->prec, DYs, stream);
+    if (st != CDMD_OK) return st;
+    for (int i = 0; i < nclips; ++i) {
+        st = run_from_sketch(ctx, D[i], m, n[i], ldd[i], p, DYs[i], mask[i], stream);
+        if (st != CDMD_OK) return st;
+    }
+    return CDMD_OK;
 }
 
 cdmd_status cdmd_run_host(cdmd_ctx* ctx, const uint8_t* D_host, int64_t m, int n, const cdmd_params* p,
@@ -365,6 +450,46 @@ cdmd_status cdmd_run_host(cdmd_ctx* ctx, const uint8_t* D_host, int64_t m, int n
     st = cdmd_run(ctx, static_cast<const uint8_t*>(dv), m, n, m, p, static_cast<uint32_t*>(dm), stream);
     if (st != CDMD_OK) return st;
     CDMD_CHECK_CUDA(cudaMemcpyAsync(mask_host, dm, mbytes, cudaMemcpyDeviceToHost, s));
+    return cdmd_status_sync(ctx, stream);
+}
+
+cdmd_status cdmd_run_host_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D_host, int64_t m, const int* n,
+                                 const cdmd_params* p, uint32_t* const* mask_host, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && p != nullptr && D_host != nullptr && n != nullptr && mask_host != nullptr,
+                 "NULL argument");
+    CDMD_REQUIRE(nclips >= 1 && nclips <= kMaxSharedRun, "nclips must be in [1, %d] (got %d)", kMaxSharedRun, nclips);
+    size_t voff[kMaxSharedRun + 1] = {0}, moff[kMaxSharedRun + 1] = {0};
+    const size_t wpf = static_cast<size_t>((m + 31) / 32);
+    for (int i = 0; i < nclips; ++i) {
+        CDMD_REQUIRE(D_host[i] != nullptr && mask_host[i] != nullptr, "clip %d: NULL buffer", i);
+        cdmd_status st = check_video(D_host[i], m, n[i], m);
+        if (st != CDMD_OK) return fail_clip(st, i);
+        voff[i + 1] = voff[i] + (static_cast<size_t>(m) * n[i] + 255) / 256 * 256;
+        moff[i + 1] = moff[i] + wpf * n[i] * sizeof(uint32_t);
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* dv = nullptr;
+    void* dm = nullptr;
+    cdmd_status st = ensure_buffer(ctx, BUF_RUN_VIDEO, voff[nclips], &dv);
+    if (st != CDMD_OK) return st;
+    st = ensure_buffer(ctx, BUF_RUN_MASK, moff[nclips], &dm);
+    if (st != CDMD_OK) return st;
+    const uint8_t* Dd[kMaxSharedRun];
+    uint32_t* Md[kMaxSharedRun];
+    int64_t ldd[kMaxSharedRun];
+    for (int i = 0; i < nclips; ++i) {
+        Dd[i] = static_cast<const uint8_t*>(dv) + voff[i];
+        Md[i] = reinterpret_cast<uint32_t*>(static_cast<char*>(dm) + moff[i]);
+        ldd[i] = m;
+        CDMD_CHECK_CUDA(cudaMemcpyAsync(const_cast<uint8_t*>(Dd[i]), D_host[i], static_cast<size_t>(m) * n[i],
+                                        cudaMemcpyHostToDevice, s));
+    }
+    st = cdmd_run_shared(ctx, nclips, Dd, m, n, ldd, p, Md, stream);
+    if (st != CDMD_OK) return st;
+    for (int i = 0; i < nclips; ++i)
+        CDMD_CHECK_CUDA(cudaMemcpyAsync(mask_host[i], Md[i], moff[i + 1] - moff[i], cudaMemcpyDeviceToHost, s));
     return cdmd_status_sync(ctx, stream);
 }
 

@@ -65,13 +65,15 @@ struct GroupedClip {             // what the grouped launches need of a clip
 
 // ---- grouped sketch: one CTA per item ----------------------------------------
 struct SketchItem {
-    const CUtensorMap* tmap;     // clip frame chunk (box 64 pixels x n frames), global memory
-    float* part;                 // this item's split: [n][k] partial sums
+    const CUtensorMap* tmap[2];  // frame chunk of each clip (box 64 pixels x n frames), global memory
+    float* part[2];              // this item's split of each clip: [n][k] partial sums
     int64_t m;
     int64_t step0, nsteps;       // 64-pixel K steps
     uint2 key;
-    int n, k, pair;
-    int pad;
+    int n[2];                    // frames of each clip (<= 256)
+    int nclips;                  // clips sharing C (same m, k, seed): 1 or 2
+    int mtiles;                  // 128-row tiles of C per CTA: 2 for one clip, 1 for two
+    int k, rowblk;               // rows rowblk * 128 mtiles .. of C
 };
 struct ReduceChunk {             // DY[e] = sum over splits of part[s * elems + e]
     const float* part;
@@ -80,7 +82,8 @@ struct ReduceChunk {             // DY[e] = sum over splits of part[s * elems + 
     int splits;
     int pad;
 };
-size_t sketch_tc_smem_bytes(int n);
+size_t sketch_tc_smem_bytes(int mtiles, int nclips, int n0, int n1);
+bool sketch_tc_pair_fits(int n0, int n1);   // two clips of n0, n1 frames can share one CTA's C
 cdmd_status launch_sketch_grouped(const SketchItem* items, int nitems, size_t smem, const ReduceChunk* chunks,
                                   const int64_t* prefix, int nchunks, int64_t total, int* status, cudaStream_t stream);
 

@@ -226,6 +226,10 @@ cdmd_status launch_sketch_fp32(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n
 cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                              cdmd_ctype ctype, int k, uint64_t seed, double* DY,
                              cudaStream_t stream);
+// Several clips of the same pixel count sketched with one C (same k, seed):
+// consecutive clips share the generator two at a time where they fit.
+cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
+                                    const int64_t* ldd, int k, uint64_t seed, double* const* DY, cudaStream_t stream);
 cdmd_status launch_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                                  const cdmd_measure* meas, double* DY, cudaStream_t stream);
 cdmd_status launch_measure_sparse_count(cdmd_ctx* ctx, int64_t m, int k, uint64_t seed,

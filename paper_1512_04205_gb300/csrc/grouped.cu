@@ -1,9 +1,10 @@
 // Grouped launches of a batch plan: the sketch and the subtract pass of every
 // clip as one launch each, over a work list built here.
 //
-//   sketch     one CTA per (clip, frame chunk of <= 256 frames, 256-row pair
-//              of C, range of `sketch_steps` 64-pixel K steps); FP32 partial
-//              sums per range, then one fixed-order FP64 reduce over all clips
+//   sketch     one CTA per (frame chunk of <= 256 frames of one clip, or of
+//              two consecutive clips that share C, row block of C, range of
+//              `sketch_steps` 64-pixel K steps); FP32 partial sums per range,
+//              then one fixed-order FP64 reduce over all clips
 //   subtract   lambda^t tables (one warp per clip), then one CTA per range of
 //              `subtract_tiles` consecutive 960-pixel tiles of one clip
 //
@@ -51,36 +52,59 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
     const int nc = nc_bucket(max_ncols);
     const int tile_px = subtract_tile_pixels();
 
-    // ---- work-item sizes (0 = automatic: about two items per SM) ----
-    int64_t pair_steps = 0, tiles_all = 0;
-    for (const GroupedClip& c : clips) {
-        pair_steps += static_cast<int64_t>((c.k + 255) / 256) * ((c.m + 63) / 64) * ((c.n + 255) / 256);
-        tiles_all += (c.m + tile_px - 1) / tile_px;
-    }
-    if (sketch_steps <= 0)
-        sketch_steps = static_cast<int>(std::max<int64_t>(64, (pair_steps + 2 * num_sms - 1) / (2 * num_sms)));
-    if (subtract_tiles <= 0)
-        subtract_tiles = static_cast<int>(std::max<int64_t>(1, (tiles_all + 2 * num_sms - 1) / (2 * num_sms)));
-
-    // ---- sizes ----
+    // ---- frame chunks, and units of one chunk or two chunks sharing C ----
     struct Chunk {
         int clip, t0, nf, splits;
         int64_t part_off;   // floats
     };
+    struct Unit {
+        int c0, c1;          // chunk indices (c1 < 0: one chunk)
+    };
     std::vector<Chunk> chunks;
-    int64_t part_floats = 0, nsk = 0;
-    for (size_t i = 0; i < clips.size(); ++i) {
-        const GroupedClip& c = clips[i];
-        const int64_t steps = (c.m + 63) / 64;
-        const int splits = static_cast<int>((steps + sketch_steps - 1) / sketch_steps);
-        const int pairs = (c.k + 255) / 256;
-        for (int t0 = 0; t0 < c.n; t0 += 256) {
-            const int nf = std::min(256, c.n - t0);
-            chunks.push_back({static_cast<int>(i), t0, nf, splits, part_floats});
-            part_floats += static_cast<int64_t>(splits) * nf * c.k;
-            nsk += static_cast<int64_t>(pairs) * splits;
+    for (size_t i = 0; i < clips.size(); ++i)
+        for (int t0 = 0; t0 < clips[i].n; t0 += 256)
+            chunks.push_back({static_cast<int>(i), t0, std::min(256, clips[i].n - t0), 0, 0});
+    auto shares_c = [&](const Chunk& a, const Chunk& b) {
+        const GroupedClip& ca = clips[a.clip];
+        const GroupedClip& cb = clips[b.clip];
+        return a.clip != b.clip && ca.m == cb.m && ca.k == cb.k && ca.seed == cb.seed &&
+               sketch_tc_pair_fits(a.nf, b.nf);
+    };
+    std::vector<Unit> units;
+    for (size_t q = 0; q < chunks.size();) {
+        if (q + 1 < chunks.size() && shares_c(chunks[q], chunks[q + 1])) {
+            units.push_back({static_cast<int>(q), static_cast<int>(q + 1)});
+            q += 2;
+        } else {
+            units.push_back({static_cast<int>(q), -1});
+            q += 1;
         }
     }
+    auto unit_rowblks = [&](const Unit& u) {
+        const int rows = u.c1 >= 0 ? 128 : 256;
+        return (clips[chunks[u.c0].clip].k + rows - 1) / rows;
+    };
+
+    // ---- work-item sizes (0 = automatic: about two items per SM) ----
+    int64_t unit_steps = 0, tiles_all = 0;
+    for (const Unit& u : units)
+        unit_steps += static_cast<int64_t>(unit_rowblks(u)) * ((clips[chunks[u.c0].clip].m + 63) / 64);
+    for (const GroupedClip& c : clips) tiles_all += (c.m + tile_px - 1) / tile_px;
+    if (sketch_steps <= 0)
+        sketch_steps = static_cast<int>(std::max<int64_t>(64, (unit_steps + 2 * num_sms - 1) / (2 * num_sms)));
+    if (subtract_tiles <= 0)
+        subtract_tiles = static_cast<int>(std::max<int64_t>(1, (tiles_all + 2 * num_sms - 1) / (2 * num_sms)));
+
+    // ---- sizes ----
+    int64_t part_floats = 0, nsk = 0;
+    for (Chunk& ch : chunks) {
+        const GroupedClip& c = clips[ch.clip];
+        const int64_t steps = (c.m + 63) / 64;
+        ch.splits = static_cast<int>((steps + sketch_steps - 1) / sketch_steps);
+        ch.part_off = part_floats;
+        part_floats += static_cast<int64_t>(ch.splits) * ch.nf * c.k;
+    }
+    for (const Unit& u : units) nsk += static_cast<int64_t>(unit_rowblks(u)) * chunks[u.c0].splits;
     int64_t nsb = 0;
     for (const GroupedClip& c : clips) {
         const int64_t tiles = (c.m + tile_px - 1) / tile_px;
@@ -139,26 +163,38 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
         cdmd_status st = make_video_tmap(&tm_sk[q], c.D + static_cast<int64_t>(ch.t0) * c.ldd, c.m, ch.nf, c.ldd, 64,
                                          ch.nf);
         if (st != CDMD_OK) return st;
-        const int64_t steps = (c.m + 63) / 64;
-        const int pairs = (c.k + 255) / 256;
-        const uint2 key = seed_key(c.seed);
-        for (int sp = 0; sp < ch.splits; ++sp)
-            for (int pr = 0; pr < pairs; ++pr) {
-                SketchItem it{};
-                it.tmap = dtm_sk + q;
-                it.part = dpart + ch.part_off + static_cast<int64_t>(sp) * ch.nf * c.k;
-                it.m = c.m;
-                it.step0 = static_cast<int64_t>(sp) * sketch_steps;
-                it.nsteps = std::min<int64_t>(sketch_steps, steps - it.step0);
-                it.key = key;
-                it.n = ch.nf;
-                it.k = c.k;
-                it.pair = pr;
-                items.push_back(it);
-            }
         rchunks[q] = ReduceChunk{dpart + ch.part_off, c.buf->DY + static_cast<int64_t>(ch.t0) * c.k,
                                  static_cast<int64_t>(ch.nf) * c.k, ch.splits, 0};
         prefix[q + 1] = prefix[q] + rchunks[q].elems;
+    }
+    size_t max_smem = 0;
+    for (const Unit& u : units) {
+        const int nclips = u.c1 >= 0 ? 2 : 1;
+        const int cq[2] = {u.c0, u.c1 >= 0 ? u.c1 : u.c0};
+        const GroupedClip& c = clips[chunks[u.c0].clip];
+        const int64_t steps = (c.m + 63) / 64;
+        const int rowblks = unit_rowblks(u);
+        max_smem = std::max(max_smem, sketch_tc_smem_bytes(nclips == 1 ? 2 : 1, nclips, chunks[cq[0]].nf,
+                                                           nclips > 1 ? chunks[cq[1]].nf : 0));
+        for (int sp = 0; sp < chunks[u.c0].splits; ++sp)
+            for (int rb = 0; rb < rowblks; ++rb) {
+                SketchItem it{};
+                for (int g = 0; g < 2; ++g) {
+                    const Chunk& ch = chunks[cq[g]];
+                    it.tmap[g] = dtm_sk + cq[g];
+                    it.part[g] = g < nclips ? dpart + ch.part_off + static_cast<int64_t>(sp) * ch.nf * c.k : nullptr;
+                    it.n[g] = g < nclips ? ch.nf : 0;
+                }
+                it.m = c.m;
+                it.step0 = static_cast<int64_t>(sp) * sketch_steps;
+                it.nsteps = std::min<int64_t>(sketch_steps, steps - it.step0);
+                it.key = seed_key(c.seed);
+                it.nclips = nclips;
+                it.mtiles = nclips == 1 ? 2 : 1;
+                it.k = c.k;
+                it.rowblk = rb;
+                items.push_back(it);
+            }
     }
     std::vector<SubtractClip> sbc(clips.size());
     std::vector<SubtractItem> sbi;
@@ -199,9 +235,7 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
     g->subtract_tiles = subtract_tiles;
     g->sk_items = reinterpret_cast<const SketchItem*>(dev + o_items);
     g->sk_nitems = static_cast<int>(items.size());
-    int max_nf = 0;
-    for (const Chunk& ch : chunks) max_nf = std::max(max_nf, ch.nf);
-    g->sk_smem = sketch_tc_smem_bytes(max_nf);
+    g->sk_smem = max_smem;
     g->rd_chunks = reinterpret_cast<const ReduceChunk*>(dev + o_chunks);
     g->rd_prefix = reinterpret_cast<const int64_t*>(dev + o_prefix);
     g->rd_nchunks = static_cast<int>(chunks.size());

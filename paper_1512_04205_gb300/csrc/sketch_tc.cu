@@ -7,17 +7,23 @@
 // Philox4x32-10 (Box-Muller with the fast MUFU log2 / sin / cos) and never
 // touches HBM.
 //
-// One persistent CTA per SM owns a pair of 128-row M tiles of C (256 rows)
-// and a contiguous pixel range; the whole frame dimension (n <= 256) is the
-// MMA N.  Per 64-pixel K step and pipeline stage:
-//   warp 0      TMA: D[frames][64 pixels] uint8 box -> staging buffer
-//   warps 2-3   convert the staged bytes to BF16 in the 128-byte swizzled
-//               K-major layout (B operand, rows = frames)
-//   warps 4-11  draw the 256 x 64 block of C and write hi / lo BF16 tiles in
-//               the same layout (A operands, rows = rows of C)
-//   warp 1      one thread issues 2 tiles x 4 K16 steps x (hi, lo) = 16
-//               tcgen05.mma (M 128, N = frames padded to 16, K 16) into two
-//               TMEM accumulators and commits to the stage's barrier
+// One persistent CTA per SM owns a block of C rows and a contiguous pixel
+// range, in one of two shapes (tensor memory holds two 256-column FP32
+// accumulators of 128 rows):
+//   solo    two 128-row tiles of C (256 rows) against one clip's frames
+//   shared  one 128-row tile of C against the frames of two clips that use
+//           the same C (same pixel count, seed and k): each Gaussian drawn
+//           feeds both clips, halving the generator's work per clip
+// The frames of a clip (n <= 256) are the MMA N.  Per 64-pixel K step and
+// pipeline stage:
+//   warp 0      TMA: D[frames][64 pixels] uint8 box of each clip -> staging
+//   warp 1      one thread issues, per accumulator, 4 K16 steps x (hi, lo)
+//               tcgen05.mma (M 128, N = frames padded to 16, K 16) and
+//               commits to the stage's barrier
+//   warps 4-11  draw the C block (rows x 64 pixels) and write hi / lo BF16
+//               tiles in the 128-byte swizzled K-major layout (A operands)
+//   warps 2-11  convert the staged bytes to BF16 in the same layout (B
+//               operands, rows = frames), an even share each
 // After the last K step warps 4-7 read the accumulators (tcgen05.ld) and write
 // FP32 partials [split][frame][row]; a second kernel sums the splits in FP64.
 // Every mbarrier wait is bounded in time; on a timeout the CTA records
@@ -58,11 +64,14 @@ cdmd_status make_video_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, int n
 namespace {
 
 constexpr int kThreads = 384;
+constexpr int kWorkers = 320;               // warps 2-11
 constexpr int kStages = 2;
 constexpr int kKStep = 64;                  // pixels per K step (one 128-byte BF16 row)
 constexpr int kTileBytes = 128 * 128;       // 128 rows x 128 bytes
 constexpr uint32_t kTmemCols = 512;
-constexpr int kMaxFrames = 256;             // frames per launch: MMA N and TMA box height limits
+constexpr uint32_t kAccCols = 256;          // one accumulator slot (128 lanes x 256 FP32 columns)
+constexpr int kMaxFrames = 256;             // frames per clip and launch: MMA N and TMA box height limits
+constexpr size_t kMaxSmem = 232448;         // opt-in shared memory per CTA
 
 // Fast Box-Muller pair (MUFU lg2 / sqrt / sin / cos), same definition as the
 // accurate form: U(w) = (w + 1/2) 2^-32, angle split into quarter turns: the
@@ -89,70 +98,87 @@ __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float&
     zs = rad * sn;
 }
 
+__host__ __device__ inline int pad16(int n) { return (n + 15) / 16 * 16; }
+
+// Shared memory of one CTA: per stage the A tiles (hi, lo per 128-row tile),
+// the B tiles of each clip (frames padded to 16 rows; each clip's region
+// starts 2048-byte aligned) and the uint8 staging of each clip (128-byte
+// aligned tensor-copy destinations), then the barriers.
 struct SmemLayout {
+    uint32_t a_stage, b_stage, dst_stage;    // bytes per stage
+    uint32_t b_clip[2], dst_clip[2];         // clip offsets inside a stage
     uint32_t a_off, b_off, dst_off, bar_off, misc_off, total;
-    uint32_t b_stage_bytes, dst_stage_bytes;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int n) {
+__host__ __device__ inline SmemLayout smem_layout(int mtiles, int nclips, int n0, int n1) {
     SmemLayout L;
-    const int npad = (n + 15) / 16 * 16;
+    L.a_stage = 2u * static_cast<uint32_t>(mtiles) * kTileBytes;
+    uint32_t b = 0, d = 0;
+    for (int g = 0; g < 2; ++g) {
+        L.b_clip[g] = b;
+        L.dst_clip[g] = d;
+        if (g < nclips) {
+            const int n = g ? n1 : n0;
+            b += static_cast<uint32_t>(pad16(n)) * 128u;
+            d += (static_cast<uint32_t>(n) * kKStep + 127u) / 128u * 128u;
+        }
+    }
+    L.b_stage = (b + 1023u) / 1024u * 1024u;
+    L.dst_stage = d;
     L.a_off = 0;
-    L.b_stage_bytes = static_cast<uint32_t>(npad) * 128u;
-    L.b_off = L.a_off + kStages * 4 * kTileBytes;
-    // tensor copies need a 128-byte aligned shared-memory destination: pad
-    // the staging stride (n * 64 bytes is only 64-byte aligned for odd n)
-    L.dst_stage_bytes = (static_cast<uint32_t>(n) * kKStep + 127u) / 128u * 128u;
-    L.dst_off = L.b_off + kStages * ((L.b_stage_bytes + 1023u) / 1024u * 1024u);
-    L.bar_off = (L.dst_off + kStages * L.dst_stage_bytes + 127u) / 128u * 128u;
-    L.misc_off = L.bar_off + (5 * kStages + 1) * 8;
+    L.b_off = kStages * L.a_stage;
+    L.dst_off = L.b_off + kStages * L.b_stage;
+    L.bar_off = L.dst_off + kStages * L.dst_stage;
+    L.misc_off = L.bar_off + (4 * kStages + 1) * 8;
     L.total = L.misc_off + 64;
     return L;
 }
 
-// One CTA's share of C D: rows pair*256 .. pair*256+255 of C over the
-// 64-pixel K steps step0 .. step0+nsteps-1, written to part[t * k + row]
-// (this split's partial sums).  Used by the per-clip and the grouped launch.
-__device__ __forceinline__ void sketch_tc_body(const CUtensorMap* tmap, int64_t m, int n, int k, uint2 key, int pair,
-                                               int64_t step0, int64_t nsteps, float* __restrict__ part, int* status,
-                                               uint8_t* smem) {
-    const SmemLayout L = smem_layout(n);
-    const int npad = (n + 15) / 16 * 16;
+// One CTA's share of C D: the rows of C in row block U.rowblk (128 mtiles
+// rows) over the 64-pixel K steps step0 .. step0+nsteps-1, against each of
+// U.nclips clips, written to U.part[g][t * k + row] (this split's partial
+// sums).  Used by the per-clip and the grouped launch.
+__device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status, uint8_t* smem) {
+    const int nclips = U.nclips, mtiles = U.mtiles, k = U.k;
+    const int n0 = U.n[0], n1 = nclips > 1 ? U.n[1] : 0;
+    const SmemLayout L = smem_layout(mtiles, nclips, n0, n1);
     uint8_t* A = smem + L.a_off;
     uint8_t* B = smem + L.b_off;
     uint8_t* Dst = smem + L.dst_off;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* tma_full = bars;
     uint64_t* d_free = bars + kStages;
-    uint64_t* b_full = bars + 2 * kStages;
-    uint64_t* a_full = bars + 3 * kStages;
-    uint64_t* mma_done = bars + 4 * kStages;
-    uint64_t* accum_done = bars + 5 * kStages;
+    uint64_t* ab_full = bars + 2 * kStages;
+    uint64_t* mma_done = bars + 3 * kStages;
+    uint64_t* accum_done = bars + 4 * kStages;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.misc_off + 8);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    if (nsteps < 0) nsteps = 0;
-    const uint32_t b_stride = (L.b_stage_bytes + 1023u) / 1024u * 1024u;
+    const int64_t nsteps = U.nsteps < 0 ? 0 : U.nsteps;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             tc::mbar_init(&tma_full[s], 1);
-            tc::mbar_init(&d_free[s], 64);
-            tc::mbar_init(&b_full[s], 64);
-            tc::mbar_init(&a_full[s], 256);
+            tc::mbar_init(&d_free[s], kWorkers);
+            tc::mbar_init(&ab_full[s], kWorkers);
             tc::mbar_init(&mma_done[s], 1);
         }
         tc::mbar_init(accum_done, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
-    // zero the padding rows (frames n..npad-1) of both B stages once
+    // zero the padding rows (frames n..npad-1) of every B region once
     for (int s = 0; s < kStages; ++s)
-        for (uint32_t off = static_cast<uint32_t>(n) * 128u + tid * 16u; off < L.b_stage_bytes; off += kThreads * 16u)
-            *reinterpret_cast<uint4*>(B + s * b_stride + off) = make_uint4(0u, 0u, 0u, 0u);
+        for (int g = 0; g < nclips; ++g) {
+            const int n = g ? n1 : n0;
+            uint8_t* base = B + s * L.b_stage + (g ? L.b_clip[1] : 0u);
+            for (uint32_t off = static_cast<uint32_t>(n) * 128u + tid * 16u; off < static_cast<uint32_t>(pad16(n)) * 128u;
+                 off += kThreads * 16u)
+                *reinterpret_cast<uint4*>(base + off) = make_uint4(0u, 0u, 0u, 0u);
+        }
     tc::fence_proxy_async_smem();
     if (warp == 0) {
         tc::tmem_alloc(tmem_slot, kTmemCols);
@@ -166,13 +192,16 @@ __device__ __forceinline__ void sketch_tc_body(const CUtensorMap* tmap, int64_t 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
+            const uint32_t bytes = static_cast<uint32_t>(n0 + n1) * kKStep;
             for (int64_t ks = 0; ks < nsteps; ++ks) {
                 const int s = static_cast<int>(ks % kStages);
                 const uint32_t u = static_cast<uint32_t>(ks / kStages);
                 if (u >= 1 && !tc::mbar_wait(&d_free[s], (u - 1) & 1u, abort_flag, status)) break;
-                tc::mbar_arrive_expect_tx(&tma_full[s], static_cast<uint32_t>(n) * kKStep);
-                tc::tma_load_2d(Dst + s * L.dst_stage_bytes, tmap, static_cast<int>((step0 + ks) * kKStep), 0,
-                                &tma_full[s]);
+                tc::mbar_arrive_expect_tx(&tma_full[s], bytes);
+                const int x = static_cast<int>((U.step0 + ks) * kKStep);
+                for (int g = 0; g < nclips; ++g)
+                    tc::tma_load_2d(Dst + s * L.dst_stage + (g ? L.dst_clip[1] : L.dst_clip[0]), g ? U.tmap[1] : U.tmap[0], x, 0,
+                                    &tma_full[s]);
             }
             // drain: the last load of each stage must have landed before exit
             for (int s = 0; s < kStages; ++s) {
@@ -183,24 +212,28 @@ __device__ __forceinline__ void sketch_tc_body(const CUtensorMap* tmap, int64_t 
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = tc::idesc_bf16_f32(128, npad);
+            const uint32_t idesc0 = tc::idesc_bf16_f32(128, pad16(n0));
+            const uint32_t idesc1 = tc::idesc_bf16_f32(128, pad16(n1 > 0 ? n1 : 16));
             for (int64_t ks = 0; ks < nsteps; ++ks) {
                 const int s = static_cast<int>(ks % kStages);
                 const uint32_t par = static_cast<uint32_t>(ks / kStages) & 1u;
-                if (!tc::mbar_wait(&a_full[s], par, abort_flag, status)) break;
-                if (!tc::mbar_wait(&b_full[s], par, abort_flag, status)) break;
+                if (!tc::mbar_wait(&ab_full[s], par, abort_flag, status)) break;
                 tc::tc_fence_after();
-                const uint32_t a_base = tc::smem_u32(A + s * 4 * kTileBytes);
-                const uint32_t b_base = tc::smem_u32(B + s * b_stride);
+                const uint32_t a_base = tc::smem_u32(A + s * L.a_stage);
+                const uint32_t b_base = tc::smem_u32(B + s * L.b_stage);
+#pragma unroll 1
+                for (int mt = 0; mt < mtiles; ++mt) {
+#pragma unroll 1
+                    for (int g = 0; g < nclips; ++g) {
+                        const uint32_t acc = tmem_base + static_cast<uint32_t>(mt * nclips + g) * kAccCols;
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t bdesc = tc::desc_sw128(b_base + (g ? L.b_clip[1] : 0u) + kk * 32);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t bdesc = tc::desc_sw128(b_base + kk * 32);
-#pragma unroll
-                        for (int hl = 0; hl < 2; ++hl) {
-                            const uint64_t adesc = tc::desc_sw128(a_base + (mt * 2 + hl) * kTileBytes + kk * 32);
-                            tc::mma_bf16(tmem_base + mt * 256, adesc, bdesc, idesc, (ks | kk | hl) ? 1u : 0u);
+                            for (int hl = 0; hl < 2; ++hl) {
+                                const uint64_t adesc = tc::desc_sw128(a_base + (mt * 2 + hl) * kTileBytes + kk * 32);
+                                tc::mma_bf16(acc, adesc, bdesc, g ? idesc1 : idesc0, (ks | kk | hl) ? 1u : 0u);
+                            }
                         }
                     }
                 }
@@ -208,121 +241,126 @@ __device__ __forceinline__ void sketch_tc_body(const CUtensorMap* tmap, int64_t 
             }
             tc::mma_commit(accum_done);   // fires once every MMA issued above has finished
         }
-    } else if (warp < 4) {
-        // ---------------- uint8 -> BF16 converters ----------------
-        const int ct = tid - 64;
+    } else {
+        // ---------------- workers: C generators (warps 4-11) and converters (warps 2-11) ----------------
+        const int wt = tid - 64;
+        const bool gen = warp >= 4;
+        const int gt = tid - 128;
+        const int row0 = U.rowblk * 128 * mtiles;
+        const int conv0 = n0 * 8, conv_total = (n0 + n1) * 8;
+        const PhiloxKeys rk = philox_round_keys(U.key);   // the same for every draw of this CTA
         for (int64_t ks = 0; ks < nsteps; ++ks) {
             const int s = static_cast<int>(ks % kStages);
             const uint32_t u = static_cast<uint32_t>(ks / kStages);
-            if (!tc::mbar_wait(&tma_full[s], u & 1u, abort_flag, status)) break;
             if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
-            const uint8_t* src = Dst + s * L.dst_stage_bytes;
-            uint8_t* dst = B + s * b_stride;
-            for (int it = ct; it < n * 8; it += 64) {
-                const int t = it >> 3, g = it & 7;
-                const uint2 raw = *reinterpret_cast<const uint2*>(src + t * kKStep + g * 8);
+            if (gen) {
+                const int64_t j0 = (U.step0 + ks) * kKStep;
+                uint8_t* a_stage = A + s * L.a_stage;
+#pragma unroll 1
+                for (int h = 0; h < mtiles; ++h) {
+                    const int it = gt + 256 * h;
+                    const int g = it & 7;        // 8-pixel group within the K step
+                    const int q = it >> 3;       // quad of rows within the block (0 .. 32 mtiles - 1)
+                    const int mt = q >> 5;
+                    const uint32_t row_t = static_cast<uint32_t>(4 * (q & 31));
+                    const uint32_t gq = static_cast<uint32_t>((row0 >> 2) + q);
+                    float z[4][8];
+                    const int64_t jg = j0 + 8 * g;
+                    if (row0 + 4 * q < k && jg + 8 <= U.m) {
+#pragma unroll
+                        for (int p = 0; p < 8; ++p) {
+                            const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), rk);
+                            box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
+                            box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
+                        }
+                    } else if (row0 + 4 * q < k) {
+                        // pixels past m (last K step only) are drawn and then zeroed
+#pragma unroll
+                        for (int p = 0; p < 8; ++p) {
+                            const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), rk);
+                            box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
+                            box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
+                            const bool in = (jg + p) < U.m;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) z[e][p] = in ? z[e][p] : 0.0f;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+#pragma unroll
+                            for (int p = 0; p < 8; ++p) z[e][p] = 0.0f;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        uint32_t hi[4], lo[4];
+#pragma unroll
+                        for (int p2 = 0; p2 < 4; ++p2) {
+                            const float a = z[e][2 * p2], b = z[e][2 * p2 + 1];
+                            const uint32_t ua = __float_as_uint(a) & 0xFFFF0000u;   // hi by truncation
+                            const uint32_t ub = __float_as_uint(b) & 0xFFFF0000u;
+                            hi[p2] = __byte_perm(ua, ub, 0x7632);
+                            lo[p2] = tc::pack_bf16_rn(a - __uint_as_float(ua), b - __uint_as_float(ub));
+                        }
+                        const uint32_t off = tc::sw128_offset(row_t + e, static_cast<uint32_t>(g));
+                        *reinterpret_cast<uint4*>(a_stage + (mt * 2 + 0) * kTileBytes + off) =
+                            make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                        *reinterpret_cast<uint4*>(a_stage + (mt * 2 + 1) * kTileBytes + off) =
+                            make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    }
+                }
+            }
+            // uint8 -> BF16: 8 pixels of one frame per item, over both clips
+            if (!tc::mbar_wait(&tma_full[s], u & 1u, abort_flag, status)) break;
+            const uint8_t* src_stage = Dst + s * L.dst_stage;
+            uint8_t* b_stage = B + s * L.b_stage;
+            for (int it = wt; it < conv_total; it += kWorkers) {
+                const int g = it >= conv0 ? 1 : 0;
+                const int li = it - (g ? conv0 : 0);
+                const int t = li >> 3, c8 = li & 7;
+                const uint2 raw = *reinterpret_cast<const uint2*>(src_stage + (g ? L.dst_clip[1] : 0u) + t * kKStep + c8 * 8);
                 uint32_t w[4];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t word = h ? raw.y : raw.x;
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
-                        const float f0 = __uint_as_float(0x4B000000u | ((word >> (16 * e)) & 0xFFu)) - 8388608.0f;
-                        const float f1 = __uint_as_float(0x4B000000u | ((word >> (16 * e + 8)) & 0xFFu)) - 8388608.0f;
+                        // byte b of the word into a float with exponent 2^23: 2^23 + b, exact
+                        const float f0 = __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540u + 2u * e)) - 8388608.0f;
+                        const float f1 = __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7541u + 2u * e)) - 8388608.0f;
                         w[h * 2 + e] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
                     }
                 }
-                *reinterpret_cast<uint4*>(dst + tc::sw128_offset(static_cast<uint32_t>(t), static_cast<uint32_t>(g))) =
+                *reinterpret_cast<uint4*>(b_stage + (g ? L.b_clip[1] : 0u) +
+                                          tc::sw128_offset(static_cast<uint32_t>(t), static_cast<uint32_t>(c8))) =
                     make_uint4(w[0], w[1], w[2], w[3]);
             }
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&d_free[s]);
-            tc::mbar_arrive(&b_full[s]);
-        }
-    } else {
-        // ---------------- C generators (256 threads) ----------------
-        const int gt = tid - 128;
-        const int row_pair0 = pair * 256;
-        const PhiloxKeys rk = philox_round_keys(key);   // the same for every draw of this CTA
-        for (int64_t ks = 0; ks < nsteps; ++ks) {
-            const int s = static_cast<int>(ks % kStages);
-            const uint32_t u = static_cast<uint32_t>(ks / kStages);
-            if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
-            const int64_t j0 = (step0 + ks) * kKStep;
-            uint8_t* a_stage = A + s * 4 * kTileBytes;
-#pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                const int it = gt + 256 * h;
-                const int g = it & 7;        // 8-pixel group within the K step
-                const int q = it >> 3;       // quad of rows within the pair (0..63)
-                const int mt = q >> 5;
-                const uint32_t row_t = static_cast<uint32_t>(4 * (q & 31));
-                const uint32_t gq = static_cast<uint32_t>((row_pair0 >> 2) + q);
-                float z[4][8];
-                const int64_t jg = j0 + 8 * g;
-                if (row_pair0 + 4 * q < k && jg + 8 <= m) {
-#pragma unroll
-                    for (int p = 0; p < 8; ++p) {
-                        const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), rk);
-                        box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
-                        box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
-                    }
-                } else if (row_pair0 + 4 * q < k) {
-                    // pixels past m (last K step only) are drawn and then zeroed
-#pragma unroll
-                    for (int p = 0; p < 8; ++p) {
-                        const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), rk);
-                        box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
-                        box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
-                        const bool in = (jg + p) < m;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) z[e][p] = in ? z[e][p] : 0.0f;
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-#pragma unroll
-                        for (int p = 0; p < 8; ++p) z[e][p] = 0.0f;
-                }
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    uint32_t hi[4], lo[4];
-#pragma unroll
-                    for (int p2 = 0; p2 < 4; ++p2) {
-                        const float a = z[e][2 * p2], b = z[e][2 * p2 + 1];
-                        const uint32_t ua = __float_as_uint(a) & 0xFFFF0000u;   // hi by truncation
-                        const uint32_t ub = __float_as_uint(b) & 0xFFFF0000u;
-                        hi[p2] = __byte_perm(ua, ub, 0x7632);
-                        lo[p2] = tc::pack_bf16_rn(a - __uint_as_float(ua), b - __uint_as_float(ub));
-                    }
-                    const uint32_t off = tc::sw128_offset(row_t + e, static_cast<uint32_t>(g));
-                    *reinterpret_cast<uint4*>(a_stage + (mt * 2 + 0) * kTileBytes + off) =
-                        make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    *reinterpret_cast<uint4*>(a_stage + (mt * 2 + 1) * kTileBytes + off) =
-                        make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                }
-            }
-            tc::fence_proxy_async_smem();
-            tc::mbar_arrive(&a_full[s]);
+            tc::mbar_arrive(&ab_full[s]);
         }
         // ---------------- epilogue (warps 4-7) ----------------
-        if (warp < 8) {
+        if (warp >= 4 && warp < 8) {
             const bool ok = tc::mbar_wait(accum_done, 0u, abort_flag, status) && !*abort_flag;
             tc::tc_fence_after();
             if (ok) {
                 const int quarter = warp & 3;
                 const int row_in_tile = quarter * 32 + lane;
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int row = pair * 256 + mt * 128 + row_in_tile;
-                    for (int c0 = 0; c0 < npad; c0 += 16) {
-                        uint32_t v[16];
-                        tc::tmem_ld_x16(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + mt * 256 + c0, v);
-                        tc::tmem_wait_ld();
-                        if (row < k) {
+                for (int mt = 0; mt < mtiles; ++mt) {
+                    const int row = row0 + mt * 128 + row_in_tile;
+                    for (int g = 0; g < nclips; ++g) {
+                        const int n = g ? n1 : n0;
+                        float* part = g ? U.part[1] : U.part[0];
+                        const uint32_t col = static_cast<uint32_t>(mt * nclips + g) * kAccCols;
+                        for (int c0 = 0; c0 < pad16(n); c0 += 16) {
+                            uint32_t v[16];
+                            tc::tmem_ld_x16(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + col + c0, v);
+                            tc::tmem_wait_ld();
+                            if (row < k) {
 #pragma unroll
-                            for (int q = 0; q < 16; ++q) {
-                                const int t = c0 + q;
-                                if (t < n) part[static_cast<int64_t>(t) * k + row] = __uint_as_float(v[q]);
+                                for (int q = 0; q < 16; ++q) {
+                                    const int t = c0 + q;
+                                    if (t < n) part[static_cast<int64_t>(t) * k + row] = __uint_as_float(v[q]);
+                                }
                             }
                         }
                     }
@@ -340,28 +378,48 @@ __device__ __forceinline__ void sketch_tc_body(const CUtensorMap* tmap, int64_t 
     }
 }
 
+struct SketchArgs {
+    float* part[2];             // [splits][n_g][k] partial sums of each clip
+    int n[2];
+    int nclips, mtiles, k;
+    int64_t m, steps_per_split, total_steps;
+    uint2 key;
+};
+
 __global__ void __launch_bounds__(kThreads, 1)
-sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, int k, uint2 key,
-                 int64_t steps_per_split, int64_t total_steps, float* __restrict__ part, int* status) {
+sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap0, const __grid_constant__ CUtensorMap tmap1,
+                 const SketchArgs a, int* status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // the runtime aligns dynamic shared memory to at least 16 bytes; round up
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int split = blockIdx.y;
-    const int64_t step0 = static_cast<int64_t>(split) * steps_per_split;
-    int64_t nsteps = total_steps - step0;
-    if (nsteps > steps_per_split) nsteps = steps_per_split;
-    sketch_tc_body(&tmap, m, n, k, key, blockIdx.x, step0, nsteps, part + static_cast<int64_t>(split) * n * k, status,
-                   smem);
+    SketchItem U;
+    U.tmap[0] = &tmap0;
+    U.tmap[1] = &tmap1;
+    U.step0 = static_cast<int64_t>(split) * a.steps_per_split;
+    U.nsteps = a.total_steps - U.step0;
+    if (U.nsteps > a.steps_per_split) U.nsteps = a.steps_per_split;
+    U.n[0] = a.n[0];
+    U.n[1] = a.n[1];
+    U.part[0] = a.part[0] + static_cast<int64_t>(split) * a.n[0] * a.k;
+    U.part[1] = a.nclips > 1 ? a.part[1] + static_cast<int64_t>(split) * a.n[1] * a.k : nullptr;
+    U.m = a.m;
+    U.key = a.key;
+    U.nclips = a.nclips;
+    U.mtiles = a.mtiles;
+    U.k = a.k;
+    U.rowblk = blockIdx.x;
+    sketch_tc_body(U, status, smem);
 }
 
-// Grouped launch: CTA b runs work item items[b] (any clip, frame chunk,
-// row pair and pixel range); the tensor maps live in global memory.
+// Grouped launch: CTA b runs work item items[b] (any clip or clip pair, frame
+// chunk, row block and pixel range); the tensor maps live in global memory.
 __global__ void __launch_bounds__(kThreads, 1)
 sketch_tc_grouped_kernel(const SketchItem* __restrict__ items, int* status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const SketchItem it = items[blockIdx.x];
-    sketch_tc_body(it.tmap, it.m, it.n, it.k, it.key, it.pair, it.step0, it.nsteps, it.part, status, smem);
+    sketch_tc_body(it, status, smem);
 }
 
 // Grouped fixed-order reduce: element idx of the concatenated outputs belongs
@@ -384,16 +442,85 @@ __global__ void sketch_reduce_grouped_kernel(const ReduceChunk* __restrict__ chu
     c.DY[e] = s;
 }
 
-// DY[t*k + i] = sum_s part[(s*n + t)*k + i], FP64, fixed order.
-__global__ void sketch_tc_reduce_kernel(const float* __restrict__ part, int splits, int k, int n,
-                                        double* __restrict__ DY, int* status) {
+// DY_g[t*k + i] = sum_s part_g[(s*n_g + t)*k + i], FP64, fixed order; blockIdx.y = clip.
+__global__ void sketch_tc_reduce_kernel(const SketchArgs a, int splits, double* DY0, double* DY1, int* status) {
+    const int g = blockIdx.y;
     const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t total = static_cast<int64_t>(k) * n;
+    const int64_t total = static_cast<int64_t>(a.k) * (g ? a.n[1] : a.n[0]);
     if (idx >= total) return;
+    const float* part = g ? a.part[1] : a.part[0];
     double s = 0.0;
     for (int sp = 0; sp < splits; ++sp) s += static_cast<double>(part[static_cast<int64_t>(sp) * total + idx]);
     if (!isfinite(s)) record_status(status, CDMD_ERR_NONFINITE);
-    DY[idx] = s;
+    (g ? DY1 : DY0)[idx] = s;
+}
+
+}  // namespace
+
+// Shared memory of a CTA in the given shape (bytes, with room to align the
+// base to 1024); larger than kMaxSmem when the shape does not fit.
+size_t sketch_tc_smem_bytes(int mtiles, int nclips, int n0, int n1) {
+    return smem_layout(mtiles, nclips, n0, n1).total + 1024;
+}
+
+bool sketch_tc_pair_fits(int n0, int n1) {
+    return n0 >= 1 && n1 >= 1 && n0 <= kMaxFrames && n1 <= kMaxFrames &&
+           sketch_tc_smem_bytes(1, 2, n0, n1) <= kMaxSmem;
+}
+
+namespace {
+
+// One launch: nclips (1 or 2) clips of <= 256 frames, each its own DY.
+cdmd_status launch_sketch_tc_unit(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
+                                  const int64_t* ldd, int k, uint64_t seed, double* const* DY, cudaStream_t stream) {
+    const int mtiles = nclips == 1 ? 2 : 1;
+    CUtensorMap tmap[2];
+    for (int g = 0; g < nclips; ++g) {
+        cdmd_status st = make_video_tmap(&tmap[g], D[g], m, n[g], ldd[g], kKStep, n[g]);
+        if (st != CDMD_OK) return st;
+    }
+    if (nclips == 1) tmap[1] = tmap[0];
+    const int rowblks = (k + 128 * mtiles - 1) / (128 * mtiles);
+    const int64_t total_steps = (m + kKStep - 1) / kKStep;
+    int64_t splits = std::max<int64_t>(1, ctx->num_sms / rowblks);
+    splits = std::min<int64_t>(splits, total_steps);
+    const int64_t steps_per_split = (total_steps + splits - 1) / splits;
+    splits = (total_steps + steps_per_split - 1) / steps_per_split;
+    size_t floats = 0;
+    for (int g = 0; g < nclips; ++g) floats += static_cast<size_t>(splits) * n[g] * k;
+    float* part = nullptr;
+    cdmd_status st = ensure_buffer(ctx, BUF_SKETCH_PARTIAL, floats * sizeof(float), reinterpret_cast<void**>(&part));
+    if (st != CDMD_OK) return st;
+    SketchArgs a{};
+    a.part[0] = part;
+    a.part[1] = nclips > 1 ? part + static_cast<size_t>(splits) * n[0] * k : nullptr;
+    a.n[0] = n[0];
+    a.n[1] = nclips > 1 ? n[1] : 0;
+    a.nclips = nclips;
+    a.mtiles = mtiles;
+    a.k = k;
+    a.m = m;
+    a.steps_per_split = steps_per_split;
+    a.total_steps = total_steps;
+    a.key = seed_key(seed);
+    const size_t smem = sketch_tc_smem_bytes(mtiles, nclips, a.n[0], a.n[1]);
+    if (smem > kMaxSmem) return fail(CDMD_ERR_UNSUPPORTED, "sketch: %zu bytes of shared memory per CTA", smem);
+    CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem)));
+    sketch_tc_kernel<<<dim3(rowblks, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(tmap[0], tmap[1], a,
+                                                                                             ctx->d_status);
+    CDMD_CHECK_LAUNCH("sketch_tc_kernel");
+    const int64_t tot = static_cast<int64_t>(k) * std::max(a.n[0], a.n[1]);
+    sketch_tc_reduce_kernel<<<dim3(static_cast<unsigned>((tot + 255) / 256), nclips), 256, 0, stream>>>(
+        a, static_cast<int>(splits), DY[0], nclips > 1 ? DY[1] : nullptr, ctx->d_status);
+    CDMD_CHECK_LAUNCH("sketch_tc_reduce_kernel");
+    return CDMD_OK;
+}
+
+cdmd_status check_tc_video(const uint8_t* D, int64_t ldd) {
+    if ((reinterpret_cast<uintptr_t>(D) & 15) != 0 || (ldd & 15) != 0)
+        return fail(CDMD_ERR_INVALID_ARG, "BF16X2 sketch needs a 16-byte aligned video and ldd %% 16 == 0");
+    return CDMD_OK;
 }
 
 }  // namespace
@@ -402,53 +529,42 @@ cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, 
                              int k, uint64_t seed, double* DY, cudaStream_t stream) {
     if (ctype != CDMD_C_GAUSSIAN)
         return fail(CDMD_ERR_UNSUPPORTED, "BF16X2 sketch is built for the Gaussian measurement matrix");
-    if ((reinterpret_cast<uintptr_t>(D) & 15) != 0 || (ldd & 15) != 0)
-        return fail(CDMD_ERR_INVALID_ARG, "BF16X2 sketch needs a 16-byte aligned video and ldd %% 16 == 0");
-    if (n > kMaxFrames) {
-        // the sketch is linear in the frames: DY[t0:t1] = C D[:, t0:t1]
-        for (int t0 = 0; t0 < n; t0 += kMaxFrames) {
-            const int nc = std::min(kMaxFrames, n - t0);
-            cdmd_status st = launch_sketch_tc(ctx, D + static_cast<int64_t>(t0) * ldd, m, nc, ldd, ctype, k, seed,
-                                              DY + static_cast<int64_t>(t0) * k, stream);
-            if (st != CDMD_OK) return st;
-        }
-        return CDMD_OK;
+    cdmd_status st = check_tc_video(D, ldd);
+    if (st != CDMD_OK) return st;
+    // the sketch is linear in the frames: DY[t0:t1] = C D[:, t0:t1]
+    for (int t0 = 0; t0 < n; t0 += kMaxFrames) {
+        const int nc = std::min(kMaxFrames, n - t0);
+        const uint8_t* Dc = D + static_cast<int64_t>(t0) * ldd;
+        double* DYc = DY + static_cast<int64_t>(t0) * k;
+        st = launch_sketch_tc_unit(ctx, 1, &Dc, m, &nc, &ldd, k, seed, &DYc, stream);
+        if (st != CDMD_OK) return st;
     }
-    CUtensorMap tmap;
-    cdmd_status st = make_video_tmap(&tmap, D, m, n, ldd, kKStep, n);
-    if (st != CDMD_OK) return st;
-    const int pairs = (k + 255) / 256;
-    const int64_t total_steps = (m + kKStep - 1) / kKStep;
-    int64_t splits = std::max<int64_t>(1, ctx->num_sms / pairs);
-    splits = std::min<int64_t>(splits, total_steps);
-    const int64_t steps_per_split = (total_steps + splits - 1) / splits;
-    splits = (total_steps + steps_per_split - 1) / steps_per_split;
-    float* part = nullptr;
-    st = ensure_buffer(ctx, BUF_SKETCH_PARTIAL, static_cast<size_t>(splits) * n * k * sizeof(float),
-                       reinterpret_cast<void**>(&part));
-    if (st != CDMD_OK) return st;
-    const SmemLayout L = smem_layout(n);
-    const size_t smem = L.total + 1024;   // room to align the base to 1024 bytes
-    CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem)));
-    sketch_tc_kernel<<<dim3(pairs, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(
-        tmap, m, n, k, seed_key(seed), steps_per_split, total_steps, part, ctx->d_status);
-    CDMD_CHECK_LAUNCH("sketch_tc_kernel");
-    const int64_t tot = static_cast<int64_t>(k) * n;
-    sketch_tc_reduce_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, stream>>>(
-        part, static_cast<int>(splits), k, n, DY, ctx->d_status);
-    CDMD_CHECK_LAUNCH("sketch_tc_reduce_kernel");
     return CDMD_OK;
 }
 
-}  // namespace cdmd
-
-namespace cdmd {
-
-size_t sketch_tc_smem_bytes(int n) { return smem_layout(n).total + 1024; }
+cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
+                                    const int64_t* ldd, int k, uint64_t seed, double* const* DY, cudaStream_t stream) {
+    for (int i = 0; i < nclips; ++i) {
+        cdmd_status st = check_tc_video(D[i], ldd[i]);
+        if (st != CDMD_OK) return st;
+    }
+    for (int i = 0; i < nclips;) {
+        if (i + 1 < nclips && sketch_tc_pair_fits(n[i], n[i + 1])) {
+            cdmd_status st = launch_sketch_tc_unit(ctx, 2, D + i, m, n + i, ldd + i, k, seed, DY + i, stream);
+            if (st != CDMD_OK) return st;
+            i += 2;
+        } else {
+            cdmd_status st = launch_sketch_tc(ctx, D[i], m, n[i], ldd[i], CDMD_C_GAUSSIAN, k, seed, DY[i], stream);
+            if (st != CDMD_OK) return st;
+            i += 1;
+        }
+    }
+    return CDMD_OK;
+}
 
 cdmd_status launch_sketch_grouped(const SketchItem* items, int nitems, size_t smem, const ReduceChunk* chunks,
                                   const int64_t* prefix, int nchunks, int64_t total, int* status, cudaStream_t stream) {
+    if (smem > kMaxSmem) return fail(CDMD_ERR_UNSUPPORTED, "grouped sketch: %zu bytes of shared memory per CTA", smem);
     CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem)));
     sketch_tc_grouped_kernel<<<static_cast<unsigned>(nitems), kThreads, smem, stream>>>(items, status);
