@@ -168,6 +168,7 @@ enum BufferId {
     BUF_SELECTOR,             // selector model blob, pick order, accept flag, fallback count
     BUF_MLP_PARTS,            // selector training: per-warp partial gradients
     BUF_RELABEL,              // selector training: OMP against a second target
+    BUF_SKETCH_WIDE,          // BF16 copies of the frames of a clip pair sketched together
     BUF_COUNT
 };
 

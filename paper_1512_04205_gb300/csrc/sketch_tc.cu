@@ -35,10 +35,14 @@
 
 namespace cdmd {
 
-cdmd_status make_video_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, int n, int64_t ldd, int box_x,
-                            int box_y) {
-    // resolved once (thread-safe static initialisation)
-    static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+namespace {
+
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+// cuTensorMapEncodeTiled from the driver, resolved once (thread-safe static
+// initialisation); NULL if the driver does not provide it.
+EncodeFn tmap_encoder() {
+    static const EncodeFn encode = []() -> EncodeFn {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
@@ -47,8 +51,16 @@ cdmd_status make_video_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, int n
             (void)cudaGetLastError();
             return nullptr;
         }
-        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        return reinterpret_cast<EncodeFn>(fn);
     }();
+    return encode;
+}
+
+}  // namespace
+
+cdmd_status make_video_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, int n, int64_t ldd, int box_x,
+                            int box_y) {
+    const EncodeFn encode = tmap_encoder();
     if (encode == nullptr) return fail(CDMD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const cuuint64_t dims[2] = {static_cast<cuuint64_t>(m), static_cast<cuuint64_t>(n)};
     const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldd)};
@@ -61,10 +73,28 @@ cdmd_status make_video_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, int n
     return CDMD_OK;
 }
 
+// BF16 frames (dim0 = pixels, dim1 = frames, row stride ldw elements), box
+// 64 pixels x box_y frames landing in the 128-byte swizzled K-major layout
+// the MMA reads (8-row atoms of 1024 bytes); pixels past m read as zero.
+static cdmd_status make_wide_tmap(CUtensorMap* map, const uint16_t* W, int64_t m, int n, int64_t ldw, int box_y) {
+    const EncodeFn encode = tmap_encoder();
+    if (encode == nullptr) return fail(CDMD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(m), static_cast<cuuint64_t>(n)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldw) * 2u};
+    const cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(box_y)};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(W), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(CDMD_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", static_cast<int>(r));
+    return CDMD_OK;
+}
+
 namespace {
 
 constexpr int kThreads = 384;
 constexpr int kWorkers = 320;               // warps 2-11
+constexpr int kGen = 256;                   // warps 4-11
 constexpr int kStages = 2;
 constexpr int kKStep = 64;                  // pixels per K step (one 128-byte BF16 row)
 constexpr int kTileBytes = 128 * 128;       // 128 rows x 128 bytes
@@ -110,7 +140,7 @@ struct SmemLayout {
     uint32_t a_off, b_off, dst_off, bar_off, misc_off, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int mtiles, int nclips, int n0, int n1) {
+__host__ __device__ inline SmemLayout smem_layout(int mtiles, int nclips, int n0, int n1, bool wide) {
     SmemLayout L;
     L.a_stage = 2u * static_cast<uint32_t>(mtiles) * kTileBytes;
     uint32_t b = 0, d = 0;
@@ -120,7 +150,7 @@ __host__ __device__ inline SmemLayout smem_layout(int mtiles, int nclips, int n0
         if (g < nclips) {
             const int n = g ? n1 : n0;
             b += static_cast<uint32_t>(pad16(n)) * 128u;
-            d += (static_cast<uint32_t>(n) * kKStep + 127u) / 128u * 128u;
+            if (!wide) d += (static_cast<uint32_t>(n) * kKStep + 127u) / 128u * 128u;
         }
     }
     L.b_stage = (b + 1023u) / 1024u * 1024u;
@@ -138,10 +168,16 @@ __host__ __device__ inline SmemLayout smem_layout(int mtiles, int nclips, int n0
 // rows) over the 64-pixel K steps step0 .. step0+nsteps-1, against each of
 // U.nclips clips, written to U.part[g][t * k + row] (this split's partial
 // sums).  Used by the per-clip and the grouped launch.
+//   kWide = false   U.tmap[g] maps the uint8 frames; the bytes are staged and
+//                   converted to BF16 by warps 2-11
+//   kWide = true    U.tmap[g] maps a BF16 copy of the frames (128-byte
+//                   swizzle): the tensor copy lands in the B operand itself
+//                   and warps 2-3 stay idle
+template <bool kWide>
 __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status, uint8_t* smem) {
     const int nclips = U.nclips, mtiles = U.mtiles, k = U.k;
     const int n0 = U.n[0], n1 = nclips > 1 ? U.n[1] : 0;
-    const SmemLayout L = smem_layout(mtiles, nclips, n0, n1);
+    const SmemLayout L = smem_layout(mtiles, nclips, n0, n1, kWide);
     uint8_t* A = smem + L.a_off;
     uint8_t* B = smem + L.b_off;
     uint8_t* Dst = smem + L.dst_off;
@@ -163,7 +199,7 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
         for (int s = 0; s < kStages; ++s) {
             tc::mbar_init(&tma_full[s], 1);
             tc::mbar_init(&d_free[s], kWorkers);
-            tc::mbar_init(&ab_full[s], kWorkers);
+            tc::mbar_init(&ab_full[s], kWide ? kGen : kWorkers);
             tc::mbar_init(&mma_done[s], 1);
         }
         tc::mbar_init(accum_done, 1);
@@ -192,16 +228,21 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            const uint32_t bytes = static_cast<uint32_t>(n0 + n1) * kKStep;
+            const uint32_t bytes = static_cast<uint32_t>(n0 + n1) * (kWide ? 128u : static_cast<uint32_t>(kKStep));
             for (int64_t ks = 0; ks < nsteps; ++ks) {
                 const int s = static_cast<int>(ks % kStages);
                 const uint32_t u = static_cast<uint32_t>(ks / kStages);
-                if (u >= 1 && !tc::mbar_wait(&d_free[s], (u - 1) & 1u, abort_flag, status)) break;
+                // the slot is free once its bytes were converted (staged) or
+                // its B tiles were read by the MMAs (wide)
+                if (u >= 1 && !tc::mbar_wait(kWide ? &mma_done[s] : &d_free[s], (u - 1) & 1u, abort_flag, status))
+                    break;
                 tc::mbar_arrive_expect_tx(&tma_full[s], bytes);
                 const int x = static_cast<int>((U.step0 + ks) * kKStep);
-                for (int g = 0; g < nclips; ++g)
-                    tc::tma_load_2d(Dst + s * L.dst_stage + (g ? L.dst_clip[1] : L.dst_clip[0]), g ? U.tmap[1] : U.tmap[0], x, 0,
-                                    &tma_full[s]);
+                for (int g = 0; g < nclips; ++g) {
+                    uint8_t* dst = kWide ? B + s * L.b_stage + (g ? L.b_clip[1] : 0u)
+                                         : Dst + s * L.dst_stage + (g ? L.dst_clip[1] : 0u);
+                    tc::tma_load_2d(dst, g ? U.tmap[1] : U.tmap[0], x, 0, &tma_full[s]);
+                }
             }
             // drain: the last load of each stage must have landed before exit
             for (int s = 0; s < kStages; ++s) {
@@ -218,6 +259,7 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
                 const int s = static_cast<int>(ks % kStages);
                 const uint32_t par = static_cast<uint32_t>(ks / kStages) & 1u;
                 if (!tc::mbar_wait(&ab_full[s], par, abort_flag, status)) break;
+                if (kWide && !tc::mbar_wait(&tma_full[s], par, abort_flag, status)) break;
                 tc::tc_fence_after();
                 const uint32_t a_base = tc::smem_u32(A + s * L.a_stage);
                 const uint32_t b_base = tc::smem_u32(B + s * L.b_stage);
@@ -249,7 +291,7 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
         const int row0 = U.rowblk * 128 * mtiles;
         const int conv0 = n0 * 8, conv_total = (n0 + n1) * 8;
         const PhiloxKeys rk = philox_round_keys(U.key);   // the same for every draw of this CTA
-        for (int64_t ks = 0; ks < nsteps; ++ks) {
+        for (int64_t ks = 0; ks < ((kWide && !gen) ? 0 : nsteps); ++ks) {
             const int s = static_cast<int>(ks % kStages);
             const uint32_t u = static_cast<uint32_t>(ks / kStages);
             if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
@@ -308,6 +350,11 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
                             make_uint4(lo[0], lo[1], lo[2], lo[3]);
                     }
                 }
+            }
+            if (kWide) {
+                tc::fence_proxy_async_smem();
+                tc::mbar_arrive(&ab_full[s]);
+                continue;
             }
             // uint8 -> BF16: 8 pixels of one frame per item, over both clips
             if (!tc::mbar_wait(&tma_full[s], u & 1u, abort_flag, status)) break;
@@ -386,6 +433,7 @@ struct SketchArgs {
     uint2 key;
 };
 
+template <bool kWide>
 __global__ void __launch_bounds__(kThreads, 1)
 sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap0, const __grid_constant__ CUtensorMap tmap1,
                  const SketchArgs a, int* status) {
@@ -409,7 +457,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap0, const __grid_constan
     U.mtiles = a.mtiles;
     U.k = a.k;
     U.rowblk = blockIdx.x;
-    sketch_tc_body(U, status, smem);
+    sketch_tc_body<kWide>(U, status, smem);
 }
 
 // Grouped launch: CTA b runs work item items[b] (any clip or clip pair, frame
@@ -419,7 +467,7 @@ sketch_tc_grouped_kernel(const SketchItem* __restrict__ items, int* status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const SketchItem it = items[blockIdx.x];
-    sketch_tc_body(it, status, smem);
+    sketch_tc_body<false>(it, status, smem);
 }
 
 // Grouped fixed-order reduce: element idx of the concatenated outputs belongs
@@ -442,6 +490,42 @@ __global__ void sketch_reduce_grouped_kernel(const ReduceChunk* __restrict__ chu
     c.DY[e] = s;
 }
 
+// W[t * ldw + j] = D[t * ldd + j] as BF16 (exact for uint8) for j < m, zero for
+// m <= j < ldw; 16 pixels per thread, blockIdx.y = frame.
+__global__ void widen_kernel(const uint8_t* __restrict__ D, int64_t m, int64_t ldd, uint16_t* __restrict__ W,
+                             int64_t ldw) {
+    const int64_t t = blockIdx.y;
+    const int64_t j = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 16;
+    if (j >= ldw) return;
+    const uint8_t* src = D + t * ldd + j;
+    uint32_t b[4];
+    if (j + 16 <= m) {
+        const uint4 raw = *reinterpret_cast<const uint4*>(src);
+        b[0] = raw.x; b[1] = raw.y; b[2] = raw.z; b[3] = raw.w;
+    } else {
+        // the last chunk of a row: read only the bytes below m
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            b[w] = 0u;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (j + 4 * w + e < m) b[w] |= static_cast<uint32_t>(src[4 * w + e]) << (8 * e);
+        }
+    }
+    uint32_t o[8];
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float f0 = __uint_as_float(__byte_perm(b[w], 0x4B000000u, 0x7540u + 2u * e)) - 8388608.0f;
+            const float f1 = __uint_as_float(__byte_perm(b[w], 0x4B000000u, 0x7541u + 2u * e)) - 8388608.0f;
+            o[2 * w + e] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+        }
+    uint4* dst = reinterpret_cast<uint4*>(W + t * ldw + j);
+    dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
 // DY_g[t*k + i] = sum_s part_g[(s*n_g + t)*k + i], FP64, fixed order; blockIdx.y = clip.
 __global__ void sketch_tc_reduce_kernel(const SketchArgs a, int splits, double* DY0, double* DY1, int* status) {
     const int g = blockIdx.y;
@@ -460,7 +544,7 @@ __global__ void sketch_tc_reduce_kernel(const SketchArgs a, int splits, double* 
 // Shared memory of a CTA in the given shape (bytes, with room to align the
 // base to 1024); larger than kMaxSmem when the shape does not fit.
 size_t sketch_tc_smem_bytes(int mtiles, int nclips, int n0, int n1) {
-    return smem_layout(mtiles, nclips, n0, n1).total + 1024;
+    return smem_layout(mtiles, nclips, n0, n1, false).total + 1024;
 }
 
 bool sketch_tc_pair_fits(int n0, int n1) {
@@ -470,14 +554,34 @@ bool sketch_tc_pair_fits(int n0, int n1) {
 
 namespace {
 
-// One launch: nclips (1 or 2) clips of <= 256 frames, each its own DY.
+// One launch: nclips (1 or 2) clips of <= 256 frames, each its own DY.  With
+// `wide` the frames are first widened to BF16 copies in the workspace and the
+// sketch's tensor copies land in the B operand directly.
 cdmd_status launch_sketch_tc_unit(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
-                                  const int64_t* ldd, int k, uint64_t seed, double* const* DY, cudaStream_t stream) {
+                                  const int64_t* ldd, int k, uint64_t seed, double* const* DY, bool wide,
+                                  cudaStream_t stream) {
     const int mtiles = nclips == 1 ? 2 : 1;
     CUtensorMap tmap[2];
-    for (int g = 0; g < nclips; ++g) {
-        cdmd_status st = make_video_tmap(&tmap[g], D[g], m, n[g], ldd[g], kKStep, n[g]);
+    if (wide) {
+        const int64_t ldw = (m + 15) / 16 * 16;
+        size_t elems = 0;
+        for (int g = 0; g < nclips; ++g) elems += static_cast<size_t>(n[g]) * ldw;
+        uint16_t* W = nullptr;
+        cdmd_status st = ensure_buffer(ctx, BUF_SKETCH_WIDE, elems * sizeof(uint16_t), reinterpret_cast<void**>(&W));
         if (st != CDMD_OK) return st;
+        for (int g = 0; g < nclips; ++g) {
+            const unsigned bx = static_cast<unsigned>((ldw / 16 + 255) / 256);
+            widen_kernel<<<dim3(bx, static_cast<unsigned>(n[g])), 256, 0, stream>>>(D[g], m, ldd[g], W, ldw);
+            CDMD_CHECK_LAUNCH("widen_kernel");
+            st = make_wide_tmap(&tmap[g], W, m, n[g], ldw, n[g]);
+            if (st != CDMD_OK) return st;
+            W += static_cast<size_t>(n[g]) * ldw;
+        }
+    } else {
+        for (int g = 0; g < nclips; ++g) {
+            cdmd_status st = make_video_tmap(&tmap[g], D[g], m, n[g], ldd[g], kKStep, n[g]);
+            if (st != CDMD_OK) return st;
+        }
     }
     if (nclips == 1) tmap[1] = tmap[0];
     const int rowblks = (k + 128 * mtiles - 1) / (128 * mtiles);
@@ -503,12 +607,18 @@ cdmd_status launch_sketch_tc_unit(cdmd_ctx* ctx, int nclips, const uint8_t* cons
     a.steps_per_split = steps_per_split;
     a.total_steps = total_steps;
     a.key = seed_key(seed);
-    const size_t smem = sketch_tc_smem_bytes(mtiles, nclips, a.n[0], a.n[1]);
+    const size_t smem = smem_layout(mtiles, nclips, a.n[0], a.n[1], wide).total + 1024;
     if (smem > kMaxSmem) return fail(CDMD_ERR_UNSUPPORTED, "sketch: %zu bytes of shared memory per CTA", smem);
-    CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem)));
-    sketch_tc_kernel<<<dim3(rowblks, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(tmap[0], tmap[1], a,
-                                                                                             ctx->d_status);
+    const dim3 grid(rowblks, static_cast<unsigned>(splits));
+    if (wide) {
+        CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem)));
+        sketch_tc_kernel<true><<<grid, kThreads, smem, stream>>>(tmap[0], tmap[1], a, ctx->d_status);
+    } else {
+        CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem)));
+        sketch_tc_kernel<false><<<grid, kThreads, smem, stream>>>(tmap[0], tmap[1], a, ctx->d_status);
+    }
     CDMD_CHECK_LAUNCH("sketch_tc_kernel");
     const int64_t tot = static_cast<int64_t>(k) * std::max(a.n[0], a.n[1]);
     sketch_tc_reduce_kernel<<<dim3(static_cast<unsigned>((tot + 255) / 256), nclips), 256, 0, stream>>>(
@@ -536,7 +646,7 @@ cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, 
         const int nc = std::min(kMaxFrames, n - t0);
         const uint8_t* Dc = D + static_cast<int64_t>(t0) * ldd;
         double* DYc = DY + static_cast<int64_t>(t0) * k;
-        st = launch_sketch_tc_unit(ctx, 1, &Dc, m, &nc, &ldd, k, seed, &DYc, stream);
+        st = launch_sketch_tc_unit(ctx, 1, &Dc, m, &nc, &ldd, k, seed, &DYc, false, stream);
         if (st != CDMD_OK) return st;
     }
     return CDMD_OK;
@@ -549,8 +659,10 @@ cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* co
         if (st != CDMD_OK) return st;
     }
     for (int i = 0; i < nclips;) {
-        if (i + 1 < nclips && sketch_tc_pair_fits(n[i], n[i + 1])) {
-            cdmd_status st = launch_sketch_tc_unit(ctx, 2, D + i, m, n + i, ldd + i, k, seed, DY + i, stream);
+        // a pair of clips of <= 256 frames each shares the generator; the
+        // widened frames keep the pair's shared memory within one CTA
+        if (i + 1 < nclips && n[i] <= kMaxFrames && n[i + 1] <= kMaxFrames) {
+            cdmd_status st = launch_sketch_tc_unit(ctx, 2, D + i, m, n + i, ldd + i, k, seed, DY + i, true, stream);
             if (st != CDMD_OK) return st;
             i += 2;
         } else {

@@ -55,11 +55,17 @@ def _compare(C, batch, clips, ctx, prec, selector):
         assert np.mean(a != b) <= 2e-4, (i, np.mean(a != b))
         v = batch.views(i)
         # the sketch matches the per-clip sketch up to the order of its FP32
-        # partial sums (the batch sums longer pixel ranges per partial)
+        # partial sums: the batch may sum a clip's whole pixel range into one
+        # partial (8 K16 products per 64-pixel step).  Accumulation in tensor
+        # memory is not round-to-nearest: each add may lose up to an ulp of
+        # the partial, the same way each time, so the error of a partial
+        # grows with its length (terms x 2^-24 relative at worst); half that
+        # bounds the difference between two partitions
         DYt = C.cdmd_sketch(ctx, c["D"], c["k"], c["seed"], prec=prec)
         DY = DYt.cpu().numpy()
+        terms = 8 * -(-m // 64)
         assert np.abs(v["DY"] - DY).max() <= 5e-5 * np.abs(DY).max()
-        assert np.linalg.norm(v["DY"] - DY) <= 1e-5 * np.linalg.norm(DY)
+        assert np.linalg.norm(v["DY"] - DY) <= max(1e-5, 0.5 * terms * 2.0 ** -24) * np.linalg.norm(DY)
         # and so do the eigenvalues of the decomposition
         dec = C.cdmd_decompose(ctx, DYt, c["r"], c["K"], selector=selector)
         C.cdmd_status_sync(ctx)

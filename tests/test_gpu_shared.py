@@ -49,7 +49,8 @@ def _clips(w, h, ns, seed0):
 
 # (w, h, frames of each clip, k): pairs of several row blocks and K steps, a
 # ragged pixel count, rows not a multiple of 128, a clip longer than 256
-# frames (sketched alone, in chunks), a pair too large for one CTA (alone)
+# frames (sketched alone, in chunks), a pair of 240-frame clips (BF16 frame
+# copies, which a pair of staged clips would not fit), an odd clip out
 CASES = [(160, 120, (100, 120), 200), (97, 61, (37, 200), 203), (64, 33, (256, 128), 300),
          (384, 160, (200, 200), 1000), (300, 40, (16, 16), 513), (48, 32, (300, 40), 120),
          (80, 48, (240, 240), 96), (112, 80, (150, 61, 77), 260)]
