@@ -555,7 +555,10 @@ def run_ours(args, rank, world, local_rank):
         achieved = 2.0 * counts["sketch_flops"] / (sketch_ms * 1e-3) / 1e12     # hi + lo tensor products
         peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": dram_traffic("sketch_tc.cu"), "kernel": "sketch (tcgen05 BF16 hi+lo)",
+                "traffic": dram_traffic("sketch_tc.cu"),
+                "kernel": ("sketch (tcgen05 BF16 hi+lo" + (", two clips per launch under one C; time per clip "
+                                                           "includes the widen pass and the reduce)" if cps > 1
+                                                           else "; time includes the reduce)")),
                 "peak_source": f"{peak_src} bf16 sustained"}
     else:
         fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
