@@ -231,6 +231,14 @@ cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, 
 // consecutive clips share the generator two at a time where they fit.
 cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
                                     const int64_t* ldd, int k, uint64_t seed, double* const* DY, cudaStream_t stream);
+// Pass (c) on the tensor cores for mask-only MODULUS / REAL calls with
+// 32 <= n <= 256 frames, ncols <= 16 and a 16-byte aligned video; lam_t and
+// amp are the lambda^t table [n][nc_pad] and the amplitudes (float2 each).
+bool subtract_tc_supported(int n, int ncols, cdmd_bgmode mode, const uint8_t* D, int64_t ldd, int64_t m,
+                           const float* bg);
+cdmd_status launch_subtract_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const float* Phi,
+                               int ncols, const void* lam_t, const void* amp, int nc_pad, float tau, cdmd_bgmode mode,
+                               uint32_t* mask, cudaStream_t stream);
 cdmd_status launch_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                                  const cdmd_measure* meas, double* DY, cudaStream_t stream);
 cdmd_status launch_measure_sparse_count(cdmd_ctx* ctx, int64_t m, int k, uint64_t seed,

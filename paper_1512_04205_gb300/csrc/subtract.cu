@@ -636,6 +636,8 @@ cdmd_status launch_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, i
     const Table tb = table_views(tbl, n, nc_pad);
     subtract_table_kernel<<<1, 32, 0, stream>>>(cols, ncols, nc_pad, beta, lambda, r, n, tb);
     CDMD_CHECK_LAUNCH("subtract_table_kernel");
+    if (subtract_tc_supported(n, ncols, mode, D, ldd, m, bg))
+        return launch_subtract_tc(ctx, D, m, n, ldd, Phi, ncols, tb.table, tb.amp, nc_pad, tau, mode, mask, stream);
     const float2* ph = reinterpret_cast<const float2*>(Phi);
     // TMA needs a 16-byte aligned base and row stride; n <= 512 keeps the
     // lambda^t table within shared memory next to the stages
