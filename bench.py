@@ -645,7 +645,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--inflight", type=int, default=8, help="steps in flight per GPU (streams)")
+    ap.add_argument("--inflight", type=int, default=12, help="steps in flight per GPU (streams)")
     ap.add_argument("--clips-per-step", type=int, choices=[1, 2], default=WORKLOAD["clips_per_step"],
                     help="clips per step, all under one C (2: one draw of C feeds both)")
     ap.add_argument("--batch", action="store_true",
