@@ -188,16 +188,21 @@ lift_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, const
                 uint8_t* blk = dst + (fg >> 3) * kPix * 128;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
+                    // pixel qq of the 8 this item holds: rotated by lane, so the
+                    // warp's 16-byte stores hit every swizzle phase (row & 7)
+                    // and no bank twice per wavefront
+                    const uint32_t qq = static_cast<uint32_t>(q + lane) & 7u;
+                    const uint32_t sel0 = 0x7540u | (qq & 3u);   // byte qq&3 under exponent 2^23
                     uint32_t w[4];
 #pragma unroll
                     for (int e2 = 0; e2 < 4; ++e2) {
-                        const uint32_t w0 = (q < 4) ? raw[2 * e2].x : raw[2 * e2].y;
-                        const uint32_t w1 = (q < 4) ? raw[2 * e2 + 1].x : raw[2 * e2 + 1].y;
-                        const float f0 = __uint_as_float(0x4B000000u | ((w0 >> (8 * (q & 3))) & 0xFFu)) - 8388608.0f;
-                        const float f1 = __uint_as_float(0x4B000000u | ((w1 >> (8 * (q & 3))) & 0xFFu)) - 8388608.0f;
+                        const uint32_t w0 = (qq < 4u) ? raw[2 * e2].x : raw[2 * e2].y;
+                        const uint32_t w1 = (qq < 4u) ? raw[2 * e2 + 1].x : raw[2 * e2 + 1].y;
+                        const float f0 = __uint_as_float(__byte_perm(w0, 0x4B000000u, sel0)) - 8388608.0f;
+                        const float f1 = __uint_as_float(__byte_perm(w1, 0x4B000000u, sel0)) - 8388608.0f;
                         w[e2] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
                     }
-                    *reinterpret_cast<uint4*>(blk + tc::sw128_offset(static_cast<uint32_t>(pg * 8 + q),
+                    *reinterpret_cast<uint4*>(blk + tc::sw128_offset(static_cast<uint32_t>(pg * 8) + qq,
                                                                      static_cast<uint32_t>(fg & 7))) =
                         make_uint4(w[0], w[1], w[2], w[3]);
                 }
