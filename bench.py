@@ -4,11 +4,12 @@
 Workload: seeded synthetic 1920x1080 grayscale clips of 200 frames
 (textured low-rank background, 3 moving rectangles, +-10 % illumination
 drift, noise sigma 3; k = 1000 Gaussian measurements drawn in-kernel from
-Philox, target rank r = 20, K = 10 background modes, threshold 25 grey), two
-per GPU (the second rendered on the device), all seen through one
+Philox, target rank r = 20, K = 10 background modes, threshold 25 grey), five
+per GPU (the others rendered on the device), all seen through one
 measurement matrix C (one camera, one sensing matrix, video processed window
-by window).  A step is one pass of the whole hot path over the two clips:
-    sketch of both (one C draw feeds both) -> per clip: decompose -> lift
+by window).  A step is one pass of the whole hot path over the five clips:
+    sketch of all (frames widened to BF16 and packed 512 to a launch, one
+    draw of C feeding every frame of it) -> per clip: decompose -> lift
     (selected modes) -> subtract + bit-pack.
 value = frames processed by all ranks / wall time of the timed steps (max over
 ranks); the clips (415 MB each) are resident in HBM and larger than L2, so
@@ -17,7 +18,7 @@ launching stream; the sketch is the dominant kernel and carries the roofline.
 --clips-per-step 1 times the one-clip step (no sharing of C).
 
 e2e: the same metric through cdmd_run_host_shared with pinned host buffers
-(both clips copied in and both masks copied out every step).
+(every clip copied in and every mask copied out, every step).
 cpu_baseline / --impl reference: the FP64 oracle on the host cores, on a
 bounded pixel sample of the clip, scaled to the full frame.
 
@@ -39,7 +40,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(width=1920, height=1080, n=200, k=1000, r=20, K=10, tau=25.0, drift=0.1, clip_seed=2024,
-                c_seed=0x5EED1080, clips_per_step=2)
+                c_seed=0x5EED1080, clips_per_step=5)
 METRIC = "cDMD 1080p frames/s"
 UNIT = "frames/s"
 
@@ -80,16 +81,18 @@ def fmeasure(pred, truth):
     return 2 * prec * rec / (prec + rec) if prec + rec > 0 else 0.0
 
 
-def launches_per_step(selector, K, clips=1):
-    """Kernels one pipeline step over `clips` clips launches: sketch 2 per
-    launch of one clip or a pair sharing C (tiles + fixed-order reduce); per
-    clip: decompose 15 (Gram 2, tridiagonalisation 1, eigenpairs 1,
+def launches_per_step(selector, K, clips=1, n=200):
+    """Kernels one pipeline step over `clips` clips of n frames launches:
+    sketch 2 for one clip (tiles + fixed-order reduce), or for several clips
+    under one C a widen pass per clip and 2 per packed launch of up to 512
+    frames; per clip: decompose 15 (Gram 2, tridiagonalisation 1, eigenpairs 1,
     orthonormalise 1, back-transform 1, B 1, A~ 1, eig FP32 1, Newton 1,
     FP64 QR fallback 1, order 1, G 1, Gram-form H 1, selection 1) + 2 for the
     learned selection (scoring, least squares on its picks, then the OMP
     launch that exits at once unless the picks were rejected); lift one per
     16 modes; subtract 2 (lambda^t table + pass)."""
-    return 2 * ((clips + 1) // 2) + clips * (15 + (2 if selector == "mlp" else 0) + (K + 15) // 16 + 2)
+    sketch = 2 if clips == 1 else clips + 2 * (-(-clips * n // 512))
+    return sketch + clips * (15 + (2 if selector == "mlp" else 0) + (K + 15) // 16 + 2)
 
 
 def algorithmic_counts():
@@ -556,8 +559,9 @@ def run_ours(args, rank, world, local_rank):
         peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": dram_traffic("sketch_tc.cu"),
-                "kernel": ("sketch (tcgen05 BF16 hi+lo" + (", two clips per launch under one C; time per clip "
-                                                           "includes the widen pass and the reduce)" if cps > 1
+                "kernel": ("sketch (tcgen05 BF16 hi+lo" + (f", {cps} clips under one C packed 512 frames to a "
+                                                           "launch; time per clip includes the widen passes and "
+                                                           "the reduces)" if cps > 1
                                                            else "; time includes the reduce)")),
                 "peak_source": f"{peak_src} bf16 sustained"}
     else:
@@ -579,7 +583,8 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": workload_name(args.prec, args.selector), "selector": args.selector, "m": m, "n": n, "k": k, "r": r, "K": K,
                        "tau": w["tau"], "clips_per_step": cps,
                        "measurement": ("gaussian (Philox4x32-10, in-kernel); one C for all clips"
-                                       + (", one draw of C feeds both clips of a step" if cps > 1 else "")),
+                                       + (", one draw of C feeds every frame of a packed launch"
+                                          if cps > 1 else "")),
                        "precision": ("sketch+lift BF16 hi+lo on tcgen05, FP32 accumulation; FP64 small solves"
                                      if args.prec == "bf16x2" else "sketch+lift FP32 FMA; FP64 small solves"),
                        "l2": f"clip {m * n / 1e6:.0f} MB each vs 129 MB L2 (no flush)",
@@ -591,7 +596,7 @@ def run_ours(args, rank, world, local_rank):
             "pass_roofline": {"lift_gbs": lift_gbs, "lift_frac_hbm": lift_gbs / hbm, "subtract_gbs": sub_gbs,
                               "subtract_frac_hbm": sub_gbs / hbm, "hbm_peak_gbs": hbm},
             "roofline": roof,
-            "gpu_launches": launches_per_step(args.selector, K, cps) * steps,
+            "gpu_launches": launches_per_step(args.selector, K, cps, n) * steps,
             "e2e": e2e}
     if piped_clocks is not None:
         line["clocks"] = piped_clocks
@@ -646,8 +651,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--inflight", type=int, default=12, help="steps in flight per GPU (streams)")
-    ap.add_argument("--clips-per-step", type=int, choices=[1, 2], default=WORKLOAD["clips_per_step"],
-                    help="clips per step, all under one C (2: one draw of C feeds both)")
+    ap.add_argument("--clips-per-step", type=int, choices=range(1, 9), default=WORKLOAD["clips_per_step"],
+                    help="clips per step, all under one C (>= 2: their frames are packed 512 to a sketch "
+                         "launch, so one draw of C feeds all of them)")
     ap.add_argument("--batch", action="store_true",
                     help="also measure a batch of 64 clips of mixed size (grouped launches, graph, autotuner)")
     ap.add_argument("--size", default=None,

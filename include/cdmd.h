@@ -191,16 +191,17 @@ cdmd_status cdmd_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64
  * for each clip, one C): DY[i] = C D[i] for i < nclips, where every clip has
  * the same pixel count m and C is drawn from the same (ctype, k, seed) as
  * cdmd_sketch draws it.  This is the case of one camera (one sensing matrix)
- * whose video is processed window by window.  With prec = CDMD_PREC_BF16X2
- * and a Gaussian C, consecutive clips of <= 256 frames (pairs whose frame
- * counts fit one CTA's shared memory, about n0 + n1 <= 430) are sketched
- * together: each entry of C drawn feeds both clips, halving the generator's
- * work per clip; the others, and every other precision or C, go one by one
- * as cdmd_sketch would.  D[i], n[i], ldd[i], DY[i] as for cdmd_sketch; the
- * four arrays are host arrays of nclips entries (D[i], DY[i] device
- * pointers).  Results agree with cdmd_sketch's up to the rounding order of
- * the split partial sums.  CDMD_ERR_INVALID_ARG (naming the clip) for
- * nclips < 1 or any argument cdmd_sketch would reject. */
+ * whose video is processed window by window.  With prec = CDMD_PREC_BF16X2,
+ * a Gaussian C and nclips >= 2, each clip's frames are first widened to a
+ * BF16 copy in the context's workspace (2 m n bytes per clip), then the
+ * frames of all clips are packed 512 to a launch: each entry of C drawn
+ * feeds every frame of the launch, whichever clip it belongs to.  A single
+ * clip, and every other precision or C, go as cdmd_sketch would.  D[i],
+ * n[i], ldd[i], DY[i] as for cdmd_sketch; the four arrays are host arrays of
+ * nclips entries (D[i], DY[i] device pointers).  Results agree with
+ * cdmd_sketch's up to the rounding order of the split partial sums.
+ * CDMD_ERR_INVALID_ARG (naming the clip) for nclips < 1 or any argument
+ * cdmd_sketch would reject. */
 cdmd_status cdmd_sketch_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m,
                                const int* n, const int64_t* ldd, cdmd_ctype ctype, int k,
                                uint64_t seed, cdmd_prec prec, double* const* DY, void* stream);

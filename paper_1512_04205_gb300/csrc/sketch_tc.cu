@@ -8,27 +8,31 @@
 // touches HBM.
 //
 // One persistent CTA per SM owns a block of C rows and a contiguous pixel
-// range, in one of two shapes (tensor memory holds two 256-column FP32
-// accumulators of 128 rows):
-//   solo    two 128-row tiles of C (256 rows) against one clip's frames
-//   shared  one 128-row tile of C against the frames of two clips that use
-//           the same C (same pixel count, seed and k): each Gaussian drawn
-//           feeds both clips, halving the generator's work per clip
-// The frames of a clip (n <= 256) are the MMA N.  Per 64-pixel K step and
-// pipeline stage:
-//   warp 0      TMA: D[frames][64 pixels] uint8 box of each clip -> staging
-//   warp 1      one thread issues, per accumulator, 4 K16 steps x (hi, lo)
-//               tcgen05.mma (M 128, N = frames padded to 16, K 16) and
-//               commits to the stage's barrier
-//   warps 4-11  draw the C block (rows x 64 pixels) and write hi / lo BF16
-//               tiles in the 128-byte swizzled K-major layout (A operands)
-//   warps 2-11  convert the staged bytes to BF16 in the same layout (B
-//               operands, rows = frames), an even share each
+// range.  Tensor memory holds 512 FP32 columns of 128 rows: every Gaussian a
+// CTA draws is applied to as many frames as fit there.
+//   per clip   two 128-row tiles of C against one clip's frames (n <= 256 per
+//              launch).  Warp 0 TMA-loads the uint8 bytes (64 pixels x n
+//              frames per K step) into a staging buffer and warps 2-11
+//              convert them to BF16 B tiles in the 128-byte swizzled layout.
+//   packed     one 128-row tile of C against up to 512 frames of several
+//              clips under the same C (same pixel count, k and seed: windows
+//              of one camera).  The frames, widened to BF16 copies in HBM
+//              beforehand (`widen_kernel`), are cut into segments packed into
+//              two 256-row slots; each segment's tensor copy lands in the B
+//              operand directly, so the conversion is done once per clip and
+//              not again in every row block.
+// In both, warp 1 issues tcgen05.mma (M 128, N = frames per slot padded to
+// 16, K 16, hi and lo) into the accumulators and commits to the stage's
+// barrier, and warps 4-11 draw the C block (rows x 64 pixels) from Philox,
+// split into BF16 hi / lo A tiles.
 // After the last K step warps 4-7 read the accumulators (tcgen05.ld) and write
 // FP32 partials [split][frame][row]; a second kernel sums the splits in FP64.
 // Every mbarrier wait is bounded in time; on a timeout the CTA records
 // CDMD_ERR_TIMEOUT, drains its copies and MMAs, frees TMEM and returns.
 #include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "tc_common.cuh"
 #include "batch_internal.cuh"
@@ -94,7 +98,6 @@ namespace {
 
 constexpr int kThreads = 384;
 constexpr int kWorkers = 320;               // warps 2-11
-constexpr int kGen = 256;                   // warps 4-11
 constexpr int kStages = 2;
 constexpr int kKStep = 64;                  // pixels per K step (one 128-byte BF16 row)
 constexpr int kTileBytes = 128 * 128;       // 128 rows x 128 bytes
@@ -140,7 +143,7 @@ struct SmemLayout {
     uint32_t a_off, b_off, dst_off, bar_off, misc_off, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int mtiles, int nclips, int n0, int n1, bool wide) {
+__host__ __device__ inline SmemLayout smem_layout(int mtiles, int nclips, int n0, int n1) {
     SmemLayout L;
     L.a_stage = 2u * static_cast<uint32_t>(mtiles) * kTileBytes;
     uint32_t b = 0, d = 0;
@@ -150,7 +153,7 @@ __host__ __device__ inline SmemLayout smem_layout(int mtiles, int nclips, int n0
         if (g < nclips) {
             const int n = g ? n1 : n0;
             b += static_cast<uint32_t>(pad16(n)) * 128u;
-            if (!wide) d += (static_cast<uint32_t>(n) * kKStep + 127u) / 128u * 128u;
+            d += (static_cast<uint32_t>(n) * kKStep + 127u) / 128u * 128u;
         }
     }
     L.b_stage = (b + 1023u) / 1024u * 1024u;
@@ -164,20 +167,75 @@ __host__ __device__ inline SmemLayout smem_layout(int mtiles, int nclips, int n0
     return L;
 }
 
+// Draw this thread's share of one K step of C: mtiles items of 4 rows x 8
+// pixels (gt + 256 h, h < mtiles) of the rows row0 .. row0 + 128 mtiles - 1
+// and pixels j0 .. j0 + 63, split into BF16 hi / lo and stored in the A
+// stage's 128-byte swizzled K-major tiles (hi, lo per 128-row tile).  Rows
+// past k and pixels past m are zero.
+__device__ __forceinline__ void draw_c_tiles(uint8_t* a_stage, int gt, int mtiles, int row0, int k, int64_t j0,
+                                             int64_t m, const PhiloxKeys& rk) {
+#pragma unroll 1
+    for (int h = 0; h < mtiles; ++h) {
+        const int it = gt + 256 * h;
+        const int g = it & 7;        // 8-pixel group within the K step
+        const int q = it >> 3;       // quad of rows within the block (0 .. 32 mtiles - 1)
+        const int mt = q >> 5;
+        const uint32_t row_t = static_cast<uint32_t>(4 * (q & 31));
+        const uint32_t gq = static_cast<uint32_t>((row0 >> 2) + q);
+        float z[4][8];
+        const int64_t jg = j0 + 8 * g;
+        if (row0 + 4 * q < k && jg + 8 <= m) {
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), rk);
+                box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
+                box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
+            }
+        } else if (row0 + 4 * q < k) {
+            // pixels past m (last K step only) are drawn and then zeroed
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), rk);
+                box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
+                box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
+                const bool in = (jg + p) < m;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) z[e][p] = in ? z[e][p] : 0.0f;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int p = 0; p < 8; ++p) z[e][p] = 0.0f;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int p2 = 0; p2 < 4; ++p2) {
+                const float a = z[e][2 * p2], b = z[e][2 * p2 + 1];
+                const uint32_t ua = __float_as_uint(a) & 0xFFFF0000u;   // hi by truncation
+                const uint32_t ub = __float_as_uint(b) & 0xFFFF0000u;
+                hi[p2] = __byte_perm(ua, ub, 0x7632);
+                lo[p2] = tc::pack_bf16_rn(a - __uint_as_float(ua), b - __uint_as_float(ub));
+            }
+            const uint32_t off = tc::sw128_offset(row_t + e, static_cast<uint32_t>(g));
+            *reinterpret_cast<uint4*>(a_stage + (mt * 2 + 0) * kTileBytes + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(a_stage + (mt * 2 + 1) * kTileBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+}
+
 // One CTA's share of C D: the rows of C in row block U.rowblk (128 mtiles
 // rows) over the 64-pixel K steps step0 .. step0+nsteps-1, against each of
 // U.nclips clips, written to U.part[g][t * k + row] (this split's partial
 // sums).  Used by the per-clip and the grouped launch.
-//   kWide = false   U.tmap[g] maps the uint8 frames; the bytes are staged and
-//                   converted to BF16 by warps 2-11
-//   kWide = true    U.tmap[g] maps a BF16 copy of the frames (128-byte
-//                   swizzle): the tensor copy lands in the B operand itself
-//                   and warps 2-3 stay idle
-template <bool kWide>
+// U.tmap[g] maps the uint8 frames; the bytes are staged and converted to BF16
+// by warps 2-11.
 __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status, uint8_t* smem) {
     const int nclips = U.nclips, mtiles = U.mtiles, k = U.k;
     const int n0 = U.n[0], n1 = nclips > 1 ? U.n[1] : 0;
-    const SmemLayout L = smem_layout(mtiles, nclips, n0, n1, kWide);
+    const SmemLayout L = smem_layout(mtiles, nclips, n0, n1);
     uint8_t* A = smem + L.a_off;
     uint8_t* B = smem + L.b_off;
     uint8_t* Dst = smem + L.dst_off;
@@ -199,7 +257,7 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
         for (int s = 0; s < kStages; ++s) {
             tc::mbar_init(&tma_full[s], 1);
             tc::mbar_init(&d_free[s], kWorkers);
-            tc::mbar_init(&ab_full[s], kWide ? kGen : kWorkers);
+            tc::mbar_init(&ab_full[s], kWorkers);
             tc::mbar_init(&mma_done[s], 1);
         }
         tc::mbar_init(accum_done, 1);
@@ -228,21 +286,17 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            const uint32_t bytes = static_cast<uint32_t>(n0 + n1) * (kWide ? 128u : static_cast<uint32_t>(kKStep));
+            const uint32_t bytes = static_cast<uint32_t>(n0 + n1) * kKStep;
             for (int64_t ks = 0; ks < nsteps; ++ks) {
                 const int s = static_cast<int>(ks % kStages);
                 const uint32_t u = static_cast<uint32_t>(ks / kStages);
-                // the slot is free once its bytes were converted (staged) or
-                // its B tiles were read by the MMAs (wide)
-                if (u >= 1 && !tc::mbar_wait(kWide ? &mma_done[s] : &d_free[s], (u - 1) & 1u, abort_flag, status))
-                    break;
+                // the slot is free once its bytes were converted
+                if (u >= 1 && !tc::mbar_wait(&d_free[s], (u - 1) & 1u, abort_flag, status)) break;
                 tc::mbar_arrive_expect_tx(&tma_full[s], bytes);
                 const int x = static_cast<int>((U.step0 + ks) * kKStep);
-                for (int g = 0; g < nclips; ++g) {
-                    uint8_t* dst = kWide ? B + s * L.b_stage + (g ? L.b_clip[1] : 0u)
-                                         : Dst + s * L.dst_stage + (g ? L.dst_clip[1] : 0u);
-                    tc::tma_load_2d(dst, g ? U.tmap[1] : U.tmap[0], x, 0, &tma_full[s]);
-                }
+                for (int g = 0; g < nclips; ++g)
+                    tc::tma_load_2d(Dst + s * L.dst_stage + (g ? L.dst_clip[1] : 0u), g ? U.tmap[1] : U.tmap[0], x, 0,
+                                    &tma_full[s]);
             }
             // drain: the last load of each stage must have landed before exit
             for (int s = 0; s < kStages; ++s) {
@@ -259,7 +313,6 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
                 const int s = static_cast<int>(ks % kStages);
                 const uint32_t par = static_cast<uint32_t>(ks / kStages) & 1u;
                 if (!tc::mbar_wait(&ab_full[s], par, abort_flag, status)) break;
-                if (kWide && !tc::mbar_wait(&tma_full[s], par, abort_flag, status)) break;
                 tc::tc_fence_after();
                 const uint32_t a_base = tc::smem_u32(A + s * L.a_stage);
                 const uint32_t b_base = tc::smem_u32(B + s * L.b_stage);
@@ -291,70 +344,12 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
         const int row0 = U.rowblk * 128 * mtiles;
         const int conv0 = n0 * 8, conv_total = (n0 + n1) * 8;
         const PhiloxKeys rk = philox_round_keys(U.key);   // the same for every draw of this CTA
-        for (int64_t ks = 0; ks < ((kWide && !gen) ? 0 : nsteps); ++ks) {
+        for (int64_t ks = 0; ks < nsteps; ++ks) {
             const int s = static_cast<int>(ks % kStages);
             const uint32_t u = static_cast<uint32_t>(ks / kStages);
             if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
             if (gen) {
-                const int64_t j0 = (U.step0 + ks) * kKStep;
-                uint8_t* a_stage = A + s * L.a_stage;
-#pragma unroll 1
-                for (int h = 0; h < mtiles; ++h) {
-                    const int it = gt + 256 * h;
-                    const int g = it & 7;        // 8-pixel group within the K step
-                    const int q = it >> 3;       // quad of rows within the block (0 .. 32 mtiles - 1)
-                    const int mt = q >> 5;
-                    const uint32_t row_t = static_cast<uint32_t>(4 * (q & 31));
-                    const uint32_t gq = static_cast<uint32_t>((row0 >> 2) + q);
-                    float z[4][8];
-                    const int64_t jg = j0 + 8 * g;
-                    if (row0 + 4 * q < k && jg + 8 <= U.m) {
-#pragma unroll
-                        for (int p = 0; p < 8; ++p) {
-                            const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), rk);
-                            box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
-                            box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
-                        }
-                    } else if (row0 + 4 * q < k) {
-                        // pixels past m (last K step only) are drawn and then zeroed
-#pragma unroll
-                        for (int p = 0; p < 8; ++p) {
-                            const uint4 wv = philox4x32_10(make_uint4(static_cast<uint32_t>(jg + p), gq, 0u, 0u), rk);
-                            box_muller_fast(wv.x, wv.y, z[0][p], z[1][p]);
-                            box_muller_fast(wv.z, wv.w, z[2][p], z[3][p]);
-                            const bool in = (jg + p) < U.m;
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) z[e][p] = in ? z[e][p] : 0.0f;
-                        }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-#pragma unroll
-                            for (int p = 0; p < 8; ++p) z[e][p] = 0.0f;
-                    }
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        uint32_t hi[4], lo[4];
-#pragma unroll
-                        for (int p2 = 0; p2 < 4; ++p2) {
-                            const float a = z[e][2 * p2], b = z[e][2 * p2 + 1];
-                            const uint32_t ua = __float_as_uint(a) & 0xFFFF0000u;   // hi by truncation
-                            const uint32_t ub = __float_as_uint(b) & 0xFFFF0000u;
-                            hi[p2] = __byte_perm(ua, ub, 0x7632);
-                            lo[p2] = tc::pack_bf16_rn(a - __uint_as_float(ua), b - __uint_as_float(ub));
-                        }
-                        const uint32_t off = tc::sw128_offset(row_t + e, static_cast<uint32_t>(g));
-                        *reinterpret_cast<uint4*>(a_stage + (mt * 2 + 0) * kTileBytes + off) =
-                            make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                        *reinterpret_cast<uint4*>(a_stage + (mt * 2 + 1) * kTileBytes + off) =
-                            make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                    }
-                }
-            }
-            if (kWide) {
-                tc::fence_proxy_async_smem();
-                tc::mbar_arrive(&ab_full[s]);
-                continue;
+                draw_c_tiles(A + s * L.a_stage, gt, mtiles, row0, k, (U.step0 + ks) * kKStep, U.m, rk);
             }
             // uint8 -> BF16: 8 pixels of one frame per item, over both clips
             if (!tc::mbar_wait(&tma_full[s], u & 1u, abort_flag, status)) break;
@@ -433,7 +428,6 @@ struct SketchArgs {
     uint2 key;
 };
 
-template <bool kWide>
 __global__ void __launch_bounds__(kThreads, 1)
 sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap0, const __grid_constant__ CUtensorMap tmap1,
                  const SketchArgs a, int* status) {
@@ -457,7 +451,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap0, const __grid_constan
     U.mtiles = a.mtiles;
     U.k = a.k;
     U.rowblk = blockIdx.x;
-    sketch_tc_body<kWide>(U, status, smem);
+    sketch_tc_body(U, status, smem);
 }
 
 // Grouped launch: CTA b runs work item items[b] (any clip or clip pair, frame
@@ -467,7 +461,7 @@ sketch_tc_grouped_kernel(const SketchItem* __restrict__ items, int* status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const SketchItem it = items[blockIdx.x];
-    sketch_tc_body<false>(it, status, smem);
+    sketch_tc_body(it, status, smem);
 }
 
 // Grouped fixed-order reduce: element idx of the concatenated outputs belongs
@@ -488,6 +482,200 @@ __global__ void sketch_reduce_grouped_kernel(const ReduceChunk* __restrict__ chu
     for (int sp = 0; sp < c.splits; ++sp) s += static_cast<double>(c.part[static_cast<int64_t>(sp) * c.elems + e]);
     if (!isfinite(s)) record_status(status, CDMD_ERR_NONFINITE);
     c.DY[e] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Packed form: the frames of several clips under one C, cut into segments of
+// consecutive frames and packed into two 256-row B slots (512 rows = the 512
+// FP32 columns of tensor memory).  One 128-row tile of C per CTA: each
+// Gaussian drawn feeds up to 512 frames of whichever clips the launch holds.
+// Segments start on 8-row boundaries (1024-byte swizzle atoms) and never
+// cross a slot; a segment's frames come from the BF16 copy of its clip by
+// one tensor copy of box 64 pixels x L frames.  Rows no segment covers stay
+// zero.  Partials are [split][B row][k]; a reduce per segment writes the
+// clip's DY columns f0 .. f0 + L - 1.
+// ---------------------------------------------------------------------------
+constexpr int kPackRows = 512;
+constexpr int kMaxSeg = 8;
+constexpr uint32_t kPackBStage = kPackRows * 128u;     // bytes of one B stage
+constexpr uint32_t kPackAStage = 2u * kTileBytes;      // hi, lo of one 128-row tile
+
+struct PackSeg {
+    double* DY;        // the clip's DY (frame-major, k per frame)
+    int row0, L, f0;   // B rows row0 .. row0 + L - 1 hold frames f0 .. f0 + L - 1
+    int pad;
+};
+
+struct PackArgs {
+    CUtensorMap tmap[kMaxSeg];   // per segment: the clip's BF16 frames, box 64 x L
+    PackSeg seg[kMaxSeg];
+    float* part;                 // [splits][kPackRows][k]
+    int nseg, k;
+    int nslot[2];                // rows of each slot the MMAs cover (multiples of 16, 0 = unused)
+    int64_t m, steps_per_split, total_steps;
+    uint2 key;
+};
+
+__host__ __device__ inline uint32_t pack_smem_bytes() {
+    return kStages * (kPackAStage + kPackBStage) + (3 * kStages + 1) * 8 + 64;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+sketch_tc_packed_kernel(const __grid_constant__ PackArgs a, int* status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t* A = smem;
+    uint8_t* B = smem + kStages * kPackAStage;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(B + kStages * kPackBStage);
+    uint64_t* tma_full = bars;
+    uint64_t* ab_full = bars + kStages;
+    uint64_t* mma_done = bars + 2 * kStages;
+    uint64_t* accum_done = bars + 3 * kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int k = a.k;
+    const int split = blockIdx.y;
+    const int row0 = blockIdx.x * 128;
+    const int64_t step0 = static_cast<int64_t>(split) * a.steps_per_split;
+    int64_t nsteps = a.total_steps - step0;
+    if (nsteps > a.steps_per_split) nsteps = a.steps_per_split;
+    if (nsteps < 0) nsteps = 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&tma_full[s], 1);
+            tc::mbar_init(&ab_full[s], 256);
+            tc::mbar_init(&mma_done[s], 1);
+        }
+        tc::mbar_init(accum_done, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    // rows no segment covers must read as zero: clear both B stages once
+    for (uint32_t off = tid * 16u; off < kStages * kPackBStage; off += kThreads * 16u)
+        *reinterpret_cast<uint4*>(B + off) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_proxy_async_smem();
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            uint32_t bytes = 0;
+            for (int i = 0; i < a.nseg; ++i) bytes += static_cast<uint32_t>(a.seg[i].L) * 128u;
+            for (int64_t ks = 0; ks < nsteps; ++ks) {
+                const int s = static_cast<int>(ks % kStages);
+                const uint32_t u = static_cast<uint32_t>(ks / kStages);
+                // the slot's B rows are free once the MMAs that read them finished
+                if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
+                tc::mbar_arrive_expect_tx(&tma_full[s], bytes);
+                const int x = static_cast<int>((step0 + ks) * kKStep);
+                for (int i = 0; i < a.nseg; ++i)
+                    tc::tma_load_2d(B + s * kPackBStage + static_cast<uint32_t>(a.seg[i].row0) * 128u, &a.tmap[i], x,
+                                    a.seg[i].f0, &tma_full[s]);
+            }
+            for (int s = 0; s < kStages; ++s) {
+                const int64_t uses = (nsteps - s + kStages - 1) / kStages;
+                if (uses >= 1) tc::mbar_wait(&tma_full[s], static_cast<uint32_t>(uses - 1) & 1u, abort_flag, status);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc0 = tc::idesc_bf16_f32(128, a.nslot[0] > 0 ? a.nslot[0] : 16);
+            const uint32_t idesc1 = tc::idesc_bf16_f32(128, a.nslot[1] > 0 ? a.nslot[1] : 16);
+            for (int64_t ks = 0; ks < nsteps; ++ks) {
+                const int s = static_cast<int>(ks % kStages);
+                const uint32_t par = static_cast<uint32_t>(ks / kStages) & 1u;
+                if (!tc::mbar_wait(&ab_full[s], par, abort_flag, status)) break;
+                if (!tc::mbar_wait(&tma_full[s], par, abort_flag, status)) break;
+                tc::tc_fence_after();
+                const uint32_t a_base = tc::smem_u32(A + s * kPackAStage);
+                const uint32_t b_base = tc::smem_u32(B + s * kPackBStage);
+#pragma unroll
+                for (int slot = 0; slot < 2; ++slot) {
+                    if (a.nslot[slot] == 0) continue;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t bdesc = tc::desc_sw128(b_base + slot * (kPackBStage / 2) + kk * 32);
+#pragma unroll
+                        for (int hl = 0; hl < 2; ++hl) {
+                            const uint64_t adesc = tc::desc_sw128(a_base + hl * kTileBytes + kk * 32);
+                            tc::mma_bf16(tmem_base + slot * kAccCols, adesc, bdesc, slot ? idesc1 : idesc0,
+                                         (ks | kk | hl) ? 1u : 0u);
+                        }
+                    }
+                }
+                tc::mma_commit(&mma_done[s]);
+            }
+            tc::mma_commit(accum_done);
+        }
+    } else if (warp >= 4) {
+        // ---------------- C generators (warps 4-11) ----------------
+        const int gt = tid - 128;
+        const PhiloxKeys rk = philox_round_keys(a.key);
+        for (int64_t ks = 0; ks < nsteps; ++ks) {
+            const int s = static_cast<int>(ks % kStages);
+            const uint32_t u = static_cast<uint32_t>(ks / kStages);
+            if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
+            draw_c_tiles(A + s * kPackAStage, gt, 1, row0, k, (step0 + ks) * kKStep, a.m, rk);
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&ab_full[s]);
+        }
+        // ---------------- epilogue (warps 4-7): partials of every used B row ----------------
+        if (warp < 8) {
+            const bool ok = tc::mbar_wait(accum_done, 0u, abort_flag, status) && !*abort_flag;
+            tc::tc_fence_after();
+            if (ok) {
+                const int quarter = warp & 3;
+                const int row = row0 + quarter * 32 + lane;
+                float* part = a.part + static_cast<int64_t>(split) * kPackRows * k;
+                for (int slot = 0; slot < 2; ++slot) {
+                    for (int c0 = 0; c0 < a.nslot[slot]; c0 += 16) {
+                        uint32_t v[16];
+                        tc::tmem_ld_x16(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + slot * kAccCols + c0,
+                                        v);
+                        tc::tmem_wait_ld();
+                        if (row < k) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                part[static_cast<int64_t>(slot * 256 + c0 + q) * k + row] = __uint_as_float(v[q]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        if (*abort_flag) tc::mbar_wait(accum_done, 0u, abort_flag, status, 2000000000ull);
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+// DY of segment blockIdx.y: DY[(f0 + t) k + i] = sum_s part[s][row0 + t][i], FP64, fixed order.
+__global__ void sketch_packed_reduce_kernel(const __grid_constant__ PackArgs a, int splits, int* status) {
+    const PackSeg sg = a.seg[blockIdx.y];
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t total = static_cast<int64_t>(sg.L) * a.k;
+    if (idx >= total) return;
+    const int64_t src = static_cast<int64_t>(sg.row0) * a.k + idx;
+    double s = 0.0;
+    for (int sp = 0; sp < splits; ++sp) s += static_cast<double>(a.part[static_cast<int64_t>(sp) * kPackRows * a.k + src]);
+    if (!isfinite(s)) record_status(status, CDMD_ERR_NONFINITE);
+    sg.DY[static_cast<int64_t>(sg.f0) * a.k + idx] = s;
 }
 
 // W[t * ldw + j] = D[t * ldd + j] as BF16 (exact for uint8) for j < m, zero for
@@ -544,7 +732,7 @@ __global__ void sketch_tc_reduce_kernel(const SketchArgs a, int splits, double* 
 // Shared memory of a CTA in the given shape (bytes, with room to align the
 // base to 1024); larger than kMaxSmem when the shape does not fit.
 size_t sketch_tc_smem_bytes(int mtiles, int nclips, int n0, int n1) {
-    return smem_layout(mtiles, nclips, n0, n1, false).total + 1024;
+    return smem_layout(mtiles, nclips, n0, n1).total + 1024;
 }
 
 bool sketch_tc_pair_fits(int n0, int n1) {
@@ -554,34 +742,14 @@ bool sketch_tc_pair_fits(int n0, int n1) {
 
 namespace {
 
-// One launch: nclips (1 or 2) clips of <= 256 frames, each its own DY.  With
-// `wide` the frames are first widened to BF16 copies in the workspace and the
-// sketch's tensor copies land in the B operand directly.
+// One launch: nclips (1 or 2) clips of <= 256 frames, each its own DY.
 cdmd_status launch_sketch_tc_unit(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
-                                  const int64_t* ldd, int k, uint64_t seed, double* const* DY, bool wide,
-                                  cudaStream_t stream) {
+                                  const int64_t* ldd, int k, uint64_t seed, double* const* DY, cudaStream_t stream) {
     const int mtiles = nclips == 1 ? 2 : 1;
     CUtensorMap tmap[2];
-    if (wide) {
-        const int64_t ldw = (m + 15) / 16 * 16;
-        size_t elems = 0;
-        for (int g = 0; g < nclips; ++g) elems += static_cast<size_t>(n[g]) * ldw;
-        uint16_t* W = nullptr;
-        cdmd_status st = ensure_buffer(ctx, BUF_SKETCH_WIDE, elems * sizeof(uint16_t), reinterpret_cast<void**>(&W));
+    for (int g = 0; g < nclips; ++g) {
+        cdmd_status st = make_video_tmap(&tmap[g], D[g], m, n[g], ldd[g], kKStep, n[g]);
         if (st != CDMD_OK) return st;
-        for (int g = 0; g < nclips; ++g) {
-            const unsigned bx = static_cast<unsigned>((ldw / 16 + 255) / 256);
-            widen_kernel<<<dim3(bx, static_cast<unsigned>(n[g])), 256, 0, stream>>>(D[g], m, ldd[g], W, ldw);
-            CDMD_CHECK_LAUNCH("widen_kernel");
-            st = make_wide_tmap(&tmap[g], W, m, n[g], ldw, n[g]);
-            if (st != CDMD_OK) return st;
-            W += static_cast<size_t>(n[g]) * ldw;
-        }
-    } else {
-        for (int g = 0; g < nclips; ++g) {
-            cdmd_status st = make_video_tmap(&tmap[g], D[g], m, n[g], ldd[g], kKStep, n[g]);
-            if (st != CDMD_OK) return st;
-        }
     }
     if (nclips == 1) tmap[1] = tmap[0];
     const int rowblks = (k + 128 * mtiles - 1) / (128 * mtiles);
@@ -607,18 +775,12 @@ cdmd_status launch_sketch_tc_unit(cdmd_ctx* ctx, int nclips, const uint8_t* cons
     a.steps_per_split = steps_per_split;
     a.total_steps = total_steps;
     a.key = seed_key(seed);
-    const size_t smem = smem_layout(mtiles, nclips, a.n[0], a.n[1], wide).total + 1024;
+    const size_t smem = smem_layout(mtiles, nclips, a.n[0], a.n[1]).total + 1024;
     if (smem > kMaxSmem) return fail(CDMD_ERR_UNSUPPORTED, "sketch: %zu bytes of shared memory per CTA", smem);
-    const dim3 grid(rowblks, static_cast<unsigned>(splits));
-    if (wide) {
-        CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem)));
-        sketch_tc_kernel<true><<<grid, kThreads, smem, stream>>>(tmap[0], tmap[1], a, ctx->d_status);
-    } else {
-        CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem)));
-        sketch_tc_kernel<false><<<grid, kThreads, smem, stream>>>(tmap[0], tmap[1], a, ctx->d_status);
-    }
+    CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem)));
+    sketch_tc_kernel<<<dim3(rowblks, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(tmap[0], tmap[1], a,
+                                                                                             ctx->d_status);
     CDMD_CHECK_LAUNCH("sketch_tc_kernel");
     const int64_t tot = static_cast<int64_t>(k) * std::max(a.n[0], a.n[1]);
     sketch_tc_reduce_kernel<<<dim3(static_cast<unsigned>((tot + 255) / 256), nclips), 256, 0, stream>>>(
@@ -646,7 +808,7 @@ cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, 
         const int nc = std::min(kMaxFrames, n - t0);
         const uint8_t* Dc = D + static_cast<int64_t>(t0) * ldd;
         double* DYc = DY + static_cast<int64_t>(t0) * k;
-        st = launch_sketch_tc_unit(ctx, 1, &Dc, m, &nc, &ldd, k, seed, &DYc, false, stream);
+        st = launch_sketch_tc_unit(ctx, 1, &Dc, m, &nc, &ldd, k, seed, &DYc, stream);
         if (st != CDMD_OK) return st;
     }
     return CDMD_OK;
@@ -658,20 +820,82 @@ cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* co
         cdmd_status st = check_tc_video(D[i], ldd[i]);
         if (st != CDMD_OK) return st;
     }
-    for (int i = 0; i < nclips;) {
-        // a pair of clips of <= 256 frames each shares the generator; the
-        // widened frames keep the pair's shared memory within one CTA
-        if (i + 1 < nclips && n[i] <= kMaxFrames && n[i + 1] <= kMaxFrames) {
-            cdmd_status st = launch_sketch_tc_unit(ctx, 2, D + i, m, n + i, ldd + i, k, seed, DY + i, true, stream);
+    if (nclips == 1) return launch_sketch_tc(ctx, D[0], m, n[0], ldd[0], CDMD_C_GAUSSIAN, k, seed, DY[0], stream);
+    // BF16 copies of every clip's frames (one HBM-bound pass each)
+    const int64_t ldw = (m + 15) / 16 * 16;
+    size_t elems = 0;
+    for (int i = 0; i < nclips; ++i) elems += static_cast<size_t>(n[i]) * ldw;
+    uint16_t* W = nullptr;
+    cdmd_status st = ensure_buffer(ctx, BUF_SKETCH_WIDE, elems * sizeof(uint16_t), reinterpret_cast<void**>(&W));
+    if (st != CDMD_OK) return st;
+    std::vector<const uint16_t*> Wc(nclips);
+    for (int i = 0; i < nclips; ++i) {
+        const unsigned bx = static_cast<unsigned>((ldw / 16 + 255) / 256);
+        widen_kernel<<<dim3(bx, static_cast<unsigned>(n[i])), 256, 0, stream>>>(D[i], m, ldd[i], W, ldw);
+        CDMD_CHECK_LAUNCH("widen_kernel");
+        Wc[i] = W;
+        W += static_cast<size_t>(n[i]) * ldw;
+    }
+    // launches of up to 512 packed frames
+    const int rowblks = (k + 127) / 128;
+    const int64_t total_steps = (m + kKStep - 1) / kKStep;
+    int64_t splits = std::max<int64_t>(1, ctx->num_sms / rowblks);
+    splits = std::min<int64_t>(splits, total_steps);
+    const int64_t steps_per_split = (total_steps + splits - 1) / splits;
+    splits = (total_steps + steps_per_split - 1) / steps_per_split;
+    float* part = nullptr;
+    st = ensure_buffer(ctx, BUF_SKETCH_PARTIAL, static_cast<size_t>(splits) * kPackRows * k * sizeof(float),
+                       reinterpret_cast<void**>(&part));
+    if (st != CDMD_OK) return st;
+    const size_t smem = pack_smem_bytes() + 1024;
+    CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem)));
+    PackArgs a{};
+    a.part = part;
+    a.k = k;
+    a.m = m;
+    a.steps_per_split = steps_per_split;
+    a.total_steps = total_steps;
+    a.key = seed_key(seed);
+    int rows = 0;     // B rows used so far in this launch (a multiple of 8)
+    auto flush = [&]() -> cdmd_status {
+        if (a.nseg == 0) return CDMD_OK;
+        a.nslot[0] = rows >= 256 ? 256 : (rows + 15) / 16 * 16;
+        a.nslot[1] = rows > 256 ? (rows - 256 + 15) / 16 * 16 : 0;
+        int maxL = 0;
+        for (int i = 0; i < a.nseg; ++i) maxL = std::max(maxL, a.seg[i].L);
+        sketch_tc_packed_kernel<<<dim3(rowblks, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(
+            a, ctx->d_status);
+        CDMD_CHECK_LAUNCH("sketch_tc_packed_kernel");
+        const int64_t tot = static_cast<int64_t>(maxL) * k;
+        sketch_packed_reduce_kernel<<<dim3(static_cast<unsigned>((tot + 255) / 256), a.nseg), 256, 0, stream>>>(
+            a, static_cast<int>(splits), ctx->d_status);
+        CDMD_CHECK_LAUNCH("sketch_packed_reduce_kernel");
+        a.nseg = 0;
+        rows = 0;
+        return CDMD_OK;
+    };
+    for (int i = 0; i < nclips; ++i) {
+        for (int f = 0; f < n[i];) {
+            if (a.nseg == kMaxSeg || rows == kPackRows) {
+                st = flush();
+                if (st != CDMD_OK) return st;
+            }
+            const int space = 256 - (rows & 255);            // rows left in the current slot
+            const int L = std::min(n[i] - f, space);
+            PackSeg& sg = a.seg[a.nseg];
+            sg.DY = DY[i];
+            sg.row0 = rows;
+            sg.L = L;
+            sg.f0 = f;
+            st = make_wide_tmap(&a.tmap[a.nseg], Wc[i], m, n[i], ldw, L);
             if (st != CDMD_OK) return st;
-            i += 2;
-        } else {
-            cdmd_status st = launch_sketch_tc(ctx, D[i], m, n[i], ldd[i], CDMD_C_GAUSSIAN, k, seed, DY[i], stream);
-            if (st != CDMD_OK) return st;
-            i += 1;
+            ++a.nseg;
+            rows += (L + 7) / 8 * 8;
+            f += L;
         }
     }
-    return CDMD_OK;
+    return flush();
 }
 
 cdmd_status launch_sketch_grouped(const SketchItem* items, int nitems, size_t smem, const ReduceChunk* chunks,

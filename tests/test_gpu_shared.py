@@ -47,13 +47,15 @@ def _clips(w, h, ns, seed0):
     return [videogen.make_clip(w, h, n, seed=seed0 + i, drift=0.05) for i, n in enumerate(ns)]
 
 
-# (w, h, frames of each clip, k): pairs of several row blocks and K steps, a
-# ragged pixel count, rows not a multiple of 128, a clip longer than 256
-# frames (sketched alone, in chunks), a pair of 240-frame clips (BF16 frame
-# copies, which a pair of staged clips would not fit), an odd clip out
+# (w, h, frames of each clip, k): several row blocks and K steps, a ragged
+# pixel count, rows not a multiple of 128, clips longer than 256 frames (cut
+# into segments), five 200-frame clips (two packed launches, clips split
+# across slots and launches), nine 16-frame clips (more segments than one
+# launch takes), frame counts that are not multiples of 8 or 16
 CASES = [(160, 120, (100, 120), 200), (97, 61, (37, 200), 203), (64, 33, (256, 128), 300),
          (384, 160, (200, 200), 1000), (300, 40, (16, 16), 513), (48, 32, (300, 40), 120),
-         (80, 48, (240, 240), 96), (112, 80, (150, 61, 77), 260)]
+         (80, 48, (240, 240), 96), (112, 80, (150, 61, 77), 260), (96, 64, (200,) * 5, 400),
+         (64, 48, (16,) * 9, 64), (72, 40, (511, 3, 90), 130)]
 
 
 @pytest.mark.parametrize("w,h,ns,k", CASES)
