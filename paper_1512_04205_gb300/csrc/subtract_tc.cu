@@ -270,6 +270,7 @@ subtract_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SubTcArgs a, 
             const int64_t tile = blockIdx.x + li * gridDim.x;
             const int64_t p = tile * kPix + row;
             const bool valid = p < a.m;
+            const bool warp_full = __all_sync(0xffffffffu, valid);
             const int64_t widx = tile * (kPix / 32) + quarter;
             const uint8_t* xs = Dst + s * L.d_stage + row;
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + 256u * h;
@@ -281,25 +282,47 @@ subtract_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SubTcArgs a, 
                 // all 16 grey levels first (independent loads that overlap the
                 // tensor-memory load), then the decisions and ballots
                 uint32_t xv[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) xv[q] = q < nq ? xs[(c0 + q) * kPix] : 0u;
-                tc::tmem_wait_ld();
                 uint32_t keep = 0u;
+                if (nq == 16 && warp_full) {
+                    // a full chunk of a warp whose pixels are all below m:
+                    // no per-frame or per-pixel guards
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    // grey level as a float: 2^23 + x, exact, minus 2^23
-                    const float x = __uint_as_float(0x4B000000u | xv[q]) - 8388608.0f;
-                    const float r = __uint_as_float(re[q]);
-                    float bgv;
-                    if (kReal) {
-                        bgv = r;
-                    } else {
-                        const float i2 = __uint_as_float(im[q]);
-                        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(bgv) : "f"(fmaf(r, r, i2 * i2)));
+                    for (int q = 0; q < 16; ++q) xv[q] = xs[(c0 + q) * kPix];
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        // grey level as a float: 2^23 + x, exact, minus 2^23
+                        const float x = __uint_as_float(0x4B000000u | xv[q]) - 8388608.0f;
+                        const float r = __uint_as_float(re[q]);
+                        float bgv;
+                        if (kReal) {
+                            bgv = r;
+                        } else {
+                            const float i2 = __uint_as_float(im[q]);
+                            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(bgv) : "f"(fmaf(r, r, i2 * i2)));
+                        }
+                        const uint32_t w = __ballot_sync(0xffffffffu, fabsf(x - bgv) > tau);
+                        keep = lane == q ? w : keep;
                     }
-                    const bool fg = fabsf(x - bgv) > tau;
-                    const uint32_t w = __ballot_sync(0xffffffffu, fg && valid && q < nq);
-                    keep = lane == q ? w : keep;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) xv[q] = q < nq ? xs[(c0 + q) * kPix] : 0u;
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float x = __uint_as_float(0x4B000000u | xv[q]) - 8388608.0f;
+                        const float r = __uint_as_float(re[q]);
+                        float bgv;
+                        if (kReal) {
+                            bgv = r;
+                        } else {
+                            const float i2 = __uint_as_float(im[q]);
+                            asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(bgv) : "f"(fmaf(r, r, i2 * i2)));
+                        }
+                        const bool fg = fabsf(x - bgv) > tau;
+                        const uint32_t w = __ballot_sync(0xffffffffu, fg && valid && q < nq);
+                        keep = lane == q ? w : keep;
+                    }
                 }
                 if (lane < nq && widx < a.words_per_frame)
                     a.mask[static_cast<int64_t>(c0 + lane) * a.words_per_frame + widx] = keep;
