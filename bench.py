@@ -322,14 +322,30 @@ def run_batch_measure(C, SEL, torch, dev, args, model):
     seq_ms = e0.elapsed_time(e1)
     pix_frames = sum(int(c["D"].shape[0]) * int(c["D"].shape[1]) for c in clips)
     batch.close()
+    # the same batch as per-clip launches on lanes (one graph, no grouped passes)
+    lanes_b = C.Batch(clips, BATCH["tau"], prec=args.prec, selector=args.selector, autotune=True, grouped=False,
+                      graph=True, lanes=8, selector_blob=model)
+    lanes_b.run()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        lanes_b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    lanes_b.status_sync()
+    lanes_ms = e0.elapsed_time(e1) / reps
+    lanes_tune = lanes_b.tuning()
+    lanes_b.close()
     return {"clips": len(clips), "frames": frames_total, "pixel_frames": pix_frames,
             "value": frames_total / (ms * 1e-3), "unit": "frames/s", "ms_per_batch": ms,
             "gpixel_frames_per_s": pix_frames / (ms * 1e-3) / 1e9,
             "sequential_cdmd_run": {"value": frames_total / (seq_ms * 1e-3), "ms_per_batch": seq_ms},
+            "per_clip_lanes": {"value": frames_total / (lanes_ms * 1e-3), "ms_per_batch": lanes_ms,
+                               "tuning": lanes_tune},
             "tuning": tune, "plan_s": plan_s,
             "config": {"sizes": BATCH["sizes"], "n": [BATCH["n_lo"], BATCH["n_hi"]], "k": "min(1000, 4n)",
-                       "r": [BATCH["r_lo"], BATCH["r_hi"]], "K": BATCH["K"], "launch": "grouped sketch + subtract, "
-                       "per-clip small solves and lifts on lanes, one CUDA graph"}}
+                       "r": [BATCH["r_lo"], BATCH["r_hi"]], "K": BATCH["K"], "launch": "grouped sketch + subtract "
+                       "per wave of clips, per-clip small solves and lifts on lanes, one CUDA graph"}}
 
 
 # ----------------------------------------------------------------------------

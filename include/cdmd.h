@@ -379,12 +379,14 @@ cdmd_status cdmd_batch_views(cdmd_batch* batch, int clip, double** DY, double** 
                              int32_t** sel, float** Phi);
 
 /* The knobs the plan runs with: lanes (streams), the SM cap of each lane's
- * full-data passes (0 = none), the sketch work-item size (64-pixel steps per
- * CTA) and the subtract work-item size (pixel tiles per CTA) of the grouped
- * launches, and the measured time of one run in milliseconds (0 if not
- * autotuned). */
-cdmd_status cdmd_batch_tuning(cdmd_batch* batch, int32_t* lanes, int32_t* sm_limit, int32_t* sketch_steps,
-                              int32_t* subtract_tiles, float* run_ms);
+ * full-data passes (0 = none), the number of waves the grouped passes are
+ * split into (0 without CDMD_BATCH_GROUPED; the small solves of one wave
+ * overlap the grouped sketch of the next), the sketch work-item size
+ * (64-pixel steps per CTA) and the subtract work-item size (pixel tiles per
+ * CTA) of the grouped launches, and the measured time of one run in
+ * milliseconds (0 if not autotuned).  Any output pointer may be NULL. */
+cdmd_status cdmd_batch_tuning(cdmd_batch* batch, int32_t* lanes, int32_t* sm_limit, int32_t* waves,
+                              int32_t* sketch_steps, int32_t* subtract_tiles, float* run_ms);
 
 void cdmd_batch_destroy(cdmd_batch* batch);
 

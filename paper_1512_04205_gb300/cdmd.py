@@ -116,6 +116,7 @@ def load_library(path=LIB_PATH):
         "cdmd_batch_status_sync": [vp, vp],
         "cdmd_batch_views": [vp, ctypes.c_int] + [ctypes.POINTER(vp)] * 5,
         "cdmd_batch_tuning": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                              ctypes.POINTER(i32),
                               ctypes.POINTER(flt)],
         "cdmd_batch_destroy": [vp],
         "cdmd_copy": [vp, vp, ctypes.c_size_t, vp],
@@ -567,11 +568,11 @@ class Batch:
         _check(self.lib.cdmd_batch_status_sync(self.handle, _stream(stream)))
 
     def tuning(self):
-        v = [ctypes.c_int32() for _ in range(4)]
+        v = [ctypes.c_int32() for _ in range(5)]
         ms = ctypes.c_float()
         _check(self.lib.cdmd_batch_tuning(self.handle, *[ctypes.byref(x) for x in v], ctypes.byref(ms)))
-        return dict(lanes=v[0].value, sm_limit=v[1].value, sketch_steps=v[2].value, subtract_tiles=v[3].value,
-                    run_ms=ms.value)
+        return dict(lanes=v[0].value, sm_limit=v[1].value, waves=v[2].value, sketch_steps=v[3].value,
+                    subtract_tiles=v[4].value, run_ms=ms.value)
 
     def views(self, i, stream=None):
         """Host copies of clip i's DY (n, k), lambda (r,), beta (r,), sel (K,)."""

@@ -8,16 +8,21 @@
 //
 //   fork          the caller's stream -> every lane stream
 //   per lane      its clips in order: sketch -> decompose -> lift -> subtract
-//                 (or, with CDMD_BATCH_GROUPED, the sketch and subtract
-//                 passes of all clips as one grouped launch each on the
-//                 caller's stream, with the small solves and lifts on lanes)
 //   join          every lane -> the caller's stream
+//
+// With CDMD_BATCH_GROUPED the clips are split into waves of about equal work
+// and the sketch and subtract passes of each wave are one grouped launch
+// each: the waves' sketches run back to back on the caller's stream; when
+// wave w's sketch is done its clips' small solves and lifts run on the lanes,
+// and when those are done its grouped subtract runs on a stream of its own.
+// So the small solves of one wave overlap the sketch of the next.
 //
 // Clips are assigned to lanes longest-first (each to the least loaded lane,
 // by k m n), so uneven clips balance.  The autotuner times candidate knobs
 // on the batch itself (two runs each, the second timed with events) and
 // keeps the fastest: the lane count, the SM cap of the lanes' full-data
-// passes, and the work-item sizes of the grouped launches.
+// passes, the number of waves and the work-item sizes of the grouped
+// launches.
 #include <algorithm>
 #include <vector>
 
@@ -36,11 +41,19 @@ struct cdmd_batch {
     std::vector<cudaEvent_t> ev_join;
     cudaEvent_t ev_fork = nullptr;
     std::vector<int> lane_of;
+    // waves of the grouped passes
+    static constexpr int kMaxWaves = 8;
+    int waves = 1;
+    std::vector<std::vector<int>> wave_clips;
+    std::vector<cudaEvent_t> ev_wave_sketch;        // [kMaxWaves]
+    std::vector<cudaEvent_t> ev_lane_wave;          // [lanes_max * kMaxWaves]
+    cudaStream_t sub_stream = nullptr;
+    cudaEvent_t ev_sub_done = nullptr;
     // per-clip buffers (one allocation)
     void* pool = nullptr;
     std::vector<cdmd::ClipBuffers> buf;
-    // grouped passes
-    cdmd::GroupedPlan grouped;
+    // grouped passes, one plan per wave
+    std::vector<cdmd::GroupedPlan> grouped;
     int sketch_steps = 0;
     int subtract_tiles = 0;
     // graph
@@ -110,6 +123,15 @@ void assign_lanes(cdmd_batch* b) {
         b->lane_of[i] = l;
         load[l] += cost(i);
     }
+    // waves of about equal work, each listing its clips longest first
+    const int nw = std::max(1, std::min<int>(b->waves, static_cast<int>(nc)));
+    std::vector<double> wl(nw, 0.0);
+    b->wave_clips.assign(nw, std::vector<int>());
+    for (int i : order) {
+        const int w = static_cast<int>(std::min_element(wl.begin(), wl.end()) - wl.begin());
+        b->wave_clips[w].push_back(i);
+        wl[w] += cost(i);
+    }
 }
 
 }  // namespace
@@ -156,62 +178,100 @@ cdmd_status run_batch(cdmd_batch* b, cudaStream_t stream) {
         cdmd_ctx* c = b->ctx[l];
         c->num_sms = b->sm_limit > 0 ? std::min(b->sm_limit, c->device_sms) : c->device_sms;
     }
-    if (grouped_sketch_on(b)) {
-        cdmd_status st = grouped_sketch(&b->grouped, b->ctx[0]->d_status, stream);
-        if (st != CDMD_OK) return st;
-    }
     CDMD_CHECK_CUDA(cudaEventRecord(b->ev_fork, stream));
     for (int l = 0; l < b->lanes; ++l) CDMD_CHECK_CUDA(cudaStreamWaitEvent(b->streams[l], b->ev_fork, 0));
-    // longest clips first within each lane
-    std::vector<int> order(b->clips.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-        const cdmd_clip &x = b->clips[a], &y = b->clips[c];
-        return static_cast<double>(x.k) * x.m * x.n > static_cast<double>(y.k) * y.m * y.n;
-    });
-    for (int i : order) {
-        cdmd_status st = run_clip(b, i);
-        if (st != CDMD_OK) return st;
+    if (!grouped(b)) {
+        // every clip on its lane, longest first
+        std::vector<int> order(b->clips.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+            const cdmd_clip &x = b->clips[a], &y = b->clips[c];
+            return static_cast<double>(x.k) * x.m * x.n > static_cast<double>(y.k) * y.m * y.n;
+        });
+        for (int i : order) {
+            cdmd_status st = run_clip(b, i);
+            if (st != CDMD_OK) return st;
+        }
+    } else {
+        const int nw = static_cast<int>(b->wave_clips.size());
+        CDMD_CHECK_CUDA(cudaStreamWaitEvent(b->sub_stream, b->ev_fork, 0));
+        // the waves' grouped sketches, back to back on the caller's stream
+        for (int w = 0; w < nw; ++w) {
+            if (grouped_sketch_on(b)) {
+                cdmd_status st = grouped_sketch(&b->grouped[w], b->ctx[0]->d_status, stream);
+                if (st != CDMD_OK) return st;
+            }
+            CDMD_CHECK_CUDA(cudaEventRecord(b->ev_wave_sketch[w], stream));
+        }
+        for (int w = 0; w < nw; ++w) {
+            // small solves and lifts of wave w on the lanes, once its sketch is done
+            for (int l = 0; l < b->lanes; ++l)
+                CDMD_CHECK_CUDA(cudaStreamWaitEvent(b->streams[l], b->ev_wave_sketch[w], 0));
+            for (int i : b->wave_clips[w]) {
+                cdmd_status st = run_clip(b, i);
+                if (st != CDMD_OK) return st;
+            }
+            // then its grouped subtract on the subtract stream
+            for (int l = 0; l < b->lanes; ++l) {
+                cudaEvent_t e = b->ev_lane_wave[static_cast<size_t>(l) * cdmd_batch::kMaxWaves + w];
+                CDMD_CHECK_CUDA(cudaEventRecord(e, b->streams[l]));
+                CDMD_CHECK_CUDA(cudaStreamWaitEvent(b->sub_stream, e, 0));
+            }
+            cdmd_status st = grouped_subtract(&b->grouped[w], b->p.bgmode, b->p.tau, b->ctx[0]->d_status,
+                                              b->sub_stream);
+            if (st != CDMD_OK) return st;
+        }
+        CDMD_CHECK_CUDA(cudaEventRecord(b->ev_sub_done, b->sub_stream));
+        CDMD_CHECK_CUDA(cudaStreamWaitEvent(stream, b->ev_sub_done, 0));
     }
     for (int l = 0; l < b->lanes; ++l) {
         CDMD_CHECK_CUDA(cudaEventRecord(b->ev_join[l], b->streams[l]));
         CDMD_CHECK_CUDA(cudaStreamWaitEvent(stream, b->ev_join[l], 0));
     }
-    if (grouped(b)) return grouped_subtract(&b->grouped, b->p.bgmode, b->p.tau, b->ctx[0]->d_status, stream);
     return CDMD_OK;
 }
 
-std::vector<GroupedClip> grouped_clips(const cdmd_batch* b) {
-    std::vector<GroupedClip> g(b->clips.size());
-    for (size_t i = 0; i < g.size(); ++i) {
+std::vector<GroupedClip> grouped_clips(const cdmd_batch* b, int w) {
+    const std::vector<int>& ids = b->wave_clips[w];
+    std::vector<GroupedClip> g(ids.size());
+    for (size_t q = 0; q < ids.size(); ++q) {
+        const int i = ids[q];
         const cdmd_clip& c = b->clips[i];
-        g[i] = GroupedClip{c.D,       c.m,       c.n, c.ldd, c.k, c.r, ncols_of(b, c),
+        g[q] = GroupedClip{c.D,       c.m,       c.n, c.ldd, c.k, c.r, ncols_of(b, c),
                            b->p.selector == CDMD_SEL_LSTSQ ? 1 : 0, c.seed, &b->buf[i], c.mask};
     }
     return g;
 }
 
-// Configure lanes, SM cap and grouped item sizes, then run once eagerly
-// (sizes every workspace).
-cdmd_status configure(cdmd_batch* b, int lanes, int sm_limit, int sketch_steps, int subtract_tiles,
+// Configure lanes, SM cap, waves and grouped item sizes, then run once
+// eagerly (sizes every workspace).
+cdmd_status configure(cdmd_batch* b, int lanes, int sm_limit, int waves, int sketch_steps, int subtract_tiles,
                       cudaStream_t stream) {
+    const bool rebuild = b->lanes != lanes || b->waves != waves || b->grouped.empty() ||
+                         b->sketch_steps != sketch_steps || b->subtract_tiles != subtract_tiles ||
+                         sketch_steps <= 0 || subtract_tiles <= 0;
     b->lanes = lanes;
     b->sm_limit = sm_limit;
+    b->waves = waves;
     assign_lanes(b);
-    if (grouped(b) && (!b->grouped.built || sketch_steps <= 0 || subtract_tiles <= 0 ||
-                       b->grouped.sketch_steps != sketch_steps || b->grouped.subtract_tiles != subtract_tiles)) {
-        cdmd_status st = grouped_build(&b->grouped, grouped_clips(b), b->p.bgmode, sketch_steps, subtract_tiles,
-                                       b->ctx[0]->device_sms, stream);
-        if (st == CDMD_ERR_UNSUPPORTED) {
-            // clips the grouped kernels do not cover: per-clip launches
-            b->p.flags &= ~CDMD_BATCH_GROUPED;
-            clear_error();
-        } else if (st != CDMD_OK) {
-            return st;
+    if (grouped(b) && rebuild) {
+        for (GroupedPlan& g : b->grouped) grouped_free(&g);
+        b->grouped.assign(b->wave_clips.size(), GroupedPlan());
+        for (size_t w = 0; w < b->wave_clips.size(); ++w) {
+            cdmd_status st = grouped_build(&b->grouped[w], grouped_clips(b, static_cast<int>(w)), b->p.bgmode,
+                                           sketch_steps, subtract_tiles, b->ctx[0]->device_sms, stream);
+            if (st == CDMD_ERR_UNSUPPORTED) {
+                // clips the grouped kernels do not cover: per-clip launches
+                b->p.flags &= ~CDMD_BATCH_GROUPED;
+                clear_error();
+                break;
+            } else if (st != CDMD_OK) {
+                return st;
+            }
         }
     }
-    b->sketch_steps = grouped(b) ? b->grouped.sketch_steps : 0;
-    b->subtract_tiles = grouped(b) ? b->grouped.subtract_tiles : 0;
+    b->sketch_steps = grouped(b) ? b->grouped[0].sketch_steps : 0;
+    b->subtract_tiles = grouped(b) ? b->grouped[0].subtract_tiles : 0;
     cdmd_status st = run_batch(b, stream);
     if (st != CDMD_OK) return st;
     CDMD_CHECK_CUDA(cudaStreamSynchronize(stream));
@@ -239,58 +299,75 @@ cdmd_status time_run(cdmd_batch* b, cudaStream_t stream, float* ms) {
 cdmd_status autotune(cdmd_batch* b, cudaStream_t stream) {
     const int sms = b->ctx[0]->device_sms;
     struct Cand {
-        int lanes, sm_limit, sketch_steps, subtract_tiles;
+        int lanes, sm_limit, waves, sketch_steps, subtract_tiles;
     };
-    std::vector<Cand> cands;
-    const int lane_opts[] = {2, 4, 8};
-    const int cap_opts[] = {0, sms - 16, sms - 32};
-    for (int lo : lane_opts) {
-        if (lo > b->lanes_max) continue;
-        for (int co : cap_opts) cands.push_back({lo, co, b->sketch_steps, b->subtract_tiles});
-    }
     float best = 1e30f;
-    Cand pick = {b->lanes, b->sm_limit, b->sketch_steps, b->subtract_tiles};
-    for (const Cand& c : cands) {
-        cdmd_status st = configure(b, c.lanes, c.sm_limit, c.sketch_steps, c.subtract_tiles, stream);
+    Cand pick = {b->lanes, b->sm_limit, b->waves, b->sketch_steps, b->subtract_tiles};
+    auto trial = [&](const Cand& c, bool* better) -> cdmd_status {
+        cdmd_status st = configure(b, c.lanes, c.sm_limit, c.waves, c.sketch_steps, c.subtract_tiles, stream);
         if (st != CDMD_OK) return st;
         float ms = 0.0f;
         st = time_run(b, stream, &ms);
         if (st != CDMD_OK) return st;
-        if (ms < best) {
-            best = ms;
-            pick = c;
+        *better = ms < best;
+        if (*better) best = ms;
+        return CDMD_OK;
+    };
+    // lanes and SM cap
+    const int lane_opts[] = {2, 4, 8};
+    const int cap_opts[] = {0, sms - 16, sms - 32};
+    for (int lo : lane_opts) {
+        if (lo > b->lanes_max) continue;
+        for (int co : cap_opts) {
+            const Cand c = {lo, co, b->waves, 0, 0};
+            bool better = false;
+            cdmd_status st = trial(c, &better);
+            if (st != CDMD_OK) return st;
+            if (better) pick = {c.lanes, c.sm_limit, c.waves, b->sketch_steps, b->subtract_tiles};
         }
     }
     if (grouped(b)) {
-        // work-item sizes of the grouped passes at the chosen lanes / cap
-        const int step_opts[] = {b->sketch_steps / 2, b->sketch_steps, b->sketch_steps * 2};
+        // waves at the chosen lanes / cap
+        const int wave_opts[] = {1, 2, 4, 8};
+        for (int wo : wave_opts) {
+            if (wo > static_cast<int>(b->clips.size())) continue;
+            const Cand c = {pick.lanes, pick.sm_limit, wo, 0, 0};
+            bool better = false;
+            cdmd_status st = trial(c, &better);
+            if (st != CDMD_OK) return st;
+            if (better) pick = {c.lanes, c.sm_limit, wo, b->sketch_steps, b->subtract_tiles};
+        }
+        // work-item sizes of the grouped passes
+        const int base_steps = pick.sketch_steps > 0 ? pick.sketch_steps : 1;
+        const int step_opts[] = {base_steps / 2, base_steps, base_steps * 2};
         const int tile_opts[] = {1, 2, 4, 8};
         for (int so : step_opts) {
             if (so < 1) continue;
             for (int to : tile_opts) {
-                cdmd_status st = configure(b, pick.lanes, pick.sm_limit, so, to, stream);
+                const Cand c = {pick.lanes, pick.sm_limit, pick.waves, so, to};
+                bool better = false;
+                cdmd_status st = trial(c, &better);
                 if (st != CDMD_OK) return st;
-                float ms = 0.0f;
-                st = time_run(b, stream, &ms);
-                if (st != CDMD_OK) return st;
-                if (ms < best) {
-                    best = ms;
-                    pick.sketch_steps = so;
-                    pick.subtract_tiles = to;
-                }
+                if (better) pick = c;
             }
         }
     }
     b->run_ms = best;
-    return configure(b, pick.lanes, pick.sm_limit, pick.sketch_steps, pick.subtract_tiles, stream);
+    return configure(b, pick.lanes, pick.sm_limit, pick.waves, pick.sketch_steps, pick.subtract_tiles, stream);
 }
 
 void release(cdmd_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    grouped_free(&b->grouped);
+    for (GroupedPlan& g : b->grouped) grouped_free(&g);
     for (cudaEvent_t e : b->ev_join)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_wave_sketch)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_lane_wave)
+        if (e) cudaEventDestroy(e);
+    if (b->ev_sub_done) cudaEventDestroy(b->ev_sub_done);
+    if (b->sub_stream) cudaStreamDestroy(b->sub_stream);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     for (cudaStream_t s : b->streams)
         if (s) cudaStreamDestroy(s);
@@ -354,8 +431,18 @@ cdmd_status cdmd_batch_create(cdmd_batch** out, int device, const cdmd_clip* cli
         b->streams.push_back(ls);
         b->ev_join.push_back(ev);
     }
-    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_sub_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->sub_stream, cudaStreamNonBlocking) != cudaSuccess)
         return fail_out(cuda_fail(cudaGetLastError(), "cdmd_batch_create: events"));
+    b->ev_wave_sketch.assign(cdmd_batch::kMaxWaves, nullptr);
+    b->ev_lane_wave.assign(static_cast<size_t>(b->lanes_max) * cdmd_batch::kMaxWaves, nullptr);
+    for (cudaEvent_t& e : b->ev_wave_sketch)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return fail_out(cuda_fail(cudaGetLastError(), "cdmd_batch_create: events"));
+    for (cudaEvent_t& e : b->ev_lane_wave)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return fail_out(cuda_fail(cudaGetLastError(), "cdmd_batch_create: events"));
     const size_t bytes = plan_buffers(b, nullptr);
     if (cudaMalloc(&b->pool, bytes) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -364,7 +451,7 @@ cdmd_status cdmd_batch_create(cdmd_batch** out, int device, const cdmd_clip* cli
     plan_buffers(b, static_cast<char*>(b->pool));
     // default knobs, then (optionally) the autotuner, then the capture
     const int sms = b->ctx[0]->device_sms;
-    cdmd_status st = configure(b, b->lanes_max, b->lanes_max > 1 ? sms - 16 : 0, 0, 0, s);
+    cdmd_status st = configure(b, b->lanes_max, b->lanes_max > 1 ? sms - 16 : 0, grouped(b) ? 4 : 1, 0, 0, s);
     if (st != CDMD_OK) return fail_out(st);
     if (params->flags & CDMD_BATCH_AUTOTUNE) {
         st = autotune(b, s);
@@ -442,12 +529,13 @@ cdmd_status cdmd_batch_views(cdmd_batch* b, int clip, double** DY, double** lamb
     return CDMD_OK;
 }
 
-cdmd_status cdmd_batch_tuning(cdmd_batch* b, int32_t* lanes, int32_t* sm_limit, int32_t* sketch_steps,
-                              int32_t* subtract_tiles, float* run_ms) {
+cdmd_status cdmd_batch_tuning(cdmd_batch* b, int32_t* lanes, int32_t* sm_limit, int32_t* waves,
+                              int32_t* sketch_steps, int32_t* subtract_tiles, float* run_ms) {
     clear_error();
     CDMD_REQUIRE(b != nullptr, "batch is NULL");
     if (lanes) *lanes = b->lanes;
     if (sm_limit) *sm_limit = b->sm_limit;
+    if (waves) *waves = grouped(b) ? static_cast<int32_t>(b->wave_clips.size()) : 0;
     if (sketch_steps) *sketch_steps = b->sketch_steps;
     if (subtract_tiles) *subtract_tiles = b->subtract_tiles;
     if (run_ms) *run_ms = b->run_ms;

@@ -28,6 +28,7 @@ struct SketchItem;
 struct ReduceChunk;
 struct SubtractClip;
 struct SubtractItem;
+struct SubTcClip;
 struct GroupedPlan {
     bool built = false;
     int sketch_steps = 0;        // 64-pixel K steps per sketch work item
@@ -49,6 +50,11 @@ struct GroupedPlan {
     int sb_nitems = 0;
     int sb_nc = 0;
     int sb_max_n = 0;
+    // tensor-core subtract
+    const SubTcClip* tc_clips = nullptr;
+    const SubtractItem* tc_items = nullptr;
+    int tc_nitems = 0;
+    int tc_max_n = 0;
 };
 
 struct GroupedClip {             // what the grouped launches need of a clip
@@ -107,6 +113,27 @@ struct SubtractItem {
     int pad;
     int64_t tile0, ntiles;
 };
+// Tensor-core subtract of one clip inside a grouped launch (mask only,
+// MODULUS or REAL, 32 <= n <= 256, ncols <= 16, aligned video).
+struct SubTcClip {
+    const CUtensorMap* tmap;     // box 128 pixels x n frames, global memory
+    const float2* Phi;           // m x ncols complex
+    const float2* lam_t;         // lambda^t table [n][nc_pad]
+    const float2* amp;           // amplitude per column
+    uint32_t* mask;
+    int64_t m;
+    int n, ncols, nc_pad;
+    int pad;
+};
+size_t subtract_tc_smem(int n);
+int subtract_tc_tile_pixels();
+cdmd_status make_subtract_tc_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, int n, int64_t ldd);
+cdmd_status launch_subtract_tc_grouped(const SubTcClip* clips, const SubtractItem* items, int nitems, int max_n,
+                                       cdmd_bgmode mode, float tau, int* status, cudaStream_t stream);
+// Device addresses of the lambda^t table and the amplitudes inside a table
+// built by the grouped table kernel (column stride nc).
+void subtract_table_ptrs(void* table, int n, int nc, const float2** lam_t, const float2** amp);
+
 size_t subtract_table_bytes_nc(int n, int nc);
 size_t subtract_tma_smem(int n, int nc);
 int subtract_tile_pixels();

@@ -5,8 +5,11 @@
 //              two consecutive clips that share C, row block of C, range of
 //              `sketch_steps` 64-pixel K steps); FP32 partial sums per range,
 //              then one fixed-order FP64 reduce over all clips
-//   subtract   lambda^t tables (one warp per clip), then one CTA per range of
-//              `subtract_tiles` consecutive 960-pixel tiles of one clip
+//   subtract   lambda^t tables (one warp per clip), then on the tensor cores
+//              one CTA per range of consecutive 128-pixel tiles of a clip with
+//              32 <= n <= 256 frames (about one item per SM), and in the
+//              CUDA-core kernel one CTA per range of `subtract_tiles`
+//              consecutive 960-pixel tiles of every other clip
 //
 // Tensor maps, descriptors, partial sums and tables live in one device
 // allocation written once per work-item size, so the launches can be
@@ -37,7 +40,6 @@ void grouped_free(GroupedPlan* g) {
 
 cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips, cdmd_bgmode mode, int sketch_steps,
                           int subtract_tiles, int num_sms, cudaStream_t stream) {
-    (void)mode;
     int max_ncols = 0, max_n = 0;
     for (size_t i = 0; i < clips.size(); ++i) {
         const GroupedClip& c = clips[i];
@@ -105,12 +107,34 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
         part_floats += static_cast<int64_t>(ch.splits) * ch.nf * c.k;
     }
     for (const Unit& u : units) nsk += static_cast<int64_t>(unit_rowblks(u)) * chunks[u.c0].splits;
-    int64_t nsb = 0;
-    for (const GroupedClip& c : clips) {
-        const int64_t tiles = (c.m + tile_px - 1) / tile_px;
-        nsb += (tiles + subtract_tiles - 1) / subtract_tiles;
+    // the subtract of a clip runs on the tensor cores (mask only, MODULUS or
+    // REAL, 32 <= n <= 256) or else in the CUDA-core kernel
+    const int tc_px = subtract_tc_tile_pixels();
+    std::vector<int> tc_slot(clips.size(), -1);
+    int ntc_clips = 0, tc_max_n = 0;
+    int64_t tc_tiles_all = 0;
+    for (size_t i = 0; i < clips.size(); ++i) {
+        const GroupedClip& c = clips[i];
+        if (mode != CDMD_BG_STATIC && c.n >= 32 && c.n <= 256 && c.ncols <= 16) {
+            tc_slot[i] = ntc_clips++;
+            tc_max_n = std::max(tc_max_n, c.n);
+            tc_tiles_all += (c.m + tc_px - 1) / tc_px;
+        }
     }
-    if (nsk > 0x7fffffff || nsb > 0x7fffffff) return fail(CDMD_ERR_UNSUPPORTED, "grouped work list too long");
+    // about one tensor-core item per SM
+    const int64_t tc_item_tiles = std::max<int64_t>(8, (tc_tiles_all + num_sms - 1) / std::max(1, num_sms));
+    int64_t nsb = 0, ntc = 0;
+    for (size_t i = 0; i < clips.size(); ++i) {
+        const GroupedClip& c = clips[i];
+        if (tc_slot[i] >= 0) {
+            ntc += ((c.m + tc_px - 1) / tc_px + tc_item_tiles - 1) / tc_item_tiles;
+        } else {
+            const int64_t tiles = (c.m + tile_px - 1) / tile_px;
+            nsb += (tiles + subtract_tiles - 1) / subtract_tiles;
+        }
+    }
+    if (nsk > 0x7fffffff || nsb > 0x7fffffff || ntc > 0x7fffffff)
+        return fail(CDMD_ERR_UNSUPPORTED, "grouped work list too long");
     size_t off = 0;
     const size_t o_tm_sk = off;
     off = align256(off + chunks.size() * sizeof(CUtensorMap));
@@ -126,6 +150,12 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
     off = align256(off + clips.size() * sizeof(SubtractClip));
     const size_t o_sbitems = off;
     off = align256(off + nsb * sizeof(SubtractItem));
+    const size_t o_tm_tc = off;
+    off = align256(off + ntc_clips * sizeof(CUtensorMap));
+    const size_t o_tcclips = off;
+    off = align256(off + ntc_clips * sizeof(SubTcClip));
+    const size_t o_tcitems = off;
+    off = align256(off + ntc * sizeof(SubtractItem));
     std::vector<size_t> o_table(clips.size());
     for (size_t i = 0; i < clips.size(); ++i) {
         o_table[i] = off;
@@ -197,8 +227,12 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
             }
     }
     std::vector<SubtractClip> sbc(clips.size());
-    std::vector<SubtractItem> sbi;
+    std::vector<SubtractItem> sbi, tci;
+    std::vector<CUtensorMap> tm_tc(ntc_clips);
+    std::vector<SubTcClip> tcc(ntc_clips);
+    const CUtensorMap* dtm_tc = reinterpret_cast<const CUtensorMap*>(dev + o_tm_tc);
     sbi.reserve(nsb);
+    tci.reserve(ntc);
     for (size_t i = 0; i < clips.size(); ++i) {
         const GroupedClip& c = clips[i];
         cdmd_status st = make_subtract_tmap(&tm_sb[i], c.D, c.m, c.n, c.ldd);
@@ -217,9 +251,28 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
         d.ncols = c.ncols;
         d.r = c.r;
         sbc[i] = d;
-        const int64_t tiles = (c.m + tile_px - 1) / tile_px;
-        for (int64_t t0 = 0; t0 < tiles; t0 += subtract_tiles)
-            sbi.push_back(SubtractItem{static_cast<int>(i), 0, t0, std::min<int64_t>(subtract_tiles, tiles - t0)});
+        if (tc_slot[i] >= 0) {
+            const int q = tc_slot[i];
+            st = make_subtract_tc_tmap(&tm_tc[q], c.D, c.m, c.n, c.ldd);
+            if (st != CDMD_OK) return st;
+            SubTcClip t{};
+            t.tmap = dtm_tc + q;
+            t.Phi = reinterpret_cast<const float2*>(c.buf->Phi);
+            subtract_table_ptrs(dev + o_table[i], c.n, nc, &t.lam_t, &t.amp);
+            t.mask = c.mask;
+            t.m = c.m;
+            t.n = c.n;
+            t.ncols = c.ncols;
+            t.nc_pad = nc;
+            tcc[q] = t;
+            const int64_t tiles = (c.m + tc_px - 1) / tc_px;
+            for (int64_t t0 = 0; t0 < tiles; t0 += tc_item_tiles)
+                tci.push_back(SubtractItem{q, 0, t0, std::min<int64_t>(tc_item_tiles, tiles - t0)});
+        } else {
+            const int64_t tiles = (c.m + tile_px - 1) / tile_px;
+            for (int64_t t0 = 0; t0 < tiles; t0 += subtract_tiles)
+                sbi.push_back(SubtractItem{static_cast<int>(i), 0, t0, std::min<int64_t>(subtract_tiles, tiles - t0)});
+        }
     }
     CDMD_CHECK_CUDA(cudaMemcpy(dev + o_tm_sk, tm_sk.data(), tm_sk.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     CDMD_CHECK_CUDA(cudaMemcpy(dev + o_tm_sb, tm_sb.data(), tm_sb.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
@@ -229,6 +282,9 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
     CDMD_CHECK_CUDA(cudaMemcpy(dev + o_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     CDMD_CHECK_CUDA(cudaMemcpy(dev + o_sbclips, sbc.data(), sbc.size() * sizeof(SubtractClip), cudaMemcpyHostToDevice));
     CDMD_CHECK_CUDA(cudaMemcpy(dev + o_sbitems, sbi.data(), sbi.size() * sizeof(SubtractItem), cudaMemcpyHostToDevice));
+    CDMD_CHECK_CUDA(cudaMemcpy(dev + o_tm_tc, tm_tc.data(), tm_tc.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    CDMD_CHECK_CUDA(cudaMemcpy(dev + o_tcclips, tcc.data(), tcc.size() * sizeof(SubTcClip), cudaMemcpyHostToDevice));
+    CDMD_CHECK_CUDA(cudaMemcpy(dev + o_tcitems, tci.data(), tci.size() * sizeof(SubtractItem), cudaMemcpyHostToDevice));
 
     g->built = true;
     g->sketch_steps = sketch_steps;
@@ -246,6 +302,10 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
     g->sb_nitems = static_cast<int>(sbi.size());
     g->sb_nc = nc;
     g->sb_max_n = max_n;
+    g->tc_clips = reinterpret_cast<const SubTcClip*>(dev + o_tcclips);
+    g->tc_items = reinterpret_cast<const SubtractItem*>(dev + o_tcitems);
+    g->tc_nitems = static_cast<int>(tci.size());
+    g->tc_max_n = tc_max_n;
     return CDMD_OK;
 }
 
@@ -255,8 +315,11 @@ cdmd_status grouped_sketch(const GroupedPlan* g, int* status, cudaStream_t strea
 }
 
 cdmd_status grouped_subtract(const GroupedPlan* g, cdmd_bgmode mode, float tau, int* status, cudaStream_t stream) {
-    return launch_subtract_grouped(g->sb_clips, g->sb_nclips, g->sb_items, g->sb_nitems, g->sb_nc, g->sb_max_n, mode,
-                                   tau, status, stream);
+    // lambda^t tables of every clip, the CUDA-core items, then the tensor-core items
+    cdmd_status st = launch_subtract_grouped(g->sb_clips, g->sb_nclips, g->sb_items, g->sb_nitems, g->sb_nc,
+                                             g->sb_max_n, mode, tau, status, stream);
+    if (st != CDMD_OK || g->tc_nitems == 0) return st;
+    return launch_subtract_tc_grouped(g->tc_clips, g->tc_items, g->tc_nitems, g->tc_max_n, mode, tau, status, stream);
 }
 
 }  // namespace cdmd

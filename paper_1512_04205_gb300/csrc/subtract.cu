@@ -668,6 +668,12 @@ cdmd_status launch_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, i
 namespace cdmd {
 
 size_t subtract_table_bytes_nc(int n, int nc) { return table_bytes(n, nc); }
+
+void subtract_table_ptrs(void* table, int n, int nc, const float2** lam_t, const float2** amp) {
+    const Table t = table_views(table, n, nc);
+    *lam_t = t.table;
+    *amp = t.amp;
+}
 size_t subtract_tma_smem(int n, int nc) { return tma_smem_bytes(n, nc); }
 int subtract_tile_pixels() { return kTmaTile; }
 
@@ -679,6 +685,7 @@ cdmd_status launch_subtract_grouped(const SubtractClip* clips, int nclips, const
                                     int nc, int max_n, cdmd_bgmode mode, float tau, int* status, cudaStream_t stream) {
     subtract_table_grouped_kernel<<<static_cast<unsigned>(nclips), 32, 0, stream>>>(clips, nc);
     CDMD_CHECK_LAUNCH("subtract_table_grouped_kernel");
+    if (nitems == 0) return CDMD_OK;
     const size_t smem = tma_smem_bytes(max_n, nc);
 #define CDMD_SUBG(NCV, MV)                                                                                   \
     {                                                                                                        \

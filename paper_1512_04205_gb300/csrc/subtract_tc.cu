@@ -29,6 +29,7 @@
 #include <algorithm>
 
 #include "tc_common.cuh"
+#include "batch_internal.cuh"
 
 namespace cdmd {
 namespace {
@@ -90,11 +91,10 @@ __device__ __forceinline__ void store_split4(uint8_t* hi_tile, uint8_t* lo_tile,
     *reinterpret_cast<float4*>(lo_tile + off) = make_float4(l[0], l[1], l[2], l[3]);
 }
 
+// The tiles tile_first + li * tile_stride (li < my_tiles) of one clip.
 template <bool kReal>
-__global__ void __launch_bounds__(kThreads, 1)
-subtract_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SubTcArgs a, int* status) {
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+__device__ __forceinline__ void subtract_tc_body(const CUtensorMap* tmap, const SubTcArgs& a, int64_t tile_first,
+                                                 int64_t tile_stride, int64_t my_tiles, int* status, uint8_t* smem) {
     const int n = a.n;
     const SubLayout L = sub_layout(n);
     uint8_t* Ahi = smem + L.a_off;
@@ -122,9 +122,6 @@ subtract_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SubTcArgs a, 
     const int nh0 = half0(n);
     const int ncols = a.ncols;
     const float tau = a.tau;
-    int64_t my_tiles = 0;
-    if (static_cast<int64_t>(blockIdx.x) < a.ntiles)
-        my_tiles = (a.ntiles - 1 - static_cast<int64_t>(blockIdx.x)) / gridDim.x + 1;
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
@@ -168,8 +165,8 @@ subtract_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SubTcArgs a, 
                 const uint32_t u = static_cast<uint32_t>(li >> 1);
                 if (u >= 1 && !tc::mbar_wait(&d_free[s], (u - 1) & 1u, abort_flag, status)) break;
                 tc::mbar_arrive_expect_tx(&tma_full[s], static_cast<uint32_t>(n) * kPix);
-                const int64_t tile = blockIdx.x + li * gridDim.x;
-                tc::tma_load_2d(Dst + s * L.d_stage, &tmap, static_cast<int>(tile * kPix), 0, &tma_full[s]);
+                const int64_t tile = tile_first + li * tile_stride;
+                tc::tma_load_2d(Dst + s * L.d_stage, tmap, static_cast<int>(tile * kPix), 0, &tma_full[s]);
             }
             for (int s = 0; s < 2; ++s) {
                 const int64_t uses = (my_tiles - s + 1) / 2;
@@ -224,7 +221,7 @@ subtract_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SubTcArgs a, 
         const int ct = tid - 64;
         float2 f[2][kMaxModes];
         auto load_phi = [&](int64_t li) {
-            const int64_t tile = blockIdx.x + li * gridDim.x;
+            const int64_t tile = tile_first + li * tile_stride;
 #pragma unroll
             for (int jj = 0; jj < 2; ++jj) {
                 const int64_t p = tile * kPix + ct + 64 * jj;
@@ -267,7 +264,7 @@ subtract_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SubTcArgs a, 
             if (!tc::mbar_wait(&acc_full[h], static_cast<uint32_t>(li & 1), abort_flag, status)) break;
             if (!tc::mbar_wait(&tma_full[s], u & 1u, abort_flag, status)) break;
             tc::tc_fence_after();
-            const int64_t tile = blockIdx.x + li * gridDim.x;
+            const int64_t tile = tile_first + li * tile_stride;
             const int64_t p = tile * kPix + row;
             const bool valid = p < a.m;
             const bool warp_full = __all_sync(0xffffffffu, valid);
@@ -348,6 +345,42 @@ subtract_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SubTcArgs a, 
     }
 }
 
+template <bool kReal>
+__global__ void __launch_bounds__(kThreads, 1)
+subtract_tc_kernel(const __grid_constant__ CUtensorMap tmap, const SubTcArgs a, int* status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    int64_t my_tiles = 0;
+    if (static_cast<int64_t>(blockIdx.x) < a.ntiles)
+        my_tiles = (a.ntiles - 1 - static_cast<int64_t>(blockIdx.x)) / gridDim.x + 1;
+    subtract_tc_body<kReal>(&tmap, a, blockIdx.x, gridDim.x, my_tiles, status, smem);
+}
+
+// Grouped: CTA b runs item items[b], consecutive tiles of one clip; the
+// clip's tensor map lives in global memory.
+template <bool kReal>
+__global__ void __launch_bounds__(kThreads, 1)
+subtract_tc_grouped_kernel(const SubTcClip* __restrict__ clips, const SubtractItem* __restrict__ items, float tau,
+                           int* status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    const SubtractItem it = items[blockIdx.x];
+    const SubTcClip c = clips[it.clip];
+    SubTcArgs a;
+    a.Phi = c.Phi;
+    a.lam_t = c.lam_t;
+    a.amp = c.amp;
+    a.mask = c.mask;
+    a.m = c.m;
+    a.words_per_frame = (c.m + 31) / 32;
+    a.ntiles = (c.m + kPix - 1) / kPix;
+    a.n = c.n;
+    a.ncols = c.ncols;
+    a.nc_pad = c.nc_pad;
+    a.tau = tau;
+    subtract_tc_body<kReal>(c.tmap, a, it.tile0, 1, it.ntiles, status, smem);
+}
+
 }  // namespace
 
 bool subtract_tc_supported(int n, int ncols, cdmd_bgmode mode, const uint8_t* D, int64_t ldd, int64_t m,
@@ -355,6 +388,32 @@ bool subtract_tc_supported(int n, int ncols, cdmd_bgmode mode, const uint8_t* D,
     return bg == nullptr && (mode == CDMD_BG_MODULUS || mode == CDMD_BG_REAL) && n >= 32 && n <= 256 &&
            ncols >= 1 && ncols <= kMaxModes && (reinterpret_cast<uintptr_t>(D) % 16 == 0) && (ldd % 16 == 0) &&
            m <= 0x7fffffffLL - kPix;
+}
+
+size_t subtract_tc_smem(int n) { return sub_layout(n).total + 1024; }
+
+int subtract_tc_tile_pixels() { return kPix; }
+
+cdmd_status make_subtract_tc_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, int n, int64_t ldd) {
+    return make_video_tmap(map, D, m, n, ldd, kPix, n);
+}
+
+cdmd_status launch_subtract_tc_grouped(const SubTcClip* clips, const SubtractItem* items, int nitems, int max_n,
+                                       cdmd_bgmode mode, float tau, int* status, cudaStream_t stream) {
+    const size_t smem = subtract_tc_smem(max_n);
+    if (mode == CDMD_BG_REAL) {
+        CDMD_CHECK_CUDA(cudaFuncSetAttribute(subtract_tc_grouped_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        subtract_tc_grouped_kernel<true><<<static_cast<unsigned>(nitems), kThreads, smem, stream>>>(clips, items, tau,
+                                                                                                   status);
+    } else {
+        CDMD_CHECK_CUDA(cudaFuncSetAttribute(subtract_tc_grouped_kernel<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        subtract_tc_grouped_kernel<false><<<static_cast<unsigned>(nitems), kThreads, smem, stream>>>(clips, items, tau,
+                                                                                                    status);
+    }
+    CDMD_CHECK_LAUNCH("subtract_tc_grouped_kernel");
+    return CDMD_OK;
 }
 
 cdmd_status launch_subtract_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const float* Phi,

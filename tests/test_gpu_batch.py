@@ -112,6 +112,7 @@ def test_batch_autotune_picks_a_candidate(C):
     batch = C.Batch(clips, 25.0, prec="bf16x2", autotune=True, lanes=8)
     t = batch.tuning()
     assert t["lanes"] in (2, 4, 8)
+    assert t["waves"] in (1, 2, 4, 8)
     assert t["run_ms"] > 0.0
     assert t["sketch_steps"] >= 1 and t["subtract_tiles"] >= 1
     batch.run()
