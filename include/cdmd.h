@@ -55,7 +55,7 @@ typedef enum {
     CDMD_ERR_NOT_CONVERGED = 4,  /* an eigen-iteration hit its bound         */
     CDMD_ERR_RANK_DEFICIENT = 5, /* sigma_r of the sketch is zero            */
     CDMD_ERR_NONFINITE = 6,      /* NaN or Inf met in the sketch             */
-    CDMD_ERR_UNSUPPORTED = 7,    /* valid request this build cannot serve    */
+    CDMD_ERR_UNSUPPORTED = 7,    /* valid request the library does not serve */
     CDMD_ERR_TIMEOUT = 8         /* a kernel's bounded wait gave up          */
 } cdmd_status;
 

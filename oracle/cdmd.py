@@ -35,7 +35,7 @@ Readings where the paper is silent (all FP64):
   the best score are ties and go to the largest Im(lambda), then lowest index;
   beta is re-solved by complex least squares on the selected columns after each
   pick; stop at K picks or when ||rho|| <= 1e-12 ||y1||.
-* Background modes: MODULUS (the benchmark spec), REAL (footnote to Eq. DMDTerms),
+* Background modes: MODULUS (the default: modulus of the complex sum), REAL (footnote to Eq. DMDTerms),
   STATIC (x_BG = Phi beta of Section 2.3, i.e. t = 0 for every frame).
 """
 import numpy as np

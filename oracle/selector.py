@@ -6,7 +6,8 @@ benchmark may import it; the product never does.
 The paper picks the background modes and their amplitudes by sparse coding
 (Section 2.3, Eq. sparsecoding; Remark 3 applies it to the compressed modes).
 This module defines a small learned replacement for the selection step and
-keeps the sparse-coding solver as its fallback and judge:
+keeps the sparse-coding solver as its fallback and as the reference its
+selections are checked against:
 
   features   per mode j of the decomposition (the continuous-time reading of
              Section 2.2 ties background modes to |lambda| near 1 and arg

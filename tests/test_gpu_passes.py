@@ -1,7 +1,7 @@
 """GPU parity of each pass against the FP64 oracle, on identical inputs.
 
 Every test feeds the CUDA pass and the oracle the same seeded input (for the
-later passes: the oracle's own upstream result), so each pass is judged on
+later passes: the oracle's own upstream result), so each pass is checked on
 its own.  Sizes span several tiles and a ragged tail (pixels not a multiple
 of 32, frames not a multiple of 32, rows not a multiple of 4 or 64).
 """
