@@ -161,6 +161,15 @@ const char* cdmd_status_string(cdmd_status s);
  * on the device by the calls enqueued so far (CDMD_OK if none). */
 cdmd_status cdmd_status_sync(cdmd_ctx* ctx, void* stream);
 
+/* Failure detection without a GPU fault: enqueue on `stream` one kernel that
+ * waits on an mbarrier nothing ever arrives at, with the bounded wait every
+ * tensor-core kernel of the library uses (a global-timer limit of limit_us
+ * microseconds, 1..2,000,000).  The wait gives up, records
+ * CDMD_ERR_TIMEOUT in the context's status word (returned and cleared by the
+ * next cdmd_status_sync) and the kernel returns; the context stays usable.
+ * CDMD_ERR_INVALID_ARG for a NULL ctx or limit_us outside the range. */
+cdmd_status cdmd_selftest_wait(cdmd_ctx* ctx, uint32_t limit_us, void* stream);
+
 /* ---- measurement matrices (Section 3.3) ---------------------------------- */
 
 /* Exact number of non-zeros of the SPARSE matrix for (m, k, seed, density),

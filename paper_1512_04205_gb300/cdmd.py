@@ -38,7 +38,8 @@ EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_strin
             "cdmd_selector_features", "cdmd_selector_fallbacks", "cdmd_mlp_forward", "cdmd_mlp_grad",
             "cdmd_mlp_train_step", "cdmd_synth_clip", "cdmd_selector_relabel", "cdmd_batch_create",
             "cdmd_batch_run", "cdmd_batch_status_sync", "cdmd_batch_views", "cdmd_batch_tuning",
-            "cdmd_batch_destroy", "cdmd_copy", "cdmd_sketch_shared", "cdmd_run_shared", "cdmd_run_host_shared"]
+            "cdmd_batch_destroy", "cdmd_copy", "cdmd_sketch_shared", "cdmd_run_shared", "cdmd_run_host_shared",
+            "cdmd_selftest_wait"]
 BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_GROUPED = 1, 2, 4
 
 
@@ -107,6 +108,7 @@ def load_library(path=LIB_PATH):
         "cdmd_sketch_shared": [vp, ctypes.c_int, vp, i64, vp, vp, ctypes.c_int, ctypes.c_int, u64, ctypes.c_int, vp,
                                vp],
         "cdmd_run_shared": [vp, ctypes.c_int, vp, i64, vp, vp, ctypes.POINTER(cdmd_params), vp, vp],
+        "cdmd_selftest_wait": [vp, ctypes.c_uint32, vp],
         "cdmd_run_host_shared": [vp, ctypes.c_int, vp, i64, vp, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_workspace_views": [vp] + [ctypes.POINTER(vp)] * 8,
         "cdmd_sketch_noalloc": [vp, i64, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, u64, vp, vp],
@@ -423,6 +425,12 @@ def cdmd_run_host_shared(ctx, D_hosts, params, mask_hosts=None, stream=None):
     out = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in mask_hosts])
     _check(ctx.lib.cdmd_run_host_shared(ctx.handle, cnt, ptrs, m, ns, ctypes.byref(params), out, _stream(stream)))
     return mask_hosts
+
+
+def cdmd_selftest_wait(ctx, limit_us, stream=None):
+    """Enqueue a kernel whose bounded wait on a barrier nothing arrives at gives
+    up after limit_us; the next cdmd_status_sync raises CDMD_ERR_TIMEOUT."""
+    _check(ctx.lib.cdmd_selftest_wait(ctx.handle, int(limit_us), _stream(stream)))
 
 
 def cdmd_workspace_views(ctx):

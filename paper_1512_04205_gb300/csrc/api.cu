@@ -161,6 +161,14 @@ cdmd_status cdmd_status_sync(cdmd_ctx* ctx, void* stream) {
     return CDMD_OK;
 }
 
+cdmd_status cdmd_selftest_wait(cdmd_ctx* ctx, uint32_t limit_us, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(limit_us >= 1 && limit_us <= 2000000, "limit_us must be in [1, 2000000] (got %u)", limit_us);
+    DeviceGuard g(ctx->device);
+    return launch_selftest_wait(ctx, static_cast<uint64_t>(limit_us) * 1000ull, static_cast<cudaStream_t>(stream));
+}
+
 cdmd_status cdmd_measure_sparse_nnz(cdmd_ctx* ctx, int64_t m, int k, uint64_t seed, double density, int64_t* nnz,
                                     void* stream) {
     clear_error();
