@@ -22,6 +22,7 @@ amplitudes.  The video D is m x n (column t = frame t).
   background  bg_jt = | sum_{s in sel} Phi_js beta_s lambda_s^t |        Eq. (DMDTerms)
   mask        M_jt = 1  iff  |x_jt - bg_jt| > tau                       Eq. (thres)
   F-measure   harmonic mean of precision and recall            Section 4 (Results)
+  post-pass   3 x 3 median filter of each mask frame, zero padding    Section 4 (BMC figure, Discussion)
 
 Readings where the paper is silent (all FP64):
 * SVD: one-sided (Hestenes) Jacobi on Y, cyclic pair order, until every pair
@@ -37,6 +38,8 @@ Readings where the paper is silent (all FP64):
   pick; stop at K picks or when ||rho|| <= 1e-12 ||y1||.
 * Background modes: MODULUS (the default: modulus of the complex sum), REAL (footnote to Eq. DMDTerms),
   STATIC (x_BG = Phi beta of Section 2.3, i.e. t = 0 for every frame).
+* Median filter: the paper gives neither the window nor the border rule;
+  the window is 3 x 3 and pixels outside the frame count as background.
 """
 import numpy as np
 
@@ -411,3 +414,30 @@ def fmeasure(pred, truth):
     recall = tp / (tp + fn) if tp + fn > 0 else 0.0
     f = 2 * precision * recall / (precision + recall) if precision + recall > 0 else 0.0
     return precision, recall, f
+
+
+# ----------------------------------------------------------------------------
+# Mask post-processing (Section 4: the BMC figure's median-filtered masks and
+# the Discussion's remark that a median filter cuts false positives)
+# ----------------------------------------------------------------------------
+
+def median3x3_mask(mask, W, H):
+    """3 x 3 median filter of each frame of an m x n boolean mask.
+
+    Pixel j of a frame sits at row j // W, column j % W (m = W * H).  The
+    window is the pixel and its eight neighbours; neighbours outside the frame
+    count as background (zero padding).  Written as the definition: stack the
+    nine shifted frames and take their median, which for 0/1 values is the
+    fifth-smallest of the nine.
+    """
+    mask = np.asarray(mask, dtype=bool)
+    m, n = mask.shape
+    if m != W * H:
+        raise ValueError("m != W * H")
+    frames = mask.T.reshape(n, H, W).astype(np.uint8)
+    padded = np.zeros((n, H + 2, W + 2), dtype=np.uint8)
+    padded[:, 1:H + 1, 1:W + 1] = frames
+    window = np.stack([padded[:, 1 + dy:H + 1 + dy, 1 + dx:W + 1 + dx]
+                       for dy in (-1, 0, 1) for dx in (-1, 0, 1)], axis=0)
+    med = np.median(window, axis=0)
+    return (med > 0.5).reshape(n, m).T
