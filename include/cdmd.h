@@ -265,6 +265,21 @@ cdmd_status cdmd_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int
                           float tau, cdmd_bgmode mode, uint32_t* mask, float* bg,
                           void* stream);
 
+/* ---- mask post-pass: 3 x 3 median filter (Section 4: the BMC figure's
+ * median-filtered masks; the Discussion's median-filter post-processing)
+ *
+ * mask and out are device arrays of n frames of ceil(W*H/32) uint32 words,
+ * laid out as for cdmd_subtract with pixel j of a frame at row j / W,
+ * column j % W.  Output bit (j, t) is the median of the 3 x 3 neighbourhood
+ * of pixel j in frame t, neighbours outside the frame counting as 0, i.e. 1
+ * iff at least five of the nine are 1.  Bits of mask past W*H are ignored;
+ * those of out are written 0.  The caller owns both; they must not overlap
+ * (no in-place filtering) and must be 4-byte aligned.
+ * CDMD_ERR_INVALID_ARG for NULL or overlapping arrays, W or H < 1,
+ * W*H > 2^31 - 1, or n outside [1, 262140]. */
+cdmd_status cdmd_median3x3(cdmd_ctx* ctx, const uint32_t* mask, int64_t W, int64_t H, int n,
+                           uint32_t* out, void* stream);
+
 /* ---- whole pipeline ------------------------------------------------------ */
 
 typedef struct {

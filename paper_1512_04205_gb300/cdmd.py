@@ -39,7 +39,7 @@ EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_strin
             "cdmd_mlp_train_step", "cdmd_synth_clip", "cdmd_selector_relabel", "cdmd_batch_create",
             "cdmd_batch_run", "cdmd_batch_status_sync", "cdmd_batch_views", "cdmd_batch_tuning",
             "cdmd_batch_destroy", "cdmd_copy", "cdmd_sketch_shared", "cdmd_run_shared", "cdmd_run_host_shared",
-            "cdmd_selftest_wait"]
+            "cdmd_selftest_wait", "cdmd_median3x3"]
 BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_GROUPED = 1, 2, 4
 
 
@@ -109,6 +109,7 @@ def load_library(path=LIB_PATH):
                                vp],
         "cdmd_run_shared": [vp, ctypes.c_int, vp, i64, vp, vp, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_selftest_wait": [vp, ctypes.c_uint32, vp],
+        "cdmd_median3x3": [vp, vp, i64, i64, ctypes.c_int, vp, vp],
         "cdmd_run_host_shared": [vp, ctypes.c_int, vp, i64, vp, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_workspace_views": [vp] + [ctypes.POINTER(vp)] * 8,
         "cdmd_sketch_noalloc": [vp, i64, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, u64, vp, vp],
@@ -425,6 +426,21 @@ def cdmd_run_host_shared(ctx, D_hosts, params, mask_hosts=None, stream=None):
     out = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in mask_hosts])
     _check(ctx.lib.cdmd_run_host_shared(ctx.handle, cnt, ptrs, m, ns, ctypes.byref(params), out, _stream(stream)))
     return mask_hosts
+
+
+def cdmd_median3x3(ctx, mask, W, H, out=None, stream=None):
+    """3 x 3 median filter of each frame of a bit-packed mask (n, ceil(W*H/32))
+    int32 on the device; returns a new mask (or fills `out`)."""
+    import torch
+    if mask.dim() != 2 or not mask.is_contiguous() or mask.dtype != torch.int32:
+        raise ValueError("mask must be a contiguous (n, words) int32 tensor")
+    n = mask.shape[0]
+    if mask.shape[1] != (int(W) * int(H) + 31) // 32:
+        raise ValueError("mask has %d words per frame, W*H needs %d" % (mask.shape[1], (W * H + 31) // 32))
+    if out is None:
+        out = torch.empty_like(mask)
+    _check(ctx.lib.cdmd_median3x3(ctx.handle, _ptr(mask), int(W), int(H), int(n), _ptr(out), _stream(stream)))
+    return out
 
 
 def cdmd_selftest_wait(ctx, limit_us, stream=None):

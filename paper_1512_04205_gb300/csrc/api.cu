@@ -343,6 +343,21 @@ cdmd_status cdmd_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int
                            static_cast<cudaStream_t>(stream));
 }
 
+cdmd_status cdmd_median3x3(cdmd_ctx* ctx, const uint32_t* mask, int64_t W, int64_t H, int n, uint32_t* out,
+                           void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && mask != nullptr && out != nullptr, "ctx, mask or out is NULL");
+    CDMD_REQUIRE(W >= 1 && H >= 1, "W and H must be >= 1");
+    CDMD_REQUIRE(W <= 0x7fffffffLL / H, "W*H must be <= 2^31 - 1");
+    CDMD_REQUIRE(n >= 1 && n <= 262140, "n must be in [1, 262140]");
+    CDMD_REQUIRE(aligned(mask, 4) && aligned(out, 4), "mask and out must be 4-byte aligned");
+    const int64_t bytes = (W * H + 31) / 32 * 4 * static_cast<int64_t>(n);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(mask), b = reinterpret_cast<uintptr_t>(out);
+    CDMD_REQUIRE(a + bytes <= b || b + bytes <= a, "mask and out overlap");
+    DeviceGuard g(ctx->device);
+    return launch_median3x3(mask, W, H, n, out, static_cast<cudaStream_t>(stream));
+}
+
 namespace {
 
 cdmd_status check_run(const uint8_t* D, int64_t m, int n, int64_t ldd, const cdmd_params* p) {

@@ -240,6 +240,8 @@ cdmd_status launch_subtract_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n
                                int ncols, const void* lam_t, const void* amp, int nc_pad, float tau, cdmd_bgmode mode,
                                uint32_t* mask, cudaStream_t stream);
 cdmd_status launch_selftest_wait(cdmd_ctx* ctx, uint64_t limit_ns, cudaStream_t stream);
+cdmd_status launch_median3x3(const uint32_t* mask, int64_t W, int64_t H, int n, uint32_t* out,
+                             cudaStream_t stream);
 cdmd_status launch_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                                  const cdmd_measure* meas, double* DY, cudaStream_t stream);
 cdmd_status launch_measure_sparse_count(cdmd_ctx* ctx, int64_t m, int k, uint64_t seed,
