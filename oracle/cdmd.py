@@ -23,6 +23,8 @@ amplitudes.  The video D is m x n (column t = frame t).
   mask        M_jt = 1  iff  |x_jt - bg_jt| > tau                       Eq. (thres)
   F-measure   harmonic mean of precision and recall            Section 4 (Results)
   post-pass   3 x 3 median filter of each mask frame, zero padding    Section 4 (BMC figure, Discussion)
+  exact DMD   the same steps on X itself (no C; Section 2.1), the comparator of
+              Section 4 (Computational Performance)
 
 Readings where the paper is silent (all FP64):
 * SVD: one-sided (Hestenes) Jacobi on Y, cyclic pair order, until every pair
@@ -358,6 +360,30 @@ def cdmd(D, C, r, K):
     out["DY"] = DY
     out["Phi"] = lift(D, out["G"])
     return out
+
+
+def exact_dmd(D, r, K):
+    """Exact DMD (Section 2.1) with the sparse-coding selection of Section 2.3.
+
+    Steps (4)-(9) run on the snapshots themselves, with no measurement: the
+    SVD is that of X, A~ = U^T X' V S^-1, the modes Phi = X' V S^-1 W are the
+    full-resolution ones, and OMP works on them with x1 = D[:, 0].  Same
+    keys as cdmd(); "Phi" is the (m x r) mode matrix.
+    """
+    out = decompose(D, r, K)
+    out["Phi"] = out["PhiY"]
+    return out
+
+
+def snapshot_gram(D):
+    """R = D^T D (n x n), the inner products of every pair of frames, in exact
+    integer arithmetic for a uint8 video (sums of m products < 2^63)."""
+    D = np.asarray(D)
+    if np.issubdtype(D.dtype, np.integer):
+        Di = D.astype(np.int64)
+        return Di.T @ Di
+    D = D.astype(np.float64)
+    return D.T @ D
 
 
 # ----------------------------------------------------------------------------

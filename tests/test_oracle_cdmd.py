@@ -197,3 +197,41 @@ def test_sharded_sketch_sums_to_full_sketch():
     bounds = [0, 100, 333, 500, clip.m]
     parts = sum(O.sketch(C[:, a:b], D[a:b]) for a, b in zip(bounds[:-1], bounds[1:]))
     np.testing.assert_allclose(parts, full, rtol=1e-12, atol=1e-9)
+
+
+def test_exact_dmd_modes_are_eigenvectors_of_the_regression():
+    # Section 2.1: A_hat = X' pinv(X); exact DMD's modes Phi = X' V S^-1 W
+    # satisfy A_hat Phi = Phi Lambda (brute force on the 48 x 48 pixel space)
+    D = _random_video(48, 30, 7)
+    r = 12
+    out = O.exact_dmd(D, r, K=4)
+    X, Xp = O.split_snapshots(D)
+    U, s, Vt = np.linalg.svd(X, full_matrices=False)
+    pinv_r = Vt[:r].T @ np.diag(1.0 / s[:r]) @ U[:, :r].T
+    A_hat = Xp @ pinv_r
+    Phi, lam = out["Phi"], out["lam"]
+    assert Phi.shape == (48, r)
+    resid = np.linalg.norm(A_hat @ Phi - Phi * lam[None, :], axis=0) / np.linalg.norm(Phi, axis=0)
+    assert resid.max() < 1e-9 * np.abs(lam).max()
+    ev = np.linalg.eigvals(A_hat)
+    ev = ev[np.argsort(-np.abs(ev))][:r]
+    assert _match(lam, ev) < 1e-10 * np.abs(ev).max()
+    # the selection picks K modes of Phi for x1 = D[:, 0] (Section 2.3)
+    assert len(out["sel"]) == 4 and len(out["beta"]) == 4
+
+
+def test_snapshot_gram_is_exact_and_matches_the_svd():
+    rng = np.random.default_rng(2)
+    D = rng.integers(0, 256, size=(500, 17), dtype=np.uint8)
+    R = O.snapshot_gram(D)
+    assert R.dtype == np.int64
+    # brute force on a few entries, Python integers
+    for s_, t_ in [(0, 0), (3, 11), (16, 2)]:
+        assert R[s_, t_] == sum(int(D[j, s_]) * int(D[j, t_]) for j in range(500))
+    assert np.array_equal(R, R.T)
+    # eigenvalues of X^T X are the squared singular values of X, here from the
+    # oracle's own Jacobi SVD (a different route from the Gram)
+    X, _ = O.split_snapshots(D.astype(np.float64))
+    _, sv, _, _ = O.jacobi_svd(X)
+    ev = np.sort(np.linalg.eigvalsh(R[:-1, :-1].astype(np.float64)))[::-1]
+    assert np.allclose(ev, np.sort(sv)[::-1] ** 2, rtol=1e-10, atol=1e-6 * ev[0])
