@@ -507,6 +507,44 @@ def run_ours(args, rank, world, local_rank):
         us = float(np.median([e0.elapsed_time(e1) for e0, e1 in evs])) * 1e3
         return us, C.unpack_mask(out, m)
 
+    def exact_comparator(prec, steps, warmup):
+        """Exact DMD on the same clip (snapshot Gram, decompose from the Gram,
+        lift, subtract; OMP selection), one clip per step on one stream: the
+        comparator the paper times cDMD against."""
+        L = lanes[0]
+        R = torch.empty((n, n), dtype=torch.float64, device=dev)
+        dec = C.decompose_outputs(n, k, r, K, dev)
+        emask = torch.empty_like(mask)
+
+        def one(ev=None):
+            with torch.cuda.stream(main_stream):
+                if ev is not None:
+                    ev[0].record(main_stream)
+                C.cdmd_snapshot_gram(ctx, D, R=R)
+                if ev is not None:
+                    ev[1].record(main_stream)
+                C.cdmd_decompose_gram(ctx, R, r, K, out=dec)
+                if ev is not None:
+                    ev[2].record(main_stream)
+                C.cdmd_lift(ctx, D, dec["G"], cols=dec["sel"], ncols=K, prec=prec, Phi=L.Phi[0])
+                if ev is not None:
+                    ev[3].record(main_stream)
+                C.cdmd_subtract(ctx, D, L.Phi[0], dec["beta"], dec["lam"], w["tau"], cols=dec["sel"], mask=emask)
+                if ev is not None:
+                    ev[4].record(main_stream)
+        for _ in range(warmup):
+            one()
+        C.cdmd_status_sync(ctx)
+        barrier()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        for e in evs:
+            one(e)
+        torch.cuda.synchronize()
+        C.cdmd_status_sync(ctx)
+        total_ms = sum(e[0].elapsed_time(e[4]) for e in evs)
+        passes = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs]).mean(axis=0)
+        return dict(total_ms=max_over_ranks(total_ms, dist, dev), passes=passes, mask=C.unpack_mask(emask, m))
+
     # the headline form and the plain FP32 + OMP form it is compared with
     forms = {"head": (args.prec, args.selector)}
     if not args.no_plain and (args.prec, args.selector) != ("fp32", "omp"):
@@ -517,6 +555,7 @@ def run_ours(args, rank, world, local_rank):
         results[label] = dict(total_ms=total_ms, passes=passes, clocks=clocks, mask=C.unpack_mask(mask, m))
         if label == "head":
             results["median"] = median_postpass()
+    exact = exact_comparator(args.prec, args.steps, args.warmup) if not args.no_exact else None
     fallbacks = None
     if args.selector == "mlp":
         fallbacks = sum(C.cdmd_selector_fallbacks(L.ctx, reset=True, stream=L.stream) for L in lanes)
@@ -660,6 +699,22 @@ def run_ours(args, rank, world, local_rank):
                         "frac_hbm": med_bytes / (med_us * 1e-6) / 1e9 / hbm, "bytes": med_bytes,
                         "fmeasure_vs_truth_after": fmeasure(med_mask, truth),
                         "timing": "median of 10 launches, each after a 256 MB L2 flush; not in the step"}
+    if exact is not None:
+        t_gram = float(exact["passes"][0]) * 1e-3
+        gram_tf = 2.0 * m * n * n / t_gram / 1e12
+        bf16_peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
+        exact_value = n * steps / (exact["total_ms"] * 1e-3)
+        line["exact_dmd"] = {
+            "value": exact_value, "unit": UNIT, "ms_per_clip": exact["total_ms"] / steps,
+            "per_pass_ms": {nm: float(v) for nm, v in zip(["snapshot_gram", "decompose", "lift", "subtract"],
+                                                           exact["passes"])},
+            "gram_roofline": {"tflops": gram_tf, "frac_bf16": gram_tf / bf16_peak,
+                              "gbs": m * n / t_gram / 1e9, "frac_hbm": m * n / t_gram / 1e9 / hbm,
+                              "flops": 2.0 * m * n * n, "bytes": m * n},
+            "cdmd_single_stream_over_exact": latency_value / exact_value,
+            "fmeasure_vs_truth": fmeasure(exact["mask"], truth),
+            "form": ("snapshot Gram D^T D on tcgen05 (uint8 exact in BF16, FP32 accumulation, FP64 reduce); "
+                     f"FP64 small solves from the Gram; OMP; {args.prec} lift; one clip per step, one stream")}
     if batch_line is not None:
         line["batch"] = batch_line
     if not args.no_cpu:
@@ -705,6 +760,7 @@ def main():
                     help="WxH of a smaller clip for profiling captures (default: the 1920x1080 workload)")
     ap.add_argument("--sm-limit", type=int, default=136,
                     help="SMs the full-data passes of each in-flight clip may fill (0 = all)")
+    ap.add_argument("--no-exact", action="store_true", help="skip the exact-DMD comparator")
     args = ap.parse_args()
     if args.size:
         wd, ht = (int(v) for v in args.size.lower().split("x"))

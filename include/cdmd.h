@@ -241,6 +241,35 @@ cdmd_status cdmd_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r,
                            double* G, double* PhiY, double* beta, int32_t* sel,
                            int32_t* nsel, void* stream);
 
+/* ---- exact DMD, the comparator (Section 2.1; Section 4, Computational
+ * Performance) --------------------------------------------------------------
+ *
+ * Exact DMD takes the SVD of X itself instead of a sketch.  In the method of
+ * snapshots every quantity the small solves use is a block of the n x n Gram
+ * R = D^T D of the video (X^T X, X^T X', X'^T X', X'^T x1), so exact DMD is
+ * cdmd_snapshot_gram, cdmd_decompose_gram, then the same lift and subtract.
+ *
+ * cdmd_snapshot_gram: R[s*n + t] = sum_j D[s*ldd + j] D[t*ldd + j] (FP64,
+ * device, n x n, exactly symmetric).  The products are exact (uint8 in
+ * BF16 on the tensor cores); sums accumulate in FP32 over each SM's pixel
+ * range (relative error <= about 2^-24 per 16-pixel step of that range) and
+ * the ranges are added in FP64.  Needs 2 <= n <= 256, D 16-byte aligned and
+ * ldd % 16 == 0 (else CDMD_ERR_UNSUPPORTED).
+ *
+ * cdmd_decompose_gram: the outputs of cdmd_decompose (no PhiY) from a Gram R
+ * (device, n x n, symmetric) instead of DY: the SVD of X = D[:, 0:n-1] from
+ * the eigen-decomposition of R[0:n-1, 0:n-1], A~ = S^-1 V^T R[0:n-1, 1:n] V
+ * S^-1, and the selection on the full modes Phi = X' G with x1 = D[:, 0]
+ * (Section 2.3, Eq. sparsecoding) in Gram form.  Selector OMP or LSTSQ
+ * (CDMD_ERR_INVALID_ARG for MLP, whose network is trained on compressed
+ * modes).  Requires 1 <= r <= min(32, n-1), 1 <= K <= r, n <= 512. */
+cdmd_status cdmd_snapshot_gram(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                               double* R, void* stream);
+cdmd_status cdmd_decompose_gram(cdmd_ctx* ctx, const double* R, int n, int r, int K,
+                                cdmd_selector selector, double* sigma, double* lambda,
+                                double* G, double* beta, int32_t* sel, int32_t* nsel,
+                                void* stream);
+
 /* ---- pass (b): mode lift  Phi = X' G  (Algorithm 1 step 8, Eq. cDMDModes) */
 
 /* Phi[j*ncols + c] = sum_{t=0}^{n-2} D[(t+1)*ldd + j] * G[:, cols[c]] for the
@@ -302,6 +331,14 @@ typedef struct {
  * frames of a pixel tile in one operand). */
 cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                      const cdmd_params* p, uint32_t* mask, void* stream);
+
+/* Exact DMD end to end (Section 2.1 with the selection of Section 2.3):
+ * snapshot Gram -> decompose from the Gram -> lift -> subtract, as cdmd_run
+ * with no sketch (p->k, p->ctype and p->seed are ignored; p->prec picks the
+ * lift).  Requires 1 <= r <= min(32, m, n-1), 1 <= K <= r, selector OMP or
+ * LSTSQ, and the snapshot Gram's limits (n <= 256, aligned D). */
+cdmd_status cdmd_run_exact(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                           const cdmd_params* p, uint32_t* mask, void* stream);
 
 /* cdmd_run on host memory: copies D_host (m x n frame-major, ldd = m; pinned
  * memory gives full copy bandwidth) to the device, runs the pipeline and

@@ -39,7 +39,8 @@ EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_strin
             "cdmd_mlp_train_step", "cdmd_synth_clip", "cdmd_selector_relabel", "cdmd_batch_create",
             "cdmd_batch_run", "cdmd_batch_status_sync", "cdmd_batch_views", "cdmd_batch_tuning",
             "cdmd_batch_destroy", "cdmd_copy", "cdmd_sketch_shared", "cdmd_run_shared", "cdmd_run_host_shared",
-            "cdmd_selftest_wait", "cdmd_median3x3"]
+            "cdmd_selftest_wait", "cdmd_median3x3", "cdmd_snapshot_gram", "cdmd_decompose_gram",
+            "cdmd_run_exact"]
 BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_GROUPED = 1, 2, 4
 
 
@@ -110,6 +111,9 @@ def load_library(path=LIB_PATH):
         "cdmd_run_shared": [vp, ctypes.c_int, vp, i64, vp, vp, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_selftest_wait": [vp, ctypes.c_uint32, vp],
         "cdmd_median3x3": [vp, vp, i64, i64, ctypes.c_int, vp, vp],
+        "cdmd_snapshot_gram": [vp, vp, i64, ctypes.c_int, i64, vp, vp],
+        "cdmd_decompose_gram": [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [vp] * 7,
+        "cdmd_run_exact": [vp, vp, i64, ctypes.c_int, i64, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_run_host_shared": [vp, ctypes.c_int, vp, i64, vp, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_workspace_views": [vp] + [ctypes.POINTER(vp)] * 8,
         "cdmd_sketch_noalloc": [vp, i64, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, u64, vp, vp],
@@ -328,6 +332,34 @@ def cdmd_decompose(ctx, DY, r, K, selector="omp", with_phiy=False, stream=None, 
     return out
 
 
+def cdmd_snapshot_gram(ctx, D, R=None, stream=None):
+    """Exact DMD's full-data pass: R = D^T D (n, n) float64 of a device video."""
+    import torch
+    n, m, ldd = _video(D)
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=D.device)
+    _check(ctx.lib.cdmd_snapshot_gram(ctx.handle, _ptr(D), m, n, ldd, _ptr(R), _stream(stream)))
+    return R
+
+
+def cdmd_decompose_gram(ctx, R, r, K, selector="omp", stream=None, out=None):
+    """cdmd_decompose's outputs (no PhiY) from an (n, n) float64 Gram."""
+    import torch
+    n = R.shape[0]
+    if out is None:
+        dev = R.device
+        out = dict(sigma=torch.empty(r, dtype=torch.float64, device=dev),
+                   lam=torch.empty((r, 2), dtype=torch.float64, device=dev),
+                   G=torch.empty((r, n - 1, 2), dtype=torch.float64, device=dev),
+                   beta=torch.empty((r, 2), dtype=torch.float64, device=dev),
+                   sel=torch.empty(K, dtype=torch.int32, device=dev),
+                   nsel=torch.empty(1, dtype=torch.int32, device=dev))
+    _check(ctx.lib.cdmd_decompose_gram(ctx.handle, _ptr(R), int(n), int(r), int(K), SELECTORS[selector],
+                                       _ptr(out["sigma"]), _ptr(out["lam"]), _ptr(out["G"]), _ptr(out["beta"]),
+                                       _ptr(out["sel"]), _ptr(out["nsel"]), _stream(stream)))
+    return out
+
+
 def cdmd_lift(ctx, D, G, cols=None, ncols=None, prec="fp32", Phi=None, stream=None):
     """Pass (b): Phi = X' G[:, cols] (returns (m, ncols, 2) float32)."""
     import torch
@@ -371,6 +403,18 @@ def cdmd_run(ctx, D, params, mask=None, stream=None):
     if mask is None:
         mask = torch.empty((n, (m + 31) // 32), dtype=torch.int32, device=D.device)
     _check(ctx.lib.cdmd_run(ctx.handle, _ptr(D), m, n, ldd, ctypes.byref(params), _ptr(mask), _stream(stream)))
+    return mask
+
+
+def cdmd_run_exact(ctx, D, params, mask=None, stream=None):
+    """Exact DMD end to end on a device video (snapshot Gram, decompose, lift,
+    subtract); returns the mask (n, ceil(m/32)) int32."""
+    import torch
+    n, m, ldd = _video(D)
+    if mask is None:
+        mask = torch.empty((n, (m + 31) // 32), dtype=torch.int32, device=D.device)
+    _check(ctx.lib.cdmd_run_exact(ctx.handle, _ptr(D), m, n, ldd, ctypes.byref(params), _ptr(mask),
+                                  _stream(stream)))
     return mask
 
 

@@ -305,6 +305,39 @@ cdmd_status cdmd_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r,
                             static_cast<cudaStream_t>(stream));
 }
 
+cdmd_status cdmd_snapshot_gram(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, double* R,
+                               void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    cdmd_status st = check_video(D, m, n, ldd);
+    if (st != CDMD_OK) return st;
+    CDMD_REQUIRE(R != nullptr && aligned(R, 8), "R is NULL or not 8-byte aligned");
+    DeviceGuard g(ctx->device);
+    return launch_gram_tc(ctx, D, m, n, ldd, R, static_cast<cudaStream_t>(stream));
+}
+
+static cdmd_status check_exact_selector(cdmd_selector selector) {
+    CDMD_REQUIRE(selector == CDMD_SEL_OMP || selector == CDMD_SEL_LSTSQ,
+                 "exact DMD selects by OMP or least squares (got selector %d)", static_cast<int>(selector));
+    return CDMD_OK;
+}
+
+cdmd_status cdmd_decompose_gram(cdmd_ctx* ctx, const double* R, int n, int r, int K, cdmd_selector selector,
+                                double* sigma, double* lambda, double* G, double* beta, int32_t* sel, int32_t* nsel,
+                                void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(R && sigma && lambda && G && beta && sel && nsel, "a required pointer is NULL");
+    CDMD_REQUIRE(n >= 2 && n <= 512, "n must be in [2, 512] (got %d)", n);
+    CDMD_REQUIRE(r >= 1 && r <= 32 && r <= n - 1, "r must be in [1, min(32, n-1)] (got %d)", r);
+    CDMD_REQUIRE(K >= 1 && K <= r, "K must be in [1, r] (got %d)", K);
+    cdmd_status st = check_exact_selector(selector);
+    if (st != CDMD_OK) return st;
+    DeviceGuard g(ctx->device);
+    return launch_decompose_gram(ctx, R, n, r, K, selector, sigma, lambda, G, beta, sel, nsel,
+                                 static_cast<cudaStream_t>(stream));
+}
+
 cdmd_status cdmd_lift(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const double* G, int r,
                       const int32_t* cols, int ncols, cdmd_prec prec, float* Phi, void* stream) {
     clear_error();
@@ -369,10 +402,11 @@ cdmd_status check_run(const uint8_t* D, int64_t m, int n, int64_t ldd, const cdm
     return CDMD_OK;
 }
 
-// Steps 4-9 of cdmd_run on a sketch DY already in device memory (the
-// context's small-solve and Phi buffers are reused, stream-ordered).
-cdmd_status run_from_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const cdmd_params* p,
-                            double* DY, uint32_t* mask, void* stream) {
+// Steps 4-9 of cdmd_run on a sketch DY already in device memory, or, with
+// DY NULL, of exact DMD on the snapshot Gram R (the context's small-solve and
+// Phi buffers are reused, stream-ordered).
+cdmd_status run_from(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const cdmd_params* p,
+                     double* DY, const double* R, uint32_t* mask, void* stream) {
     const int k = p->k, r = p->r, K = p->K;
     const int p1 = n - 1;
     const int ncols = (p->selector == CDMD_SEL_LSTSQ) ? r : K;
@@ -392,7 +426,9 @@ cdmd_status run_from_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, i
     ctx->run_DY = DY; ctx->run_sigma = sigma; ctx->run_lambda = lambda; ctx->run_G = Gm;
     ctx->run_beta = beta; ctx->run_sel = sel; ctx->run_nsel = nsel; ctx->run_Phi = Phi;
 
-    st = cdmd_decompose(ctx, DY, k, n, r, K, p->selector, sigma, lambda, Gm, nullptr, beta, sel, nsel, stream);
+    st = DY != nullptr
+             ? cdmd_decompose(ctx, DY, k, n, r, K, p->selector, sigma, lambda, Gm, nullptr, beta, sel, nsel, stream)
+             : cdmd_decompose_gram(ctx, R, n, r, K, p->selector, sigma, lambda, Gm, beta, sel, nsel, stream);
     if (st != CDMD_OK) return st;
     // OMP: lift and subtract only the selected modes (sel, -1 padded);
     // LSTSQ: every mode carries an amplitude, so all r are used.
@@ -420,7 +456,27 @@ cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t 
     double* DY = static_cast<double*>(v);
     st = cdmd_sketch(ctx, D, m, n, ldd, p->ctype, p->k, p->seed, p->prec, DY, stream);
     if (st != CDMD_OK) return st;
-    return run_from_sketch(ctx, D, m, n, ldd, p, DY, mask, stream);
+    return run_from(ctx, D, m, n, ldd, p, DY, nullptr, mask, stream);
+}
+
+cdmd_status cdmd_run_exact(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const cdmd_params* p,
+                           uint32_t* mask, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr && p != nullptr && mask != nullptr, "ctx, params or mask is NULL");
+    cdmd_status st = check_video(D, m, n, ldd);
+    if (st != CDMD_OK) return st;
+    CDMD_REQUIRE(p->r >= 1 && p->r <= 32 && p->r <= n - 1 && p->r <= m, "r must be in [1, min(32, m, n-1)]");
+    CDMD_REQUIRE(p->K >= 1 && p->K <= p->r, "K must be in [1, r]");
+    st = check_exact_selector(p->selector);
+    if (st != CDMD_OK) return st;
+    DeviceGuard g(ctx->device);
+    void* v = nullptr;
+    st = ensure_buffer(ctx, BUF_RUN_GRAM, static_cast<size_t>(n) * n * sizeof(double), &v);
+    if (st != CDMD_OK) return st;
+    double* R = static_cast<double*>(v);
+    st = cdmd_snapshot_gram(ctx, D, m, n, ldd, R, stream);
+    if (st != CDMD_OK) return st;
+    return run_from(ctx, D, m, n, ldd, p, nullptr, R, mask, stream);
 }
 
 cdmd_status cdmd_run_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
@@ -446,7 +502,7 @@ cdmd_status cdmd_run_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, 
     st = cdmd_sketch_shared(ctx, nclips, D, m, n, ldd, p->ctype, p->k, p->seed, p->prec, DYs, stream);
     if (st != CDMD_OK) return st;
     for (int i = 0; i < nclips; ++i) {
-        st = run_from_sketch(ctx, D[i], m, n[i], ldd[i], p, DYs[i], mask[i], stream);
+        st = run_from(ctx, D[i], m, n[i], ldd[i], p, DYs[i], nullptr, mask[i], stream);
         if (st != CDMD_OK) return st;
     }
     return CDMD_OK;

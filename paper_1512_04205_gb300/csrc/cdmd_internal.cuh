@@ -156,7 +156,7 @@ struct Buffer {
 
 enum BufferId {
     BUF_SKETCH_PARTIAL = 0,   // sketch split partials (float)
-    BUF_GRAM,                 // n x n Gram of the sketch (double) + split partials
+    BUF_GRAM,                 // snapshot Gram split partials (float)
     BUF_EIG,                  // eigen-solver scratch (double)
     BUF_SMALL,                // small-solve scratch (double)
     BUF_RUN_DY,               // cdmd_run intermediates
@@ -169,6 +169,7 @@ enum BufferId {
     BUF_MLP_PARTS,            // selector training: per-warp partial gradients
     BUF_RELABEL,              // selector training: OMP against a second target
     BUF_SKETCH_WIDE,          // BF16 copies of the frames of a clip pair sketched together
+    BUF_RUN_GRAM,             // cdmd_run_exact: the n x n snapshot Gram (double)
     BUF_COUNT
 };
 
@@ -240,6 +241,11 @@ cdmd_status launch_subtract_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n
                                int ncols, const void* lam_t, const void* amp, int nc_pad, float tau, cdmd_bgmode mode,
                                uint32_t* mask, cudaStream_t stream);
 cdmd_status launch_selftest_wait(cdmd_ctx* ctx, uint64_t limit_ns, cudaStream_t stream);
+cdmd_status launch_gram_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, double* R,
+                           cudaStream_t stream);
+cdmd_status launch_decompose_gram(cdmd_ctx* ctx, const double* R, int n, int r, int K, cdmd_selector selector,
+                                  double* sigma, double* lambda, double* G, double* beta, int32_t* sel,
+                                  int32_t* nsel, cudaStream_t stream);
 cdmd_status launch_median3x3(const uint32_t* mask, int64_t W, int64_t H, int n, uint32_t* out,
                              cudaStream_t stream);
 cdmd_status launch_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,

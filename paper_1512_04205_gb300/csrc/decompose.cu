@@ -1,7 +1,8 @@
 // Small solves on the device, FP64 (Algorithm 1 steps 4-7 and 9, Remark 3).
 //
 // Everything after the sketch is derived from the n x n Gram matrix
-// R = DY^T DY of the sketch:
+// R = DY^T DY of the sketch (for exact DMD, R = D^T D of the video itself,
+// computed by the snapshot Gram pass, and DY is never formed):
 //   Y^T Y  = R[0:p, 0:p]     (p = n-1)      -> V, S   (SVD of Y, step 4)
 //   Y^T Y' = R[0:p, 1:n]                     -> A~ = S^-1 V^T (Y^T Y') V S^-1 (step 6)
 //   Y'^T Y'= R[1:n, 1:n], Y'^T y1 = R[1:n, 0] -> Gram form of the OMP on the
@@ -1518,15 +1519,18 @@ cdmd_status launch_selector_relabel(cdmd_ctx* ctx, const double* DY, int k, int 
     return CDMD_OK;
 }
 
-cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r, int K,
-                             cdmd_selector selector, double* sigma, double* lambda, double* G,
-                             double* PhiY, double* beta, int32_t* sel, int32_t* nsel,
-                             cudaStream_t stream) {
+namespace {
+
+// Steps 4-7 and 9 from the Gram of the sketch DY (k x n), or, when Rin is
+// given, from that n x n Gram directly (DY and PhiY unused).
+cdmd_status decompose_impl(cdmd_ctx* ctx, const double* DY, int k, const double* Rin, int n, int r, int K,
+                           cdmd_selector selector, double* sigma, double* lambda, double* G, double* PhiY,
+                           double* beta, int32_t* sel, int32_t* nsel, cudaStream_t stream) {
     const int p = n - 1;
     // ---- workspace layout (doubles) ----
     const int ntiles = (n + kGT - 1) / kGT;
     const int kchunk = 128;
-    const int splits = (k + kchunk - 1) / kchunk;
+    const int splits = Rin != nullptr ? 0 : (k + kchunk - 1) / kchunk;
     const size_t n_gram_part = static_cast<size_t>(splits) * n * n;
     const size_t n_R = static_cast<size_t>(n) * n;
     const size_t n_Hv = static_cast<size_t>(p) * p;
@@ -1540,8 +1544,9 @@ cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int 
     if (st != CDMD_OK) return st;
     int* eig_flag = reinterpret_cast<int*>(ws + total);   // written by eig_f32_kernel before any read
     double* gpart = ws;
-    double* R = gpart + n_gram_part;
-    double* Hv = R + n_R;
+    double* Rws = gpart + n_gram_part;
+    const double* R = Rin != nullptr ? Rin : Rws;
+    double* Hv = Rws + n_R;
     double* htau = Hv + n_Hv;
     double* dd = htau + n_vec;
     double* ee = dd + n_vec;
@@ -1559,10 +1564,12 @@ cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int 
     float* W32 = reinterpret_cast<float*>(cvec + 4 * r);         // 2r^2 floats (n_small/2 doubles)
 
     // 1. Gram
-    gram_partial_kernel<<<dim3(ntiles, ntiles, splits), 256, 0, stream>>>(DY, k, n, kchunk, gpart);
-    CDMD_CHECK_LAUNCH("gram_partial_kernel");
-    gram_reduce_kernel<<<(n * n + 255) / 256, 256, 0, stream>>>(gpart, splits, n, R, ctx->d_status);
-    CDMD_CHECK_LAUNCH("gram_reduce_kernel");
+    if (Rin == nullptr) {
+        gram_partial_kernel<<<dim3(ntiles, ntiles, splits), 256, 0, stream>>>(DY, k, n, kchunk, gpart);
+        CDMD_CHECK_LAUNCH("gram_partial_kernel");
+        gram_reduce_kernel<<<(n * n + 255) / 256, 256, 0, stream>>>(gpart, splits, n, Rws, ctx->d_status);
+        CDMD_CHECK_LAUNCH("gram_reduce_kernel");
+    }
 
     // 2. tridiagonalisation on a cluster of 8 CTAs (else 4).  A cluster must
     // fit in one GPC beside other clips' full-data passes: 8 CTAs gave 3.8 %
@@ -1656,12 +1663,27 @@ cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int 
                                          nsel, ctx->d_status, nullptr, nullptr, nullptr, nullptr);
     }
     CDMD_CHECK_LAUNCH("omp_kernel");
-    if (PhiY != nullptr) {
+    if (PhiY != nullptr && DY != nullptr) {
         const int64_t tot = static_cast<int64_t>(k) * r;
         phiy_kernel<<<static_cast<unsigned>((tot + 127) / 128), 128, 0, stream>>>(DY, G, k, p, r, PhiY);
         CDMD_CHECK_LAUNCH("phiy_kernel");
     }
     return CDMD_OK;
+}
+
+}  // namespace
+
+cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r, int K,
+                             cdmd_selector selector, double* sigma, double* lambda, double* G,
+                             double* PhiY, double* beta, int32_t* sel, int32_t* nsel,
+                             cudaStream_t stream) {
+    return decompose_impl(ctx, DY, k, nullptr, n, r, K, selector, sigma, lambda, G, PhiY, beta, sel, nsel, stream);
+}
+
+cdmd_status launch_decompose_gram(cdmd_ctx* ctx, const double* R, int n, int r, int K, cdmd_selector selector,
+                                  double* sigma, double* lambda, double* G, double* beta, int32_t* sel,
+                                  int32_t* nsel, cudaStream_t stream) {
+    return decompose_impl(ctx, nullptr, 0, R, n, r, K, selector, sigma, lambda, G, nullptr, beta, sel, nsel, stream);
 }
 
 }  // namespace cdmd

@@ -1,0 +1,274 @@
+// Exact DMD's one full-data contraction: the snapshot Gram R = D^T D of the
+// uint8 video (R[s][t] = sum_j D[s][j] D[t][j], n x n), on the tensor cores.
+//
+// Exact DMD (Section 2.1) takes the SVD of X itself.  In the method of
+// snapshots every quantity the small solves need (X^T X, X^T X', X'^T X',
+// X'^T x1) is a block of this one Gram matrix, so the decomposition that
+// follows is the compressed one's with R in place of DY^T DY, and the lift
+// and subtract passes are shared.  This is the comparator of the paper's
+// Computational Performance section.
+//
+// uint8 values are exact in BF16 and so are their products; the sums
+// accumulate in FP32 in tensor memory, per CTA over a contiguous pixel range,
+// and a second kernel adds the CTAs' partials in FP64.  Frames are both the
+// A and the B operand, taken from the same shared-memory tile:
+//   tile 0   A = frames 0..127   x  B = frames 0..n-1    (R rows 0..127)
+//   tile 1   A = frames 128..255 x  B = frames 128..n-1  (n > 128 only)
+// The block of rows 128.. against columns 0..127 is the transpose of part of
+// tile 0 and is not computed; the reduce reads every entry from the upper
+// triangle, so R comes out exactly symmetric.
+//
+// One CTA per SM, 256 threads:
+//   warp 0       TMA: the uint8 bytes of 64 pixels x n frames per K step
+//   warp 1       tcgen05.mma issue (M 128, K 16) and commits
+//   warps 2-7    convert the staged bytes to a BF16 tile in the 128-byte
+//                swizzled K-major layout (rows = frames)
+//   warps 4-7    epilogue: tcgen05.ld of the accumulators, FP32 partials
+// Every mbarrier wait is bounded; on a timeout the CTA records
+// CDMD_ERR_TIMEOUT, drains its copies and MMAs, frees TMEM and returns.
+#include "tc_common.cuh"
+
+namespace cdmd {
+namespace {
+
+constexpr int kGThreads = 256;
+constexpr int kGConv = 192;                  // warps 2-7
+constexpr int kGStages = 4;
+constexpr int kGKStep = 64;                  // pixels per K step
+constexpr uint32_t kGBTile = 256u * 128u;    // 256 frame rows x 128 bytes of BF16
+constexpr uint32_t kGStaging = 256u * 64u;   // 256 frames x 64 uint8 pixels
+constexpr uint32_t kGTmemCols = 512;
+
+__host__ __device__ inline int gpad16(int n) { return (n + 15) / 16 * 16; }
+
+__host__ __device__ inline uint32_t gram_smem_bytes() {
+    return kGStages * (kGBTile + kGStaging) + (4 * kGStages + 1) * 8 + 64;
+}
+
+struct GramArgs {
+    float* part;        // [ctas][n][n] FP32 partial sums
+    int64_t m;          // pixels
+    int64_t total_steps, steps_per_cta;
+    int n;
+};
+
+__global__ void __launch_bounds__(kGThreads, 1)
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ GramArgs a, int* status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t* B = smem;                                    // kGStages BF16 tiles (1024-byte aligned)
+    uint8_t* Dst = smem + kGStages * kGBTile;             // kGStages uint8 stagings
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Dst + kGStages * kGStaging);
+    uint64_t* tma_full = bars;
+    uint64_t* d_free = bars + kGStages;
+    uint64_t* b_full = bars + 2 * kGStages;
+    uint64_t* mma_done = bars + 3 * kGStages;
+    uint64_t* accum_done = bars + 4 * kGStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4 * kGStages + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int n = a.n;
+    const int n16 = gpad16(n);
+    const bool two_tiles = n > 128;
+    const int64_t step0 = static_cast<int64_t>(blockIdx.x) * a.steps_per_cta;
+    int64_t nsteps = a.total_steps - step0;
+    if (nsteps > a.steps_per_cta) nsteps = a.steps_per_cta;
+    if (nsteps < 0) nsteps = 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kGStages; ++s) {
+            tc::mbar_init(&tma_full[s], 1);
+            tc::mbar_init(&d_free[s], kGConv);
+            tc::mbar_init(&b_full[s], kGConv);
+            tc::mbar_init(&mma_done[s], 1);
+        }
+        tc::mbar_init(accum_done, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    // frame rows n..255 of every B tile are read by the MMAs (A rows of a
+    // 128-row tile, B rows up to n16) but never written: zero them once
+    for (int s = 0; s < kGStages; ++s)
+        for (uint32_t off = static_cast<uint32_t>(n) * 128u + tid * 16u; off < kGBTile; off += kGThreads * 16u)
+            *reinterpret_cast<uint4*>(B + s * kGBTile + off) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_proxy_async_smem();
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, kGTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            const uint32_t bytes = static_cast<uint32_t>(n) * kGKStep;
+            for (int64_t ks = 0; ks < nsteps; ++ks) {
+                const int s = static_cast<int>(ks % kGStages);
+                const uint32_t u = static_cast<uint32_t>(ks / kGStages);
+                // the staging slot is free once its bytes were converted
+                if (u >= 1 && !tc::mbar_wait(&d_free[s], (u - 1) & 1u, abort_flag, status)) break;
+                tc::mbar_arrive_expect_tx(&tma_full[s], bytes);
+                tc::tma_load_2d(Dst + s * kGStaging, &tmap, static_cast<int>((step0 + ks) * kGKStep), 0, &tma_full[s]);
+            }
+            // drain: the last load of each stage must have landed before exit
+            for (int s = 0; s < kGStages; ++s) {
+                const int64_t uses = (nsteps - s + kGStages - 1) / kGStages;
+                if (uses >= 1) tc::mbar_wait(&tma_full[s], static_cast<uint32_t>(uses - 1) & 1u, abort_flag, status);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc0 = tc::idesc_bf16_f32(128, n16);
+            const uint32_t idesc1 = tc::idesc_bf16_f32(128, two_tiles ? n16 - 128 : 16);
+            for (int64_t ks = 0; ks < nsteps; ++ks) {
+                const int s = static_cast<int>(ks % kGStages);
+                const uint32_t par = static_cast<uint32_t>(ks / kGStages) & 1u;
+                if (!tc::mbar_wait(&b_full[s], par, abort_flag, status)) break;
+                tc::tc_fence_after();
+                const uint32_t base = tc::smem_u32(B + s * kGBTile);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t d0 = tc::desc_sw128(base + kk * 32);                 // frames 0..
+                    tc::mma_bf16(tmem_base, d0, d0, idesc0, (ks | kk) ? 1u : 0u);
+                }
+                if (two_tiles) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t d1 = tc::desc_sw128(base + 128u * 128u + kk * 32);   // frames 128..
+                        tc::mma_bf16(tmem_base + 256u, d1, d1, idesc1, (ks | kk) ? 1u : 0u);
+                    }
+                }
+                tc::mma_commit(&mma_done[s]);
+            }
+            tc::mma_commit(accum_done);   // fires once every MMA issued above has finished
+        }
+    } else {
+        // ---------------- converters (warps 2-7): uint8 -> BF16, 8 pixels of one frame per item ----------------
+        const int ct = tid - 64;
+        const int items = n * 8;
+        for (int64_t ks = 0; ks < nsteps; ++ks) {
+            const int s = static_cast<int>(ks % kGStages);
+            const uint32_t u = static_cast<uint32_t>(ks / kGStages);
+            // the B tile is free once the MMAs of its previous use finished
+            if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
+            if (!tc::mbar_wait(&tma_full[s], u & 1u, abort_flag, status)) break;
+            const uint8_t* src = Dst + s * kGStaging;
+            uint8_t* dst = B + s * kGBTile;
+            for (int it = ct; it < items; it += kGConv) {
+                const int t = it >> 3, c8 = it & 7;
+                const uint2 raw = *reinterpret_cast<const uint2*>(src + t * kGKStep + c8 * 8);
+                uint32_t w[4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t word = h ? raw.y : raw.x;
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        // byte into the mantissa of 2^23: 2^23 + b, exact; minus 2^23
+                        const float f0 = __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540u + 2u * e)) - 8388608.0f;
+                        const float f1 = __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7541u + 2u * e)) - 8388608.0f;
+                        w[h * 2 + e] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+                    }
+                }
+                *reinterpret_cast<uint4*>(dst + tc::sw128_offset(static_cast<uint32_t>(t), static_cast<uint32_t>(c8))) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&d_free[s]);
+            tc::mbar_arrive(&b_full[s]);
+        }
+        // ---------------- epilogue (warps 4-7): FP32 partials of the upper block ----------------
+        if (warp >= 4) {
+            const bool ok = tc::mbar_wait(accum_done, 0u, abort_flag, status) && !*abort_flag;
+            tc::tc_fence_after();
+            if (ok) {
+                const int quarter = warp & 3;
+                float* part = a.part + static_cast<int64_t>(blockIdx.x) * n * n;
+                for (int tile = 0; tile < (two_tiles ? 2 : 1); ++tile) {
+                    const int srow = tile * 128 + quarter * 32 + lane;   // frame of this thread's accumulator row
+                    const int ncol = tile ? n16 - 128 : n16;
+                    for (int c0 = 0; c0 < ncol; c0 += 16) {
+                        uint32_t v[16];
+                        tc::tmem_ld_x16(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + tile * 256u + c0, v);
+                        tc::tmem_wait_ld();
+                        if (srow < n) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const int t = tile * 128 + c0 + q;
+                                if (t < n) part[static_cast<int64_t>(srow) * n + t] = __uint_as_float(v[q]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // teardown: every MMA has finished (accum_done) before TMEM is released
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        if (*abort_flag) tc::mbar_wait(accum_done, 0u, abort_flag, status, 2000000000ull);
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem_base, kGTmemCols);
+    }
+}
+
+// R[s][t] = R[t][s] = sum over CTAs of part[c][min(s,t)][max(s,t)], FP64, in
+// CTA order; blockIdx.y = s, threads over t >= s.
+__global__ void gram_tc_reduce_kernel(const float* __restrict__ part, int ctas, int n, double* __restrict__ R,
+                                      int* status) {
+    const int s = blockIdx.y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < s || t >= n) return;
+    const int64_t nn = static_cast<int64_t>(n) * n;
+    const int64_t src = static_cast<int64_t>(s) * n + t;
+    double v = 0.0;
+    for (int c = 0; c < ctas; ++c) v += static_cast<double>(part[c * nn + src]);
+    if (!isfinite(v)) record_status(status, CDMD_ERR_NONFINITE);
+    R[src] = v;
+    R[static_cast<int64_t>(t) * n + s] = v;
+}
+
+}  // namespace
+
+cdmd_status launch_gram_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, double* R,
+                           cudaStream_t stream) {
+    if (n < 2 || n > 256)
+        return fail(CDMD_ERR_UNSUPPORTED, "the snapshot Gram covers 2 <= n <= 256 frames (got %d)", n);
+    if ((reinterpret_cast<uintptr_t>(D) & 15u) != 0 || (ldd & 15) != 0)
+        return fail(CDMD_ERR_UNSUPPORTED, "the snapshot Gram needs a 16-byte aligned video with ldd %% 16 == 0");
+    CUtensorMap tmap;
+    cdmd_status st = make_video_tmap(&tmap, D, m, n, ldd, kGKStep, n);
+    if (st != CDMD_OK) return st;
+    const int64_t steps = (m + kGKStep - 1) / kGKStep;
+    const int sms = ctx->num_sms > 0 ? ctx->num_sms : 1;
+    int64_t ctas = steps < sms ? steps : sms;
+    const int64_t per = (steps + ctas - 1) / ctas;
+    ctas = (steps + per - 1) / per;
+    float* part = nullptr;
+    st = ensure_buffer(ctx, BUF_GRAM, static_cast<size_t>(ctas) * n * n * sizeof(float), reinterpret_cast<void**>(&part));
+    if (st != CDMD_OK) return st;
+    GramArgs a;
+    a.part = part;
+    a.m = m;
+    a.total_steps = steps;
+    a.steps_per_cta = per;
+    a.n = n;
+    const size_t smem = gram_smem_bytes() + 1024;
+    CDMD_CHECK_CUDA(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem)));
+    gram_tc_kernel<<<static_cast<unsigned>(ctas), kGThreads, smem, stream>>>(tmap, a, ctx->d_status);
+    CDMD_CHECK_LAUNCH("gram_tc_kernel");
+    gram_tc_reduce_kernel<<<dim3((n + 127) / 128, n), 128, 0, stream>>>(part, static_cast<int>(ctas), n, R,
+                                                                        ctx->d_status);
+    CDMD_CHECK_LAUNCH("gram_tc_reduce_kernel");
+    return CDMD_OK;
+}
+
+}  // namespace cdmd
