@@ -18,12 +18,13 @@
 // tile 0 and is not computed; the reduce reads every entry from the upper
 // triangle, so R comes out exactly symmetric.
 //
-// One CTA per SM, 256 threads:
+// One CTA per SM, 384 threads:
 //   warp 0       TMA: the uint8 bytes of 64 pixels x n frames per K step
 //   warp 1       tcgen05.mma issue (M 128, K 16) and commits
-//   warps 2-7    convert the staged bytes to a BF16 tile in the 128-byte
-//                swizzled K-major layout (rows = frames)
-//   warps 4-7    epilogue: tcgen05.ld of the accumulators, FP32 partials
+//   warps 2-11   convert the staged bytes to a BF16 tile in the 128-byte
+//                swizzled K-major layout (rows = frames), 16 pixels per item
+//   warps 4-7    epilogue: tcgen05.ld of the accumulators, FP32 partials of
+//                the upper triangle
 // Every mbarrier wait is bounded; on a timeout the CTA records
 // CDMD_ERR_TIMEOUT, drains its copies and MMAs, frees TMEM and returns.
 #include "tc_common.cuh"
@@ -31,8 +32,8 @@
 namespace cdmd {
 namespace {
 
-constexpr int kGThreads = 256;
-constexpr int kGConv = 192;                  // warps 2-7
+constexpr int kGThreads = 384;
+constexpr int kGConv = 320;                  // warps 2-11
 constexpr int kGStages = 4;
 constexpr int kGKStep = 64;                  // pixels per K step
 constexpr uint32_t kGBTile = 256u * 128u;    // 256 frame rows x 128 bytes of BF16
@@ -150,9 +151,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
             tc::mma_commit(accum_done);   // fires once every MMA issued above has finished
         }
     } else {
-        // ---------------- converters (warps 2-7): uint8 -> BF16, 8 pixels of one frame per item ----------------
+        // ---------------- converters (warps 2-11): uint8 -> BF16, 16 pixels of one frame per item ----------------
         const int ct = tid - 64;
-        const int items = n * 8;
+        const int items = n * 4;
         for (int64_t ks = 0; ks < nsteps; ++ks) {
             const int s = static_cast<int>(ks % kGStages);
             const uint32_t u = static_cast<uint32_t>(ks / kGStages);
@@ -162,12 +163,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
             const uint8_t* src = Dst + s * kGStaging;
             uint8_t* dst = B + s * kGBTile;
             for (int it = ct; it < items; it += kGConv) {
-                const int t = it >> 3, c8 = it & 7;
-                const uint2 raw = *reinterpret_cast<const uint2*>(src + t * kGKStep + c8 * 8);
-                uint32_t w[4];
+                const int t = it >> 2, c16 = it & 3;
+                const uint4 raw = *reinterpret_cast<const uint4*>(src + t * kGKStep + c16 * 16);
+                uint32_t w[8];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t word = h ? raw.y : raw.x;
+                for (int h = 0; h < 4; ++h) {
+                    const uint32_t word = h == 0 ? raw.x : h == 1 ? raw.y : h == 2 ? raw.z : raw.w;
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         // byte into the mantissa of 2^23: 2^23 + b, exact; minus 2^23
@@ -176,8 +177,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
                         w[h * 2 + e] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
                     }
                 }
-                *reinterpret_cast<uint4*>(dst + tc::sw128_offset(static_cast<uint32_t>(t), static_cast<uint32_t>(c8))) =
-                    make_uint4(w[0], w[1], w[2], w[3]);
+                // two 16-byte chunks of the swizzled row; a quarter warp covers
+                // an even and an odd row, so its eight stores hit distinct banks
+                const uint32_t row = static_cast<uint32_t>(t);
+                *reinterpret_cast<uint4*>(dst + tc::sw128_offset(row, 2u * c16)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(dst + tc::sw128_offset(row, 2u * c16 + 1u)) = make_uint4(w[4], w[5], w[6], w[7]);
             }
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&d_free[s]);
@@ -201,7 +205,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
 #pragma unroll
                             for (int q = 0; q < 16; ++q) {
                                 const int t = tile * 128 + c0 + q;
-                                if (t < n) part[static_cast<int64_t>(srow) * n + t] = __uint_as_float(v[q]);
+                                if (t >= srow && t < n) part[static_cast<int64_t>(srow) * n + t] = __uint_as_float(v[q]);
                             }
                         }
                     }
@@ -219,20 +223,38 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
     }
 }
 
-// R[s][t] = R[t][s] = sum over CTAs of part[c][min(s,t)][max(s,t)], FP64, in
-// CTA order; blockIdx.y = s, threads over t >= s.
-__global__ void gram_tc_reduce_kernel(const float* __restrict__ part, int ctas, int n, double* __restrict__ R,
-                                      int* status) {
+// R[s][t] = R[t][s] = sum over CTAs of part[c][s][t] (t >= s), FP64, in a
+// fixed order.  blockIdx.y = s; a block covers 32 consecutive t and its 8
+// warps split the CTAs (warp g adds CTAs g, g+8, ...), then warp 0 adds the
+// 8 sums in warp order.
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(32 * kRedWarps)
+gram_tc_reduce_kernel(const float* __restrict__ part, int ctas, int n, double* __restrict__ R, int* status) {
+    __shared__ double red[kRedWarps][32];
     const int s = blockIdx.y;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < s || t >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int g = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + lane;
+    if (blockIdx.x * 32 + 31 < s) return;   // the whole block is below the diagonal
+    const bool live = t >= s && t < n;
     const int64_t nn = static_cast<int64_t>(n) * n;
     const int64_t src = static_cast<int64_t>(s) * n + t;
     double v = 0.0;
-    for (int c = 0; c < ctas; ++c) v += static_cast<double>(part[c * nn + src]);
-    if (!isfinite(v)) record_status(status, CDMD_ERR_NONFINITE);
-    R[src] = v;
-    R[static_cast<int64_t>(t) * n + s] = v;
+    if (live) {
+#pragma unroll 4
+        for (int c = g; c < ctas; c += kRedWarps) v += static_cast<double>(part[c * nn + src]);
+    }
+    red[g][lane] = v;
+    __syncthreads();
+    if (g == 0 && live) {
+        double tot = 0.0;
+#pragma unroll
+        for (int i = 0; i < kRedWarps; ++i) tot += red[i][lane];
+        if (!isfinite(tot)) record_status(status, CDMD_ERR_NONFINITE);
+        R[src] = tot;
+        R[static_cast<int64_t>(t) * n + s] = tot;
+    }
 }
 
 }  // namespace
@@ -265,8 +287,8 @@ cdmd_status launch_gram_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, in
                                          static_cast<int>(smem)));
     gram_tc_kernel<<<static_cast<unsigned>(ctas), kGThreads, smem, stream>>>(tmap, a, ctx->d_status);
     CDMD_CHECK_LAUNCH("gram_tc_kernel");
-    gram_tc_reduce_kernel<<<dim3((n + 127) / 128, n), 128, 0, stream>>>(part, static_cast<int>(ctas), n, R,
-                                                                        ctx->d_status);
+    gram_tc_reduce_kernel<<<dim3((n + 31) / 32, n), 32 * kRedWarps, 0, stream>>>(part, static_cast<int>(ctas), n, R,
+                                                                                 ctx->d_status);
     CDMD_CHECK_LAUNCH("gram_tc_reduce_kernel");
     return CDMD_OK;
 }

@@ -9,8 +9,9 @@
 // (row above, same row, row below; left, centre, right), clears the
 // neighbours that would wrap across a row end, and counts the ones per bit
 // with a bit-sliced adder.  A thread keeps one word position for four frames,
-// so its row-edge masks are computed once.  HBM traffic is one read and one
-// write of the mask; the row above and below come from L1/L2.
+// so its row-edge masks are computed once, and loads all their words before
+// it uses any (36 loads in flight).  HBM traffic is one read and one write of
+// the mask; the row above and below come from L1/L2.
 #include "cdmd_internal.cuh"
 
 namespace cdmd {
@@ -52,19 +53,31 @@ __global__ void __launch_bounds__(kMedianThreads) median3x3_kernel(const uint32_
     for (uint32_t b = (x0 == 0u) ? 0u : W - x0; b < 32u; b += W) left |= 1u << b;
     for (uint32_t b = W - 1u - x0; b < 32u; b += W) right |= 1u << b;
 
-    const int f_end = min(n, static_cast<int>(blockIdx.y + 1) * kMedianFrames);
-    for (int f = blockIdx.y * kMedianFrames; f < f_end; ++f) {
+    // all frames' words are loaded before any is used, so each thread keeps
+    // 9 x kMedianFrames loads in flight
+    const int f0 = static_cast<int>(blockIdx.y) * kMedianFrames;
+    uint32_t win[kMedianFrames][3][3];
+#pragma unroll
+    for (int i = 0; i < kMedianFrames; ++i) {
+        const int f = min(f0 + i, n - 1);   // a frame past n repeats the last one; its result is not stored
         const uint32_t* fr = in + static_cast<int64_t>(f) * nw;
-        uint32_t v[9];
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
             // the row's window starts one pixel left of p0 + (dy - 1) W
             const int64_t q = static_cast<int64_t>(p0) + static_cast<int64_t>(dy - 1) * W - 1;
             const int64_t wq = q >> 5;   // floor for negative q too
+#pragma unroll
+            for (int c = 0; c < 3; ++c) win[i][dy][c] = mask_word(fr, wq + c, nw, tail);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kMedianFrames; ++i) {
+        uint32_t v[9];
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const int64_t q = static_cast<int64_t>(p0) + static_cast<int64_t>(dy - 1) * W - 1;
             const uint32_t s = static_cast<uint32_t>(q) & 31u;
-            const uint32_t a = mask_word(fr, wq, nw, tail);
-            const uint32_t b = mask_word(fr, wq + 1, nw, tail);
-            const uint32_t c = mask_word(fr, wq + 2, nw, tail);
+            const uint32_t a = win[i][dy][0], b = win[i][dy][1], c = win[i][dy][2];
             v[3 * dy + 0] = window(a, b, c, s) & ~left;
             v[3 * dy + 1] = window(a, b, c, s + 1u);
             v[3 * dy + 2] = window(a, b, c, s + 2u) & ~right;
@@ -80,7 +93,7 @@ __global__ void __launch_bounds__(kMedianThreads) median3x3_kernel(const uint32_
         const uint32_t ge2 = t2 | (C & t1);
         uint32_t r = ge3 | (ge2 & S);
         if (w == nw - 1) r &= tail;
-        out[static_cast<int64_t>(f) * nw + w] = r;
+        if (f0 + i < n) out[static_cast<int64_t>(f0 + i) * nw + w] = r;
     }
 }
 
