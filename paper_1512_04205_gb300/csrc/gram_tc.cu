@@ -19,10 +19,12 @@
 // triangle, so R comes out exactly symmetric.
 //
 // One CTA per SM, 384 threads:
-//   warp 0       TMA: the uint8 bytes of 64 pixels x n frames per K step
+//   warp 0       TMA: the uint8 bytes of 64 pixels x n frames per K step,
+//                into an 8-slot staging ring (8 loads in flight)
 //   warp 1       tcgen05.mma issue (M 128, K 16) and commits
 //   warps 2-11   convert the staged bytes to a BF16 tile in the 128-byte
-//                swizzled K-major layout (rows = frames), 16 pixels per item
+//                swizzled K-major layout (rows = frames), 16 pixels per item,
+//                into a 3-slot ring of operand tiles
 //   warps 4-7    epilogue: tcgen05.ld of the accumulators, FP32 partials of
 //                the upper triangle
 // Every mbarrier wait is bounded; on a timeout the CTA records
@@ -34,7 +36,8 @@ namespace {
 
 constexpr int kGThreads = 384;
 constexpr int kGConv = 320;                  // warps 2-11
-constexpr int kGStages = 4;
+constexpr int kGStg = 8;                     // uint8 staging slots (loads in flight)
+constexpr int kGBuf = 3;                     // BF16 operand tiles
 constexpr int kGKStep = 64;                  // pixels per K step
 constexpr uint32_t kGBTile = 256u * 128u;    // 256 frame rows x 128 bytes of BF16
 constexpr uint32_t kGStaging = 256u * 64u;   // 256 frames x 64 uint8 pixels
@@ -43,7 +46,7 @@ constexpr uint32_t kGTmemCols = 512;
 __host__ __device__ inline int gpad16(int n) { return (n + 15) / 16 * 16; }
 
 __host__ __device__ inline uint32_t gram_smem_bytes() {
-    return kGStages * (kGBTile + kGStaging) + (4 * kGStages + 1) * 8 + 64;
+    return kGBuf * kGBTile + kGStg * kGStaging + (2 * kGStg + 2 * kGBuf + 1) * 8 + 64;
 }
 
 struct GramArgs {
@@ -57,15 +60,15 @@ __global__ void __launch_bounds__(kGThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ GramArgs a, int* status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint8_t* B = smem;                                    // kGStages BF16 tiles (1024-byte aligned)
-    uint8_t* Dst = smem + kGStages * kGBTile;             // kGStages uint8 stagings
-    uint64_t* bars = reinterpret_cast<uint64_t*>(Dst + kGStages * kGStaging);
-    uint64_t* tma_full = bars;
-    uint64_t* d_free = bars + kGStages;
-    uint64_t* b_full = bars + 2 * kGStages;
-    uint64_t* mma_done = bars + 3 * kGStages;
-    uint64_t* accum_done = bars + 4 * kGStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4 * kGStages + 1);
+    uint8_t* B = smem;                                    // kGBuf BF16 tiles (1024-byte aligned)
+    uint8_t* Dst = smem + kGBuf * kGBTile;                // kGStg uint8 stagings
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Dst + kGStg * kGStaging);
+    uint64_t* tma_full = bars;                            // [kGStg] bytes landed
+    uint64_t* d_free = bars + kGStg;                      // [kGStg] bytes converted
+    uint64_t* b_full = bars + 2 * kGStg;                  // [kGBuf] tile written
+    uint64_t* mma_done = bars + 2 * kGStg + kGBuf;        // [kGBuf] tile read by the MMAs
+    uint64_t* accum_done = bars + 2 * kGStg + 2 * kGBuf;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum_done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
     const int tid = threadIdx.x;
@@ -80,9 +83,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
     if (nsteps < 0) nsteps = 0;
 
     if (tid == 0) {
-        for (int s = 0; s < kGStages; ++s) {
+        for (int s = 0; s < kGStg; ++s) {
             tc::mbar_init(&tma_full[s], 1);
             tc::mbar_init(&d_free[s], kGConv);
+        }
+        for (int s = 0; s < kGBuf; ++s) {
             tc::mbar_init(&b_full[s], kGConv);
             tc::mbar_init(&mma_done[s], 1);
         }
@@ -92,7 +97,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
     }
     // frame rows n..255 of every B tile are read by the MMAs (A rows of a
     // 128-row tile, B rows up to n16) but never written: zero them once
-    for (int s = 0; s < kGStages; ++s)
+    for (int s = 0; s < kGBuf; ++s)
         for (uint32_t off = static_cast<uint32_t>(n) * 128u + tid * 16u; off < kGBTile; off += kGThreads * 16u)
             *reinterpret_cast<uint4*>(B + s * kGBTile + off) = make_uint4(0u, 0u, 0u, 0u);
     tc::fence_proxy_async_smem();
@@ -110,16 +115,16 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
         if (lane == 0) {
             const uint32_t bytes = static_cast<uint32_t>(n) * kGKStep;
             for (int64_t ks = 0; ks < nsteps; ++ks) {
-                const int s = static_cast<int>(ks % kGStages);
-                const uint32_t u = static_cast<uint32_t>(ks / kGStages);
+                const int s = static_cast<int>(ks % kGStg);
+                const uint32_t u = static_cast<uint32_t>(ks / kGStg);
                 // the staging slot is free once its bytes were converted
                 if (u >= 1 && !tc::mbar_wait(&d_free[s], (u - 1) & 1u, abort_flag, status)) break;
                 tc::mbar_arrive_expect_tx(&tma_full[s], bytes);
                 tc::tma_load_2d(Dst + s * kGStaging, &tmap, static_cast<int>((step0 + ks) * kGKStep), 0, &tma_full[s]);
             }
             // drain: the last load of each stage must have landed before exit
-            for (int s = 0; s < kGStages; ++s) {
-                const int64_t uses = (nsteps - s + kGStages - 1) / kGStages;
+            for (int s = 0; s < kGStg; ++s) {
+                const int64_t uses = (nsteps - s + kGStg - 1) / kGStg;
                 if (uses >= 1) tc::mbar_wait(&tma_full[s], static_cast<uint32_t>(uses - 1) & 1u, abort_flag, status);
             }
         }
@@ -129,8 +134,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
             const uint32_t idesc0 = tc::idesc_bf16_f32(128, n16);
             const uint32_t idesc1 = tc::idesc_bf16_f32(128, two_tiles ? n16 - 128 : 16);
             for (int64_t ks = 0; ks < nsteps; ++ks) {
-                const int s = static_cast<int>(ks % kGStages);
-                const uint32_t par = static_cast<uint32_t>(ks / kGStages) & 1u;
+                const int s = static_cast<int>(ks % kGBuf);
+                const uint32_t par = static_cast<uint32_t>(ks / kGBuf) & 1u;
                 if (!tc::mbar_wait(&b_full[s], par, abort_flag, status)) break;
                 tc::tc_fence_after();
                 const uint32_t base = tc::smem_u32(B + s * kGBTile);
@@ -155,13 +160,15 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
         const int ct = tid - 64;
         const int items = n * 4;
         for (int64_t ks = 0; ks < nsteps; ++ks) {
-            const int s = static_cast<int>(ks % kGStages);
-            const uint32_t u = static_cast<uint32_t>(ks / kGStages);
+            const int sg = static_cast<int>(ks % kGStg);
+            const uint32_t ug = static_cast<uint32_t>(ks / kGStg);
+            const int sb = static_cast<int>(ks % kGBuf);
+            const uint32_t ub = static_cast<uint32_t>(ks / kGBuf);
             // the B tile is free once the MMAs of its previous use finished
-            if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
-            if (!tc::mbar_wait(&tma_full[s], u & 1u, abort_flag, status)) break;
-            const uint8_t* src = Dst + s * kGStaging;
-            uint8_t* dst = B + s * kGBTile;
+            if (ub >= 1 && !tc::mbar_wait(&mma_done[sb], (ub - 1) & 1u, abort_flag, status)) break;
+            if (!tc::mbar_wait(&tma_full[sg], ug & 1u, abort_flag, status)) break;
+            const uint8_t* src = Dst + sg * kGStaging;
+            uint8_t* dst = B + sb * kGBTile;
             for (int it = ct; it < items; it += kGConv) {
                 const int t = it >> 2, c16 = it & 3;
                 const uint4 raw = *reinterpret_cast<const uint4*>(src + t * kGKStep + c16 * 16);
@@ -184,8 +191,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
                 *reinterpret_cast<uint4*>(dst + tc::sw128_offset(row, 2u * c16 + 1u)) = make_uint4(w[4], w[5], w[6], w[7]);
             }
             tc::fence_proxy_async_smem();
-            tc::mbar_arrive(&d_free[s]);
-            tc::mbar_arrive(&b_full[s]);
+            tc::mbar_arrive(&d_free[sg]);
+            tc::mbar_arrive(&b_full[sb]);
         }
         // ---------------- epilogue (warps 4-7): FP32 partials of the upper block ----------------
         if (warp >= 4) {

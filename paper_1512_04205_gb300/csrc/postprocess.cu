@@ -20,18 +20,6 @@ namespace {
 constexpr int kMedianThreads = 256;
 constexpr int kMedianFrames = 4;   // frames per thread
 
-// Word w of a frame, zero outside [0, nw), bits past m cleared.
-__device__ __forceinline__ uint32_t mask_word(const uint32_t* f, int64_t w, int64_t nw, uint32_t tail) {
-    if (w < 0 || w >= nw) return 0u;
-    const uint32_t v = __ldg(f + w);
-    return (w == nw - 1) ? (v & tail) : v;
-}
-
-// Bits off .. off+31 of the 96-bit string c:b:a (off <= 33).
-__device__ __forceinline__ uint32_t window(uint32_t a, uint32_t b, uint32_t c, uint32_t off) {
-    return off < 32u ? __funnelshift_r(a, b, off) : __funnelshift_r(b, c, off - 32u);
-}
-
 __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t& sum, uint32_t& carry) {
     const uint32_t t = a ^ b;
     sum = t ^ c;
@@ -53,6 +41,24 @@ __global__ void __launch_bounds__(kMedianThreads) median3x3_kernel(const uint32_
     for (uint32_t b = (x0 == 0u) ? 0u : W - x0; b < 32u; b += W) left |= 1u << b;
     for (uint32_t b = W - 1u - x0; b < 32u; b += W) right |= 1u << b;
 
+    // Frame-independent part: row dy's window starts one pixel left of
+    // p0 + (dy - 1) W, i.e. at bit s of word wq; the three words wq .. wq+2
+    // cover it.  keep[][] is 0 for a word outside the frame, the tail mask
+    // for the last word, all ones otherwise.
+    int64_t wq[3];
+    uint32_t sh[3], keep[3][3];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+        const int64_t q = static_cast<int64_t>(p0) + static_cast<int64_t>(dy - 1) * W - 1;
+        wq[dy] = q >> 5;   // floor for negative q too
+        sh[dy] = static_cast<uint32_t>(q) & 31u;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int64_t x = wq[dy] + c;
+            keep[dy][c] = (x < 0 || x >= nw) ? 0u : (x == nw - 1 ? tail : 0xffffffffu);
+        }
+    }
+
     // all frames' words are loaded before any is used, so each thread keeps
     // 9 x kMedianFrames loads in flight
     const int f0 = static_cast<int>(blockIdx.y) * kMedianFrames;
@@ -62,25 +68,22 @@ __global__ void __launch_bounds__(kMedianThreads) median3x3_kernel(const uint32_
         const int f = min(f0 + i, n - 1);   // a frame past n repeats the last one; its result is not stored
         const uint32_t* fr = in + static_cast<int64_t>(f) * nw;
 #pragma unroll
-        for (int dy = 0; dy < 3; ++dy) {
-            // the row's window starts one pixel left of p0 + (dy - 1) W
-            const int64_t q = static_cast<int64_t>(p0) + static_cast<int64_t>(dy - 1) * W - 1;
-            const int64_t wq = q >> 5;   // floor for negative q too
+        for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) win[i][dy][c] = mask_word(fr, wq + c, nw, tail);
-        }
+            for (int c = 0; c < 3; ++c) win[i][dy][c] = keep[dy][c] ? (__ldg(fr + wq[dy] + c) & keep[dy][c]) : 0u;
     }
 #pragma unroll
     for (int i = 0; i < kMedianFrames; ++i) {
         uint32_t v[9];
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
-            const int64_t q = static_cast<int64_t>(p0) + static_cast<int64_t>(dy - 1) * W - 1;
-            const uint32_t s = static_cast<uint32_t>(q) & 31u;
-            const uint32_t a = win[i][dy][0], b = win[i][dy][1], c = win[i][dy][2];
-            v[3 * dy + 0] = window(a, b, c, s) & ~left;
-            v[3 * dy + 1] = window(a, b, c, s + 1u);
-            v[3 * dy + 2] = window(a, b, c, s + 2u) & ~right;
+            // bits s .. s+31 and s+32 .. s+63 of the 96-bit string c:b:a; the
+            // centre and right windows start one and two bits later
+            const uint32_t lo = __funnelshift_r(win[i][dy][0], win[i][dy][1], sh[dy]);
+            const uint32_t hi = __funnelshift_r(win[i][dy][1], win[i][dy][2], sh[dy]);
+            v[3 * dy + 0] = lo & ~left;
+            v[3 * dy + 1] = __funnelshift_r(lo, hi, 1u);
+            v[3 * dy + 2] = __funnelshift_r(lo, hi, 2u) & ~right;
         }
         uint32_t s1, c1, s2, c2, s3, c3, S, C, t1, t2;
         full_add(v[0], v[1], v[2], s1, c1);
