@@ -713,7 +713,7 @@ def run_ours(args, rank, world, local_rank):
                               "flops": 2.0 * m * n * n, "bytes": m * n},
             "cdmd_single_stream_over_exact": latency_value / exact_value,
             "fmeasure_vs_truth": fmeasure(exact["mask"], truth),
-            "form": ("snapshot Gram D^T D on tcgen05 (uint8 exact in BF16, FP32 accumulation, FP64 reduce); "
+            "form": ("snapshot Gram D^T D on tcgen05 (uint8 exact in FP16, FP32 accumulation, FP64 reduce); "
                      f"FP64 small solves from the Gram; OMP; {args.prec} lift; one clip per step, one stream")}
     if batch_line is not None:
         line["batch"] = batch_line

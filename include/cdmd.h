@@ -251,7 +251,7 @@ cdmd_status cdmd_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r,
  *
  * cdmd_snapshot_gram: R[s*n + t] = sum_j D[s*ldd + j] D[t*ldd + j] (FP64,
  * device, n x n, exactly symmetric).  The products are exact (uint8 in
- * BF16 on the tensor cores); sums accumulate in FP32 over each SM's pixel
+ * FP16 on the tensor cores); sums accumulate in FP32 over each SM's pixel
  * range (the accumulation truncates: relative error <= 2^-23 per 16-pixel
  * step of that range, coherent) and the ranges are added in FP64.  Needs 2 <= n <= 256, D 16-byte aligned and
  * ldd % 16 == 0 (else CDMD_ERR_UNSUPPORTED).

@@ -8,9 +8,13 @@
 // and subtract passes are shared.  This is the comparator of the paper's
 // Computational Performance section.
 //
-// uint8 values are exact in BF16 and so are their products; the sums
+// uint8 values are exact in FP16 and so are their products; the sums
 // accumulate in FP32 in tensor memory, per CTA over a contiguous pixel range,
-// and a second kernel adds the CTAs' partials in FP64.  Frames are both the
+// and a second kernel adds the CTAs' partials in FP64.  FP16 rather than
+// BF16 because both operands are frames and FP16 converts in two
+// instructions per pixel pair: 1024 + b (b < 1024) is exact in FP16, so a
+// byte permute builds the halves 0x6400 | b and one packed subtract of 1024
+// leaves b.  Frames are both the
 // A and the B operand, taken from the same shared-memory tile:
 //   tile 0   A = frames 0..127   x  B = frames 0..n-1    (R rows 0..127)
 //   tile 1   A = frames 128..255 x  B = frames 128..n-1  (n > 128 only)
@@ -22,7 +26,7 @@
 //   warp 0       TMA: the uint8 bytes of 64 pixels x n frames per K step,
 //                into an 8-slot staging ring (8 loads in flight)
 //   warp 1       tcgen05.mma issue (M 128, K 16) and commits
-//   warps 2-11   convert the staged bytes to a BF16 tile in the 128-byte
+//   warps 2-11   convert the staged bytes to an FP16 tile in the 128-byte
 //                swizzled K-major layout (rows = frames), 16 pixels per item,
 //                into a 3-slot ring of operand tiles
 //   warps 4-7    epilogue: tcgen05.ld of the accumulators, FP32 partials of
@@ -37,13 +41,20 @@ namespace {
 constexpr int kGThreads = 384;
 constexpr int kGConv = 320;                  // warps 2-11
 constexpr int kGStg = 8;                     // uint8 staging slots (loads in flight)
-constexpr int kGBuf = 3;                     // BF16 operand tiles
+constexpr int kGBuf = 3;                     // FP16 operand tiles
 constexpr int kGKStep = 64;                  // pixels per K step
-constexpr uint32_t kGBTile = 256u * 128u;    // 256 frame rows x 128 bytes of BF16
+constexpr uint32_t kGBTile = 256u * 128u;    // 256 frame rows x 128 bytes of FP16
 constexpr uint32_t kGStaging = 256u * 64u;   // 256 frames x 64 uint8 pixels
 constexpr uint32_t kGTmemCols = 512;
 
 __host__ __device__ inline int gpad16(int n) { return (n + 15) / 16 * 16; }
+
+// Both FP16 halves of x minus 1024 (exact for halves 1024 .. 2047).
+__device__ __forceinline__ uint32_t sub_1024_f16x2(uint32_t x) {
+    uint32_t r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(0x64006400u));
+    return r;
+}
 
 __host__ __device__ inline uint32_t gram_smem_bytes() {
     return kGBuf * kGBTile + kGStg * kGStaging + (2 * kGStg + 2 * kGBuf + 1) * 8 + 64;
@@ -60,7 +71,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ GramArgs a, int* status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint8_t* B = smem;                                    // kGBuf BF16 tiles (1024-byte aligned)
+    uint8_t* B = smem;                                    // kGBuf FP16 tiles (1024-byte aligned)
     uint8_t* Dst = smem + kGBuf * kGBTile;                // kGStg uint8 stagings
     uint64_t* bars = reinterpret_cast<uint64_t*>(Dst + kGStg * kGStaging);
     uint64_t* tma_full = bars;                            // [kGStg] bytes landed
@@ -131,8 +142,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc0 = tc::idesc_bf16_f32(128, n16);
-            const uint32_t idesc1 = tc::idesc_bf16_f32(128, two_tiles ? n16 - 128 : 16);
+            const uint32_t idesc0 = tc::idesc_f16_f32(128, n16);
+            const uint32_t idesc1 = tc::idesc_f16_f32(128, two_tiles ? n16 - 128 : 16);
             for (int64_t ks = 0; ks < nsteps; ++ks) {
                 const int s = static_cast<int>(ks % kGBuf);
                 const uint32_t par = static_cast<uint32_t>(ks / kGBuf) & 1u;
@@ -142,13 +153,13 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const uint64_t d0 = tc::desc_sw128(base + kk * 32);                 // frames 0..
-                    tc::mma_bf16(tmem_base, d0, d0, idesc0, (ks | kk) ? 1u : 0u);
+                    tc::mma_f16(tmem_base, d0, d0, idesc0, (ks | kk) ? 1u : 0u);
                 }
                 if (two_tiles) {
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint64_t d1 = tc::desc_sw128(base + 128u * 128u + kk * 32);   // frames 128..
-                        tc::mma_bf16(tmem_base + 256u, d1, d1, idesc1, (ks | kk) ? 1u : 0u);
+                        tc::mma_f16(tmem_base + 256u, d1, d1, idesc1, (ks | kk) ? 1u : 0u);
                     }
                 }
                 tc::mma_commit(&mma_done[s]);
@@ -156,7 +167,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
             tc::mma_commit(accum_done);   // fires once every MMA issued above has finished
         }
     } else {
-        // ---------------- converters (warps 2-11): uint8 -> BF16, 16 pixels of one frame per item ----------------
+        // ---------------- converters (warps 2-11): uint8 -> FP16, 16 pixels of one frame per item ----------------
         const int ct = tid - 64;
         const int items = n * 4;
         for (int64_t ks = 0; ks < nsteps; ++ks) {
@@ -176,13 +187,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     const uint32_t word = h == 0 ? raw.x : h == 1 ? raw.y : h == 2 ? raw.z : raw.w;
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        // byte into the mantissa of 2^23: 2^23 + b, exact; minus 2^23
-                        const float f0 = __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540u + 2u * e)) - 8388608.0f;
-                        const float f1 = __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7541u + 2u * e)) - 8388608.0f;
-                        w[h * 2 + e] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
-                    }
+                    // halves 0x6400 | b = 1024 + b for bytes (0, 1) and (2, 3), then minus 1024, exact
+                    w[h * 2 + 0] = sub_1024_f16x2(__byte_perm(word, 0x64646464u, 0x4140u));
+                    w[h * 2 + 1] = sub_1024_f16x2(__byte_perm(word, 0x64646464u, 0x4342u));
                 }
                 // two 16-byte chunks of the swizzled row; a quarter warp covers
                 // an even and an odd row, so its eight stores hit distinct banks

@@ -121,6 +121,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
         : "memory");
 }
 
+// The same instruction for FP16 inputs: kind::f16 takes its A and B type
+// (both F16 or both BF16) from the instruction descriptor (idesc_f16_f32).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    mma_bf16(d_tmem, a_desc, b_desc, idesc, accumulate);
+}
+
 // D[tmem] (+)= A[smem] * B[smem]^T, TF32 inputs (FP32 words in shared memory,
 // the low 13 mantissa bits ignored), FP32 accumulation, M = 128, K = 8.
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
@@ -169,6 +176,11 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
            (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// Instruction descriptor: kind::f16, A = B = F16, D = F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+    return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 // Instruction descriptor: kind::tf32, A = B = TF32, D = F32, both K-major.

@@ -3,7 +3,7 @@ Computational Performance): the snapshot Gram pass against exact integer
 inner products, the decomposition from a Gram against the one from a sketch,
 and the whole exact-DMD pipeline against the FP64 oracle's exact DMD.
 
-The Gram's products are exact (uint8 in BF16) and its sums accumulate in
+The Gram's products are exact (uint8 in FP16) and its sums accumulate in
 FP32 over each CTA's pixel range.  The tensor cores' accumulation is not
 rounded to nearest: an addition may lose up to one unit in the last place,
 2^-23 of the running sum, and the losses add up coherently.  Every partial
