@@ -61,7 +61,7 @@ __host__ __device__ inline uint32_t gram_smem_bytes() {
 }
 
 struct GramArgs {
-    float* part;        // [ctas][n][n] FP32 partial sums
+    float* part;        // [ctas][t][s] FP32 partial sums, s <= t
     int64_t m;          // pixels
     int64_t total_steps, steps_per_cta;
     int n;
@@ -215,11 +215,13 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
                         uint32_t v[16];
                         tc::tmem_ld_x16(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + tile * 256u + c0, v);
                         tc::tmem_wait_ld();
+                        // column-major partials: for each t the warp's 32 rows
+                        // are 32 consecutive floats
                         if (srow < n) {
 #pragma unroll
                             for (int q = 0; q < 16; ++q) {
                                 const int t = tile * 128 + c0 + q;
-                                if (t >= srow && t < n) part[static_cast<int64_t>(srow) * n + t] = __uint_as_float(v[q]);
+                                if (t >= srow && t < n) part[static_cast<int64_t>(t) * n + srow] = __uint_as_float(v[q]);
                             }
                         }
                     }
@@ -237,8 +239,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
     }
 }
 
-// R[s][t] = R[t][s] = sum over CTAs of part[c][s][t] (t >= s), FP64, in a
-// fixed order.  blockIdx.y = s; a block covers 32 consecutive t and its 8
+// R[s][t] = R[t][s] = sum over CTAs of part[c][t][s] (s <= t), FP64, in a
+// fixed order.  blockIdx.y = t; a block covers 32 consecutive s and its 8
 // warps split the CTAs (warp g adds CTAs g, g+8, ...), then warp 0 adds the
 // 8 sums in warp order.
 constexpr int kRedWarps = 8;
@@ -246,14 +248,14 @@ constexpr int kRedWarps = 8;
 __global__ void __launch_bounds__(32 * kRedWarps)
 gram_tc_reduce_kernel(const float* __restrict__ part, int ctas, int n, double* __restrict__ R, int* status) {
     __shared__ double red[kRedWarps][32];
-    const int s = blockIdx.y;
+    const int t = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const int g = threadIdx.x >> 5;
-    const int t = blockIdx.x * 32 + lane;
-    if (blockIdx.x * 32 + 31 < s) return;   // the whole block is below the diagonal
-    const bool live = t >= s && t < n;
+    const int s = blockIdx.x * 32 + lane;
+    if (blockIdx.x * 32 > t) return;   // the whole block is below the diagonal
+    const bool live = s <= t;
     const int64_t nn = static_cast<int64_t>(n) * n;
-    const int64_t src = static_cast<int64_t>(s) * n + t;
+    const int64_t src = static_cast<int64_t>(t) * n + s;
     double v = 0.0;
     if (live) {
 #pragma unroll 4
@@ -266,8 +268,8 @@ gram_tc_reduce_kernel(const float* __restrict__ part, int ctas, int n, double* _
 #pragma unroll
         for (int i = 0; i < kRedWarps; ++i) tot += red[i][lane];
         if (!isfinite(tot)) record_status(status, CDMD_ERR_NONFINITE);
-        R[src] = tot;
-        R[static_cast<int64_t>(t) * n + s] = tot;
+        R[src] = tot;                                   // R[t][s]
+        R[static_cast<int64_t>(s) * n + t] = tot;       // R[s][t]
     }
 }
 

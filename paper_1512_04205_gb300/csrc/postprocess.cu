@@ -42,35 +42,52 @@ __global__ void __launch_bounds__(kMedianThreads) median3x3_kernel(const uint32_
     for (uint32_t b = W - 1u - x0; b < 32u; b += W) right |= 1u << b;
 
     // Frame-independent part: row dy's window starts one pixel left of
-    // p0 + (dy - 1) W, i.e. at bit s of word wq; the three words wq .. wq+2
-    // cover it.  keep[][] is 0 for a word outside the frame, the tail mask
-    // for the last word, all ones otherwise.
+    // p0 + (dy - 1) W, i.e. at bit sh[dy] of word wq[dy]; the three words
+    // wq .. wq+2 cover it.
     int64_t wq[3];
-    uint32_t sh[3], keep[3][3];
+    uint32_t sh[3];
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy) {
         const int64_t q = static_cast<int64_t>(p0) + static_cast<int64_t>(dy - 1) * W - 1;
         wq[dy] = q >> 5;   // floor for negative q too
         sh[dy] = static_cast<uint32_t>(q) & 31u;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int64_t x = wq[dy] + c;
-            keep[dy][c] = (x < 0 || x >= nw) ? 0u : (x == nw - 1 ? tail : 0xffffffffu);
-        }
     }
+    const uint32_t rmask = (w == nw - 1) ? tail : 0xffffffffu;
+    const int f0 = static_cast<int>(blockIdx.y) * kMedianFrames;
+    const int nf = min(kMedianFrames, n - f0);
 
     // all frames' words are loaded before any is used, so each thread keeps
-    // 9 x kMedianFrames loads in flight
-    const int f0 = static_cast<int>(blockIdx.y) * kMedianFrames;
+    // 9 x kMedianFrames loads in flight.  Almost every thread reads nine
+    // words inside the frame, none of them the last: plain loads.  The rest
+    // zero the words outside the frame and mask the last word's spare bits.
     uint32_t win[kMedianFrames][3][3];
+    if (wq[0] >= 0 && wq[2] + 2 < nw - 1) {
 #pragma unroll
-    for (int i = 0; i < kMedianFrames; ++i) {
-        const int f = min(f0 + i, n - 1);   // a frame past n repeats the last one; its result is not stored
-        const uint32_t* fr = in + static_cast<int64_t>(f) * nw;
+        for (int i = 0; i < kMedianFrames; ++i) {
+            const uint32_t* fr = in + static_cast<int64_t>(f0 + min(i, nf - 1)) * nw;
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) win[i][dy][c] = __ldg(fr + wq[dy] + c);
+        }
+    } else {
+        uint32_t keep[3][3];
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) win[i][dy][c] = keep[dy][c] ? (__ldg(fr + wq[dy] + c) & keep[dy][c]) : 0u;
+            for (int c = 0; c < 3; ++c) {
+                const int64_t x = wq[dy] + c;
+                keep[dy][c] = (x < 0 || x >= nw) ? 0u : (x == nw - 1 ? tail : 0xffffffffu);
+            }
+#pragma unroll
+        for (int i = 0; i < kMedianFrames; ++i) {
+            const uint32_t* fr = in + static_cast<int64_t>(f0 + min(i, nf - 1)) * nw;
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    win[i][dy][c] = keep[dy][c] ? (__ldg(fr + wq[dy] + c) & keep[dy][c]) : 0u;
+        }
     }
 #pragma unroll
     for (int i = 0; i < kMedianFrames; ++i) {
@@ -94,9 +111,7 @@ __global__ void __launch_bounds__(kMedianThreads) median3x3_kernel(const uint32_
         // twos = C + t1 + 2 t2; count >= 5 iff twos >= 3, or twos >= 2 and S
         const uint32_t ge3 = t2 & (C | t1);
         const uint32_t ge2 = t2 | (C & t1);
-        uint32_t r = ge3 | (ge2 & S);
-        if (w == nw - 1) r &= tail;
-        if (f0 + i < n) out[static_cast<int64_t>(f0 + i) * nw + w] = r;
+        if (i < nf) out[static_cast<int64_t>(f0 + i) * nw + w] = (ge3 | (ge2 & S)) & rmask;
     }
 }
 
