@@ -23,6 +23,8 @@ amplitudes.  The video D is m x n (column t = frame t).
   mask        M_jt = 1  iff  |x_jt - bg_jt| > tau                       Eq. (thres)
   F-measure   harmonic mean of precision and recall            Section 4 (Results)
   post-pass   3 x 3 median filter of each mask frame, zero padding    Section 4 (BMC figure, Discussion)
+  rank        optional: r from the optimal hard threshold on the singular values
+              of Y (Remark 2)
   exact DMD   the same steps on X itself (no C; Section 2.1), the comparator of
               Section 4 (Computational Performance)
 
@@ -345,6 +347,41 @@ def decompose(DY, r, K):
     sel, beta = omp(PhiY, DY[:, 0], K, lam)
     return dict(U=U, sigma=s, V=V, Atilde=Atil, lam=lam, W=W, G=G, PhiY=PhiY,
                 sel=sel, beta=beta)
+
+
+def gd_omega(beta):
+    """Coefficient of the optimal hard threshold for singular values when the
+    noise level is unknown (Gavish and Donoho, the work cited in Remark 2): the
+    cubic approximation they publish, within about 0.02 of the exact value."""
+    return 0.56 * beta ** 3 - 0.95 * beta ** 2 + 1.82 * beta + 1.43
+
+
+def gd_rank(s, shape, r_max):
+    """Target rank by the optimal hard threshold (Remark 2, Section 4's
+    evaluation settings): with beta = min(shape) / max(shape) and y_med the
+    median of the min(shape) singular values s of the matrix, keep the
+    singular values above tau = gd_omega(beta) * y_med.  Returns (r, tau) with
+    r clamped to [1, r_max]."""
+    q = min(shape)
+    s = np.sort(np.asarray(s, dtype=np.float64))[::-1][:q]
+    beta = q / max(shape)
+    tau = gd_omega(beta) * float(np.median(s))
+    r = int(np.sum(s > tau))
+    return max(1, min(r, r_max)), tau
+
+
+def decompose_auto(DY, r_max, K):
+    """Steps (4)-(9) with the target rank chosen by gd_rank on the singular
+    values of Y = DY[:, 0:n-1] (Remark 2: the threshold combined with step 4);
+    K is capped at that rank."""
+    DY = np.asarray(DY, dtype=np.float64)
+    Y = DY[:, :-1]
+    _, sv, _, _ = jacobi_svd(Y)
+    r, tau = gd_rank(sv, Y.shape, r_max)
+    out = decompose(DY, r, min(K, r))
+    out["rank"] = r
+    out["rank_tau"] = tau
+    return out
 
 
 def lift(D, G):
