@@ -545,6 +545,27 @@ def run_ours(args, rank, world, local_rank):
         passes = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs]).mean(axis=0)
         return dict(total_ms=max_over_ranks(total_ms, dist, dev), passes=passes, mask=C.unpack_mask(emask, m))
 
+    def auto_rank_measure():
+        """The rank the optimal hard threshold picks on this clip's sketch
+        (Remark 2) and the time of the decomposition that picks it (one call,
+        including its host synchronisation), beside the fixed-rank one."""
+        L = lanes[0]
+        with torch.cuda.stream(main_stream):
+            C.cdmd_sketch(ctx, D, k, w["c_seed"], prec=args.prec, DY=L.DY[0])
+            times = []
+            for i in range(4):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(main_stream)
+                _, r_auto, tau = C.cdmd_decompose_auto(ctx, L.DY[0], min(32, k, n - 1), K, selector="omp")
+                e1.record(main_stream)
+                torch.cuda.synchronize()
+                if i:
+                    times.append(e0.elapsed_time(e1))
+        C.cdmd_status_sync(ctx)
+        return {"rank": r_auto, "tau": tau, "r_max": min(32, k, n - 1), "decompose_auto_ms": float(np.median(times)),
+                "note": "rank chosen on the device from the sketch of the benchmark clip; the headline keeps r = "
+                        f"{r} as its workload fixes"}
+
     # the headline form and the plain FP32 + OMP form it is compared with
     forms = {"head": (args.prec, args.selector)}
     if not args.no_plain and (args.prec, args.selector) != ("fp32", "omp"):
@@ -622,6 +643,7 @@ def run_ours(args, rank, world, local_rank):
         step(args.prec, args.selector)   # the head form's mask, whatever form ran last
     results["median"] = median_postpass()
     exact = exact_comparator(args.prec, args.steps, args.warmup) if not args.no_exact else None
+    rank_line = auto_rank_measure()
 
     batch_line = run_batch_measure(C, SEL, torch, dev, args, model) if args.batch else None
 
@@ -722,6 +744,7 @@ def run_ours(args, rank, world, local_rank):
             "fmeasure_vs_truth": fmeasure(exact["mask"], truth),
             "form": ("snapshot Gram D^T D on tcgen05 (uint8 exact in FP16, FP32 accumulation, FP64 reduce); "
                      f"FP64 small solves from the Gram; OMP; {args.prec} lift; one clip per step, one stream")}
+    line["auto_rank"] = rank_line
     if batch_line is not None:
         line["batch"] = batch_line
     if not args.no_cpu:

@@ -270,6 +270,24 @@ cdmd_status cdmd_decompose_gram(cdmd_ctx* ctx, const double* R, int n, int r, in
                                 double* G, double* beta, int32_t* sel, int32_t* nsel,
                                 void* stream);
 
+/* cdmd_decompose with the target rank chosen on the device by the optimal
+ * hard threshold for singular values (Remark 2; Gavish and Donoho, unknown
+ * noise level; Section 4 uses it for every batch): with q = min(k, n-1),
+ * beta = q / max(k, n-1) and y_med the median of the q largest singular
+ * values of Y, tau = omega(beta) y_med with
+ *   omega(beta) = 0.56 beta^3 - 0.95 beta^2 + 1.82 beta + 1.43,
+ * and r = #{sigma_i > tau} clamped to [1, r_max].  K is capped at r.
+ * Outputs are sized as for cdmd_decompose with r = r_max; the first r
+ * entries (columns) are written and sel holds -1 past the capped K.
+ * *r_out (host) receives r, *tau_out (host, may be NULL) tau.  Unlike the
+ * other calls this one synchronises `stream` once (after the tridiagonal
+ * reduction), because the launches that follow are sized by r; it is not
+ * graph-capturable.  Requires 1 <= r_max <= min(32, k, n-1), 1 <= K <= r_max. */
+cdmd_status cdmd_decompose_auto(cdmd_ctx* ctx, const double* DY, int k, int n, int r_max, int K,
+                                cdmd_selector selector, double* sigma, double* lambda,
+                                double* G, double* PhiY, double* beta, int32_t* sel,
+                                int32_t* nsel, int* r_out, double* tau_out, void* stream);
+
 /* ---- pass (b): mode lift  Phi = X' G  (Algorithm 1 step 8, Eq. cDMDModes) */
 
 /* Phi[j*ncols + c] = sum_{t=0}^{n-2} D[(t+1)*ldd + j] * G[:, cols[c]] for the
@@ -313,7 +331,9 @@ cdmd_status cdmd_median3x3(cdmd_ctx* ctx, const uint32_t* mask, int64_t W, int64
 
 typedef struct {
     int32_t k;              /* sketch rows                                  */
-    int32_t r;              /* target rank                                  */
+    int32_t r;              /* target rank; 0 = automatic (cdmd_decompose_auto,
+                               at most min(32, k, n-1); cdmd_run and
+                               cdmd_run_shared then synchronise once per clip) */
     int32_t K;              /* modes kept by the selection                  */
     cdmd_ctype ctype;       /* GAUSSIAN or RADEMACHER (dense, in-kernel)    */
     uint64_t seed;

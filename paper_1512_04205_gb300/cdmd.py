@@ -40,7 +40,7 @@ EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_strin
             "cdmd_batch_run", "cdmd_batch_status_sync", "cdmd_batch_views", "cdmd_batch_tuning",
             "cdmd_batch_destroy", "cdmd_copy", "cdmd_sketch_shared", "cdmd_run_shared", "cdmd_run_host_shared",
             "cdmd_selftest_wait", "cdmd_median3x3", "cdmd_snapshot_gram", "cdmd_decompose_gram",
-            "cdmd_run_exact"]
+            "cdmd_run_exact", "cdmd_decompose_auto"]
 BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_GROUPED = 1, 2, 4
 
 
@@ -114,6 +114,8 @@ def load_library(path=LIB_PATH):
         "cdmd_snapshot_gram": [vp, vp, i64, ctypes.c_int, i64, vp, vp],
         "cdmd_decompose_gram": [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [vp] * 7,
         "cdmd_run_exact": [vp, vp, i64, ctypes.c_int, i64, ctypes.POINTER(cdmd_params), vp, vp],
+        "cdmd_decompose_auto": [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                               + [vp] * 7 + [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp],
         "cdmd_run_host_shared": [vp, ctypes.c_int, vp, i64, vp, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_workspace_views": [vp] + [ctypes.POINTER(vp)] * 8,
         "cdmd_sketch_noalloc": [vp, i64, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, u64, vp, vp],
@@ -330,6 +332,22 @@ def cdmd_decompose(ctx, DY, r, K, selector="omp", with_phiy=False, stream=None, 
                                   _ptr(out["sigma"]), _ptr(out["lam"]), _ptr(out["G"]), _ptr(out["PhiY"]),
                                   _ptr(out["beta"]), _ptr(out["sel"]), _ptr(out["nsel"]), _stream(stream)))
     return out
+
+
+def cdmd_decompose_auto(ctx, DY, r_max, K, selector="omp", with_phiy=False, stream=None, out=None):
+    """cdmd_decompose with the rank from the optimal hard threshold (at most
+    r_max); synchronises the stream once.  Returns (outputs, r, tau); the
+    outputs are sized for r_max and their first r entries are valid."""
+    n, k = DY.shape
+    if out is None:
+        out = decompose_outputs(n, k, r_max, K, DY.device, with_phiy=with_phiy)
+    r = ctypes.c_int(0)
+    tau = ctypes.c_double(0.0)
+    _check(ctx.lib.cdmd_decompose_auto(ctx.handle, _ptr(DY), int(k), int(n), int(r_max), int(K), SELECTORS[selector],
+                                       _ptr(out["sigma"]), _ptr(out["lam"]), _ptr(out["G"]), _ptr(out["PhiY"]),
+                                       _ptr(out["beta"]), _ptr(out["sel"]), _ptr(out["nsel"]), ctypes.byref(r),
+                                       ctypes.byref(tau), _stream(stream)))
+    return out, r.value, tau.value
 
 
 def cdmd_snapshot_gram(ctx, D, R=None, stream=None):

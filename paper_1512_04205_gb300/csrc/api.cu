@@ -1,4 +1,5 @@
 // extern "C" entry points of libcdmd: argument checks, workspace, dispatch.
+#include <algorithm>
 #include <cstdarg>
 #include <cstring>
 #include <vector>
@@ -305,6 +306,26 @@ cdmd_status cdmd_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r,
                             static_cast<cudaStream_t>(stream));
 }
 
+cdmd_status cdmd_decompose_auto(cdmd_ctx* ctx, const double* DY, int k, int n, int r_max, int K,
+                                cdmd_selector selector, double* sigma, double* lambda, double* G, double* PhiY,
+                                double* beta, int32_t* sel, int32_t* nsel, int* r_out, double* tau_out, void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(DY && sigma && lambda && G && beta && sel && nsel && r_out, "a required pointer is NULL");
+    CDMD_REQUIRE(n >= 2 && n <= 512, "n must be in [2, 512] (got %d)", n);
+    CDMD_REQUIRE(k >= 1, "k must be >= 1");
+    CDMD_REQUIRE(r_max >= 1 && r_max <= 32 && r_max <= k && r_max <= n - 1,
+                 "r_max must be in [1, min(32, k, n-1)] (got %d)", r_max);
+    CDMD_REQUIRE(K >= 1 && K <= r_max, "K must be in [1, r_max] (got %d)", K);
+    CDMD_REQUIRE(selector == CDMD_SEL_OMP || selector == CDMD_SEL_LSTSQ || selector == CDMD_SEL_MLP,
+                 "unknown selector %d", static_cast<int>(selector));
+    CDMD_REQUIRE(selector != CDMD_SEL_MLP || ctx->selector_loaded,
+                 "CDMD_SEL_MLP needs a model (cdmd_selector_load)");
+    DeviceGuard g(ctx->device);
+    return launch_decompose_auto(ctx, DY, k, n, r_max, K, selector, sigma, lambda, G, PhiY, beta, sel, nsel, r_out,
+                                 tau_out, static_cast<cudaStream_t>(stream));
+}
+
 cdmd_status cdmd_snapshot_gram(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, double* R,
                                void* stream) {
     clear_error();
@@ -397,8 +418,11 @@ cdmd_status check_run(const uint8_t* D, int64_t m, int n, int64_t ldd, const cdm
     cdmd_status st = check_video(D, m, n, ldd);
     if (st != CDMD_OK) return st;
     const int k = p->k, r = p->r, K = p->K;
-    CDMD_REQUIRE(r >= 1 && r <= 32 && r <= k && r <= n - 1, "r must be in [1, min(32, k, n-1)]");
-    CDMD_REQUIRE(K >= 1 && K <= r, "K must be in [1, r]");
+    CDMD_REQUIRE(k >= 1, "k must be >= 1");
+    CDMD_REQUIRE(r == 0 || (r >= 1 && r <= 32 && r <= k && r <= n - 1),
+                 "r must be 0 (automatic) or in [1, min(32, k, n-1)]");
+    const int r_bound = r == 0 ? std::min(32, std::min(k, n - 1)) : r;
+    CDMD_REQUIRE(K >= 1 && K <= r_bound, "K must be in [1, r] (r = 0: [1, min(32, k, n-1)])");
     return CDMD_OK;
 }
 
@@ -407,9 +431,13 @@ cdmd_status check_run(const uint8_t* D, int64_t m, int n, int64_t ldd, const cdm
 // Phi buffers are reused, stream-ordered).
 cdmd_status run_from(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const cdmd_params* p,
                      double* DY, const double* R, uint32_t* mask, void* stream) {
-    const int k = p->k, r = p->r, K = p->K;
+    const int k = p->k, K = p->K;
+    // r == 0: the rank comes from the optimal hard threshold (Remark 2), at
+    // most min(32, k, n-1); buffers are sized for that bound
+    const bool auto_rank = p->r == 0;
+    int r = auto_rank ? std::min(32, std::min(k, n - 1)) : p->r;
     const int p1 = n - 1;
-    const int ncols = (p->selector == CDMD_SEL_LSTSQ) ? r : K;
+    const int ncols_max = (p->selector == CDMD_SEL_LSTSQ) ? r : K;
     void* v = nullptr;
     const size_t n_small = static_cast<size_t>(r) + 2 * r + 2 * static_cast<size_t>(p1) * r + 2 * r + 8;
     cdmd_status st = ensure_buffer(ctx, BUF_RUN_SMALL, n_small * sizeof(double) + (r + 8) * sizeof(int32_t), &v);
@@ -420,16 +448,21 @@ cdmd_status run_from(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t 
     double* beta = Gm + 2 * static_cast<size_t>(p1) * r;
     int32_t* sel = reinterpret_cast<int32_t*>(beta + 2 * r + 8);
     int32_t* nsel = sel + r + 4;
-    st = ensure_buffer(ctx, BUF_RUN_PHI, static_cast<size_t>(m) * ncols * 2 * sizeof(float), &v);
+    st = ensure_buffer(ctx, BUF_RUN_PHI, static_cast<size_t>(m) * ncols_max * 2 * sizeof(float), &v);
     if (st != CDMD_OK) return st;
     float* Phi = static_cast<float*>(v);
     ctx->run_DY = DY; ctx->run_sigma = sigma; ctx->run_lambda = lambda; ctx->run_G = Gm;
     ctx->run_beta = beta; ctx->run_sel = sel; ctx->run_nsel = nsel; ctx->run_Phi = Phi;
 
-    st = DY != nullptr
-             ? cdmd_decompose(ctx, DY, k, n, r, K, p->selector, sigma, lambda, Gm, nullptr, beta, sel, nsel, stream)
-             : cdmd_decompose_gram(ctx, R, n, r, K, p->selector, sigma, lambda, Gm, beta, sel, nsel, stream);
+    if (DY != nullptr && auto_rank)
+        st = cdmd_decompose_auto(ctx, DY, k, n, r, K, p->selector, sigma, lambda, Gm, nullptr, beta, sel, nsel, &r,
+                                 nullptr, stream);
+    else if (DY != nullptr)
+        st = cdmd_decompose(ctx, DY, k, n, r, K, p->selector, sigma, lambda, Gm, nullptr, beta, sel, nsel, stream);
+    else
+        st = cdmd_decompose_gram(ctx, R, n, r, K, p->selector, sigma, lambda, Gm, beta, sel, nsel, stream);
     if (st != CDMD_OK) return st;
+    const int ncols = (p->selector == CDMD_SEL_LSTSQ) ? r : std::min(K, r);
     // OMP: lift and subtract only the selected modes (sel, -1 padded);
     // LSTSQ: every mode carries an amplitude, so all r are used.
     const int32_t* cols = (p->selector == CDMD_SEL_LSTSQ) ? nullptr : sel;

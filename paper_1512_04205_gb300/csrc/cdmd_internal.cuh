@@ -243,6 +243,10 @@ cdmd_status launch_subtract_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n
 cdmd_status launch_selftest_wait(cdmd_ctx* ctx, uint64_t limit_ns, cudaStream_t stream);
 cdmd_status launch_gram_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, double* R,
                            cudaStream_t stream);
+cdmd_status launch_decompose_auto(cdmd_ctx* ctx, const double* DY, int k, int n, int r_max, int K,
+                                  cdmd_selector selector, double* sigma, double* lambda, double* G, double* PhiY,
+                                  double* beta, int32_t* sel, int32_t* nsel, int* r_out, double* tau_out,
+                                  cudaStream_t stream);
 cdmd_status launch_decompose_gram(cdmd_ctx* ctx, const double* R, int n, int r, int K, cdmd_selector selector,
                                   double* sigma, double* lambda, double* G, double* beta, int32_t* sel,
                                   int32_t* nsel, cudaStream_t stream);

@@ -478,6 +478,80 @@ tridiag_eigpair_kernel(const double* __restrict__ dd, const double* __restrict__
     for (int i = 0; i < p; ++i) Z[static_cast<int64_t>(w) * p + i] = z[i];
 }
 
+// ---------------------------------------------------------------------------
+// Target rank by the optimal hard threshold for singular values (Remark 2;
+// Gavish and Donoho, unknown noise level): the singular values of Y are the
+// square roots of the eigenvalues of T.  One warp finds the median of the q
+// largest by multisection on Sturm counts, sets tau = omega * median and
+// counts the eigenvalues above tau^2 with one more Sturm count.
+// ---------------------------------------------------------------------------
+__device__ double kth_eigenvalue(const double* d, const double* e2, int p, int idx, double lo, double hi, double tn,
+                                 int* status) {
+    const int lane = threadIdx.x & 31;
+    bool converged = false;
+    for (int it = 0; it < 40; ++it) {
+        const double width = hi - lo;
+        if (width <= 2.0 * kEps * fmax(fabs(lo), fabs(hi)) + kEps * tn + 1e-300) { converged = true; break; }
+        const double step = width * (1.0 / (kShifts + 1));
+        int n0, n1;
+        sturm_count2(d, e2, p, fma(step, static_cast<double>(lane + 1), lo),
+                     fma(step, static_cast<double>(lane + 33), lo), n0, n1);
+        const unsigned b0 = __ballot_sync(0xffffffffu, n0 > idx);
+        const unsigned b1 = __ballot_sync(0xffffffffu, n1 > idx);
+        const int f = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : kShifts);
+        const double nlo = (f == 0) ? lo : fma(step, static_cast<double>(f), lo);
+        const double nhi = (f == kShifts) ? hi : fma(step, static_cast<double>(f + 1), lo);
+        if (nlo >= nhi || (nlo == lo && nhi == hi)) { converged = true; break; }
+        lo = nlo;
+        hi = nhi;
+    }
+    if (!converged && lane == 0) record_status(status, CDMD_ERR_NOT_CONVERGED);
+    return 0.5 * (lo + hi);
+}
+
+__global__ void __launch_bounds__(32)
+gd_rank_kernel(const double* __restrict__ dd, const double* __restrict__ ee, int p, int q, double omega, int r_max,
+               int* r_out, double* tau_out, int* status) {
+    extern __shared__ double gsm[];
+    double* d = gsm;        // p
+    double* e2 = d + p;     // p (e2[p-1] = 0)
+    const int lane = threadIdx.x;
+    double lo = 1e300, hi = -1e300, tn = 0.0;
+    for (int i = lane; i < p; i += 32) {
+        const double e = (i + 1 < p) ? ee[i] : 0.0;
+        const double em = (i > 0) ? ee[i - 1] : 0.0;
+        d[i] = dd[i];
+        e2[i] = e * e;
+        const double rad = fabs(e) + fabs(em);
+        lo = fmin(lo, dd[i] - rad);
+        hi = fmax(hi, dd[i] + rad);
+        tn = fmax(tn, fabs(dd[i]) + rad);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    }
+    __syncwarp();
+    const double pad = 2.0 * kEps * tn + 1e-300;
+    lo -= pad;
+    hi += pad;
+    // descending positions j0 <= j1 of the median of the q largest
+    const int j0 = (q - 1) / 2, j1 = q / 2;
+    const double l0 = kth_eigenvalue(d, e2, p, p - 1 - j0, lo, hi, tn, status);
+    const double l1 = (j1 == j0) ? l0 : kth_eigenvalue(d, e2, p, p - 1 - j1, lo, hi, tn, status);
+    const double ymed = 0.5 * (sqrt(fmax(l0, 0.0)) + sqrt(fmax(l1, 0.0)));
+    const double tau = omega * ymed;
+    int below, unused;
+    sturm_count2(d, e2, p, tau * tau, tau * tau, below, unused);   // eigenvalues < tau^2
+    if (lane == 0) {
+        const int above = p - below;
+        *r_out = above < 1 ? 1 : (above > r_max ? r_max : above);
+        *tau_out = tau;
+    }
+}
+
 // 4a. Classical Gram-Schmidt over the r columns of Z (descending eigenvalue
 // order), applied twice: the dots of a column with all earlier columns are
 // taken in parallel (one warp each).  Z is not __restrict__: threads read
@@ -1523,9 +1597,15 @@ namespace {
 
 // Steps 4-7 and 9 from the Gram of the sketch DY (k x n), or, when Rin is
 // given, from that n x n Gram directly (DY and PhiY unused).
+struct AutoRank {
+    int* r_host;        // receives the chosen rank
+    double* tau_host;   // receives the threshold (may be NULL)
+};
+
 cdmd_status decompose_impl(cdmd_ctx* ctx, const double* DY, int k, const double* Rin, int n, int r, int K,
                            cdmd_selector selector, double* sigma, double* lambda, double* G, double* PhiY,
-                           double* beta, int32_t* sel, int32_t* nsel, cudaStream_t stream) {
+                           double* beta, int32_t* sel, int32_t* nsel, cudaStream_t stream,
+                           const AutoRank* autor = nullptr) {
     const int p = n - 1;
     // ---- workspace layout (doubles) ----
     const int ntiles = (n + kGT - 1) / kGT;
@@ -1538,11 +1618,14 @@ cdmd_status decompose_impl(cdmd_ctx* ctx, const double* DY, int k, const double*
     const size_t n_Z = static_cast<size_t>(p) * r;
     const size_t n_small = static_cast<size_t>(r) * r * 2;
     const size_t total = n_gram_part + n_R + n_Hv + 3 * n_vec + r + 3 * n_Z + 5 * n_small + 6 * r + 64;
-    // + one slot for the eigen-solver's fallback flag
+    // + one slot for the eigen-solver's fallback flag and two for the rank
+    // threshold's result; with an automatic rank, r is its upper bound here
     double* ws = nullptr;
-    cdmd_status st = ensure_buffer(ctx, BUF_EIG, (total + 1) * sizeof(double), reinterpret_cast<void**>(&ws));
+    cdmd_status st = ensure_buffer(ctx, BUF_EIG, (total + 3) * sizeof(double), reinterpret_cast<void**>(&ws));
     if (st != CDMD_OK) return st;
     int* eig_flag = reinterpret_cast<int*>(ws + total);   // written by eig_f32_kernel before any read
+    int* gd_r = reinterpret_cast<int*>(ws + total + 1);
+    double* gd_tau = ws + total + 2;
     double* gpart = ws;
     double* Rws = gpart + n_gram_part;
     const double* R = Rin != nullptr ? Rin : Rws;
@@ -1551,17 +1634,25 @@ cdmd_status decompose_impl(cdmd_ctx* ctx, const double* DY, int k, const double*
     double* dd = htau + n_vec;
     double* ee = dd + n_vec;
     double* lamT = ee + n_vec;
-    double* Z = lamT + r;
-    double* V = Z + n_Z;
-    double* B = V + n_Z;
-    double* At = B + n_Z;
-    double* W = At + n_small;
-    double* M = W + n_small;
-    double* WR = M + n_small;
-    double* lamR = WR + n_small;
-    double* cvec = lamR + 2 * r;
-    float* lam32 = reinterpret_cast<float*>(cvec + 2 * r);       // 2r floats
-    float* W32 = reinterpret_cast<float*>(cvec + 4 * r);         // 2r^2 floats (n_small/2 doubles)
+    // the regions below depend on r; with an automatic rank they are laid out
+    // again once the rank is known (a smaller r fits the same allocation)
+    double *Z, *V, *B, *At, *W, *M, *WR, *lamR, *cvec;
+    float *lam32, *W32;
+    auto lay_out = [&](int rr) {
+        const size_t nz = static_cast<size_t>(p) * rr, ns = static_cast<size_t>(rr) * rr * 2;
+        Z = lamT + rr;
+        V = Z + nz;
+        B = V + nz;
+        At = B + nz;
+        W = At + ns;
+        M = W + ns;
+        WR = M + ns;
+        lamR = WR + ns;
+        cvec = lamR + 2 * rr;
+        lam32 = reinterpret_cast<float*>(cvec + 2 * rr);    // 2r floats
+        W32 = reinterpret_cast<float*>(cvec + 4 * rr);      // 2r^2 floats (ns/2 doubles)
+    };
+    lay_out(r);
 
     // 1. Gram
     if (Rin == nullptr) {
@@ -1609,6 +1700,29 @@ cdmd_status decompose_impl(cdmd_ctx* ctx, const double* DY, int k, const double*
     } else {
         tiny_tridiag_kernel<<<1, 1, 0, stream>>>(R, n, p, dd, ee, htau);
         CDMD_CHECK_LAUNCH("tiny_tridiag_kernel");
+    }
+    // 2b. optional automatic rank (Remark 2): the one host synchronisation of
+    // the decomposition, since the launches below are sized by r
+    if (autor != nullptr) {
+        const int q = k < p ? k : p;
+        const double bq = static_cast<double>(q) / static_cast<double>(k > p ? k : p);
+        const double omega = ((0.56 * bq - 0.95) * bq + 1.82) * bq + 1.43;
+        gd_rank_kernel<<<1, 32, 2 * static_cast<size_t>(p) * sizeof(double), stream>>>(dd, ee, p, q, omega, r, gd_r,
+                                                                                         gd_tau, ctx->d_status);
+        CDMD_CHECK_LAUNCH("gd_rank_kernel");
+        int hr = 0;
+        double ht = 0.0;
+        CDMD_CHECK_CUDA(cudaMemcpyAsync(&hr, gd_r, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CDMD_CHECK_CUDA(cudaMemcpyAsync(&ht, gd_tau, sizeof(double), cudaMemcpyDeviceToHost, stream));
+        CDMD_CHECK_CUDA(cudaStreamSynchronize(stream));
+        if (hr < 1 || hr > r) return fail(CDMD_ERR_CUDA, "rank threshold returned %d (bound %d)", hr, r);
+        // picks past the capped K read as "no mode"
+        CDMD_CHECK_CUDA(cudaMemsetAsync(sel, 0xff, static_cast<size_t>(K) * sizeof(int32_t), stream));
+        r = hr;
+        if (K > r) K = r;
+        *autor->r_host = r;
+        if (autor->tau_host != nullptr) *autor->tau_host = ht;
+        lay_out(r);
     }
     // 3. eigenpairs of T, orthonormalisation, back-transform
     {
@@ -1678,6 +1792,15 @@ cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int 
                              double* PhiY, double* beta, int32_t* sel, int32_t* nsel,
                              cudaStream_t stream) {
     return decompose_impl(ctx, DY, k, nullptr, n, r, K, selector, sigma, lambda, G, PhiY, beta, sel, nsel, stream);
+}
+
+cdmd_status launch_decompose_auto(cdmd_ctx* ctx, const double* DY, int k, int n, int r_max, int K,
+                                  cdmd_selector selector, double* sigma, double* lambda, double* G, double* PhiY,
+                                  double* beta, int32_t* sel, int32_t* nsel, int* r_out, double* tau_out,
+                                  cudaStream_t stream) {
+    const AutoRank a{r_out, tau_out};
+    return decompose_impl(ctx, DY, k, nullptr, n, r_max, K, selector, sigma, lambda, G, PhiY, beta, sel, nsel, stream,
+                          &a);
 }
 
 cdmd_status launch_decompose_gram(cdmd_ctx* ctx, const double* R, int n, int r, int K, cdmd_selector selector,
