@@ -349,6 +349,98 @@ def run_batch_measure(C, SEL, torch, dev, args, model):
 
 
 # ----------------------------------------------------------------------------
+# Measurement-matrix study (Section 4: fps and F-measure against the number of
+# samples p for Gaussian, sparse and single-pixel C on a 720x480x200 video;
+# bootstrap confidence intervals of F over random draws of C)
+# ----------------------------------------------------------------------------
+
+STUDY = dict(width=720, height=480, n=200, p=[25, 50, 100, 200, 400, 700, 1000], seeds=12, K=10, tau=25.0,
+             clip_seed=31, boot=4000)
+
+
+def bootstrap_ci(values, rng, boot):
+    """Percentile bootstrap 95 % interval of the mean."""
+    v = np.asarray(values, dtype=np.float64)
+    means = v[rng.integers(0, len(v), size=(boot, len(v)))].mean(axis=1)
+    return [float(np.percentile(means, 2.5)), float(np.percentile(means, 97.5))]
+
+
+def run_study(args):
+    """One JSON line: per measurement type and p, the time of sketch +
+    decompose + lift (the foreground mask excluded, as in the paper's study),
+    the F-measure of the mask against the generator's truth, and its
+    bootstrap interval over independent draws of C.  The rank is automatic
+    (optimal hard threshold, at most min(32, p, n-1)) and K = 10 modes are
+    selected by OMP, as in the paper's evaluation settings."""
+    import torch
+
+    import videogen
+    from paper_1512_04205_gb300 import build
+    from paper_1512_04205_gb300 import cdmd as C
+
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    S = STUDY
+    clip = videogen.make_clip(S["width"], S["height"], S["n"], seed=S["clip_seed"], drift=0.1)
+    m, n = clip.m, clip.n
+    truth = clip.truth.T
+    D = torch.from_numpy(clip.frames).to(dev)
+    ctx = C.Context(0)
+    stream = torch.cuda.current_stream()
+    density = float(np.log(m) / m)      # sparsity factor s = m / log(m) (Section 4, evaluation settings)
+    rng = np.random.default_rng(7)
+    rows = []
+    for ctype in ("gaussian", "sparse", "rowsample"):
+        for p in S["p"]:
+            r_max = min(32, p, n - 1)
+            times, fs, ranks, build_ms = [], [], [], []
+            for sd in range(S["seeds"] + 1):       # the first draw warms up and is not kept
+                seed = 1000 * sd + p
+                meas = None
+                if ctype != "gaussian":
+                    t0 = time.perf_counter()
+                    meas = C.Measure(ctx, ctype, m, p, seed, density=density if ctype == "sparse" else 0.0)
+                    torch.cuda.synchronize()
+                    bms = (time.perf_counter() - t0) * 1e3
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if meas is None:
+                    DY = C.cdmd_sketch(ctx, D, p, seed, prec=args.prec)
+                else:
+                    DY = C.cdmd_sketch_gather(ctx, D, meas)
+                dec, r, _ = C.cdmd_decompose_auto(ctx, DY, r_max, min(S["K"], r_max), selector="omp")
+                Kc = min(S["K"], r)
+                Phi = C.cdmd_lift(ctx, D, dec["G"][:r], cols=dec["sel"], ncols=Kc, prec=args.prec)
+                e1.record(stream)
+                mask = C.cdmd_subtract(ctx, D, Phi, dec["beta"][:r], dec["lam"][:r], S["tau"], cols=dec["sel"])
+                C.cdmd_status_sync(ctx)
+                if sd == 0:
+                    continue
+                times.append(e0.elapsed_time(e1))
+                fs.append(fmeasure(C.unpack_mask(mask, m), truth))
+                ranks.append(r)
+                if meas is not None:
+                    build_ms.append(bms)
+            ms = float(np.median(times))
+            rows.append({"ctype": ctype, "p": p, "ms": ms, "fps": n / (ms * 1e-3),
+                         "F_mean": float(np.mean(fs)), "F_ci95": bootstrap_ci(fs, rng, S["boot"]),
+                         "F_min": float(np.min(fs)), "F_max": float(np.max(fs)),
+                         "rank_median": float(np.median(ranks)),
+                         "build_ms": float(np.median(build_ms)) if build_ms else None})
+    line = {"study": "measurement matrices (Gaussian, sparse, single pixel) against the number of samples p",
+            "workload": f"synthetic {S['width']}x{S['height']}x{S['n']}, seed {S['clip_seed']}",
+            "timing": ("CUDA events around sketch + decompose + lift (mask excluded), median over "
+                       f"{S['seeds']} draws of C after one warm-up draw; the Gaussian C is drawn in the sketch "
+                       "kernel, sparse and single-pixel C are built on the device beforehand (build_ms, host "
+                       "timed, not in ms)"),
+            "sparse_density": density, "precision": args.prec, "selector": "omp", "rank": "automatic",
+            "K": S["K"], "tau": S["tau"], "draws_of_C": S["seeds"], "bootstrap": S["boot"], "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
 # GPU path
 # ----------------------------------------------------------------------------
 
@@ -791,6 +883,9 @@ def main():
     ap.add_argument("--sm-limit", type=int, default=136,
                     help="SMs the full-data passes of each in-flight clip may fill (0 = all)")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-DMD comparator")
+    ap.add_argument("--study", action="store_true",
+                    help="run the measurement-matrix study (p sweep of Gaussian, sparse and single-pixel C on "
+                         "720x480x200, F-measure with bootstrap intervals) instead of the benchmark")
     args = ap.parse_args()
     if args.size:
         wd, ht = (int(v) for v in args.size.lower().split("x"))
@@ -802,6 +897,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.study:
+        return run_study(args)
     return run_ours(args, rank, world, local_rank)
 
 
