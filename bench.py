@@ -403,27 +403,31 @@ def run_study(args):
                     meas = C.Measure(ctx, ctype, m, p, seed, density=density if ctype == "sparse" else 0.0)
                     torch.cuda.synchronize()
                     bms = (time.perf_counter() - t0) * 1e3
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                ev[0].record(stream)
                 if meas is None:
                     DY = C.cdmd_sketch(ctx, D, p, seed, prec=args.prec)
                 else:
                     DY = C.cdmd_sketch_gather(ctx, D, meas)
+                ev[1].record(stream)
                 dec, r, _ = C.cdmd_decompose_auto(ctx, DY, r_max, min(S["K"], r_max), selector="omp")
+                ev[2].record(stream)
                 Kc = min(S["K"], r)
                 Phi = C.cdmd_lift(ctx, D, dec["G"][:r], cols=dec["sel"], ncols=Kc, prec=args.prec)
-                e1.record(stream)
+                ev[3].record(stream)
                 mask = C.cdmd_subtract(ctx, D, Phi, dec["beta"][:r], dec["lam"][:r], S["tau"], cols=dec["sel"])
                 C.cdmd_status_sync(ctx)
                 if sd == 0:
                     continue
-                times.append(e0.elapsed_time(e1))
+                times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
                 fs.append(fmeasure(C.unpack_mask(mask, m), truth))
                 ranks.append(r)
                 if meas is not None:
                     build_ms.append(bms)
-            ms = float(np.median(times))
+            per = np.median(np.array(times), axis=0)
+            ms = float(np.median(np.array(times).sum(axis=1)))
             rows.append({"ctype": ctype, "p": p, "ms": ms, "fps": n / (ms * 1e-3),
+                         "sketch_ms": float(per[0]), "decompose_ms": float(per[1]), "lift_ms": float(per[2]),
                          "F_mean": float(np.mean(fs)), "F_ci95": bootstrap_ci(fs, rng, S["boot"]),
                          "F_min": float(np.min(fs)), "F_max": float(np.max(fs)),
                          "rank_median": float(np.median(ranks)),
@@ -652,7 +656,7 @@ def run_ours(args, rank, world, local_rank):
                 e1.record(main_stream)
                 torch.cuda.synchronize()
                 if i:
-                    times.append(e0.elapsed_time(e1))
+                    times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
         C.cdmd_status_sync(ctx)
         return {"rank": r_auto, "tau": tau, "r_max": min(32, k, n - 1), "decompose_auto_ms": float(np.median(times)),
                 "note": "rank chosen on the device from the sketch of the benchmark clip; the headline keeps r = "
