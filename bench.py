@@ -656,7 +656,7 @@ def run_ours(args, rank, world, local_rank):
                 e1.record(main_stream)
                 torch.cuda.synchronize()
                 if i:
-                    times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
+                    times.append(e0.elapsed_time(e1))
         C.cdmd_status_sync(ctx)
         return {"rank": r_auto, "tau": tau, "r_max": min(32, k, n - 1), "decompose_auto_ms": float(np.median(times)),
                 "note": "rank chosen on the device from the sketch of the benchmark clip; the headline keeps r = "
