@@ -662,6 +662,30 @@ def run_ours(args, rank, world, local_rank):
                 "note": "rank chosen on the device from the sketch of the benchmark clip; the headline keeps r = "
                         f"{r} as its workload fixes"}
 
+    def rademacher_measure():
+        """The step's sketch with Rademacher C instead of Gaussian: +-1 is
+        exact in BF16, so one tensor product instead of hi + lo, and one Philox
+        counter gives a pixel's 128 rows.  Timed over the same clips, per clip,
+        against the tensor peak (2 k m n flop per clip)."""
+        L = lanes[0]
+        evs = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        with torch.cuda.stream(main_stream):
+            for _ in range(2):
+                C.cdmd_sketch_shared(ctx, Ds, k, w["c_seed"], ctype="rademacher", prec=args.prec, DYs=L.DY)
+            evs[0].record(main_stream)
+            for _ in range(args.steps):
+                C.cdmd_sketch_shared(ctx, Ds, k, w["c_seed"], ctype="rademacher", prec=args.prec, DYs=L.DY)
+            evs[1].record(main_stream)
+        torch.cuda.synchronize()
+        C.cdmd_status_sync(ctx)
+        ms = evs[0].elapsed_time(evs[1]) / (args.steps * cps)
+        tf = 2.0 * k * m * n / (ms * 1e-3) / 1e12
+        peak = float(load_peaks()[0].get("bf16_tflops_sustained", load_peaks()[0]["bf16_tflops"]))
+        return {"sketch_ms_per_clip": ms, "tflops": tf, "frac": tf / peak, "peak_tflops": peak,
+                "bytes_gbs": m * n / (ms * 1e-3) / 1e9,
+                "form": (f"{cps} clips under one Rademacher C, packed 512 frames to a launch; time per clip "
+                         "includes the widen passes and the reduces; one BF16 product (C exact)")}
+
     # the headline form and the plain FP32 + OMP form it is compared with
     forms = {"head": (args.prec, args.selector)}
     if not args.no_plain and (args.prec, args.selector) != ("fp32", "omp"):
@@ -740,6 +764,7 @@ def run_ours(args, rank, world, local_rank):
     results["median"] = median_postpass()
     exact = exact_comparator(args.prec, args.steps, args.warmup) if not args.no_exact else None
     rank_line = auto_rank_measure()
+    rad_line = rademacher_measure() if args.prec == "bf16x2" else None
 
     batch_line = run_batch_measure(C, SEL, torch, dev, args, model) if args.batch else None
 
@@ -841,6 +866,8 @@ def run_ours(args, rank, world, local_rank):
             "form": ("snapshot Gram D^T D on tcgen05 (uint8 exact in FP16, FP32 accumulation, FP64 reduce); "
                      f"FP64 small solves from the Gram; OMP; {args.prec} lift; one clip per step, one stream")}
     line["auto_rank"] = rank_line
+    if rad_line is not None:
+        line["rademacher_sketch"] = rad_line
     if batch_line is not None:
         line["batch"] = batch_line
     if not args.no_cpu:

@@ -255,8 +255,7 @@ cdmd_status cdmd_sketch_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* 
                  "cdmd_sketch_shared generates GAUSSIAN or RADEMACHER C");
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (prec == CDMD_PREC_BF16X2 && ctype == CDMD_C_GAUSSIAN)
-        return launch_sketch_tc_shared(ctx, nclips, D, m, n, ldd, k, seed, DY, s);
+    if (prec == CDMD_PREC_BF16X2) return launch_sketch_tc_shared(ctx, nclips, D, m, n, ldd, ctype, k, seed, DY, s);
     if (prec != CDMD_PREC_FP32 && prec != CDMD_PREC_BF16X2)
         return fail(CDMD_ERR_INVALID_ARG, "unknown precision %d", static_cast<int>(prec));
     for (int i = 0; i < nclips; ++i) {

@@ -231,7 +231,8 @@ cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, 
 // Several clips of the same pixel count sketched with one C (same k, seed):
 // consecutive clips share the generator two at a time where they fit.
 cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
-                                    const int64_t* ldd, int k, uint64_t seed, double* const* DY, cudaStream_t stream);
+                                    const int64_t* ldd, cdmd_ctype ctype, int k, uint64_t seed, double* const* DY,
+                                    cudaStream_t stream);
 // Pass (c) on the tensor cores for mask-only MODULUS / REAL calls with
 // 32 <= n <= 256 frames, ncols <= 16 and a 16-byte aligned video; lam_t and
 // amp are the lambda^t table [n][nc_pad] and the amplitudes (float2 each).

@@ -226,12 +226,48 @@ __device__ __forceinline__ void draw_c_tiles(uint8_t* a_stage, int gt, int mtile
     }
 }
 
+// One 128-row Rademacher tile of C (rows row0 .. row0 + 127, row0 a multiple
+// of 128; pixels j0 .. j0 + 63) as BF16 +1 / -1 in the 128-byte swizzled
+// K-major layout.  Entry (i, j) is bit (i % 128) % 32 of word (i % 128) / 32
+// of the Philox counter (j, i / 128, 1, 0): clear = +1, set = -1.  One counter
+// gives all 128 rows of a pixel, so generator warp gw (0 .. 7) covers the rows
+// of one word, 32 (gw & 3) .. +31, and 32 pixels, 32 (gw >> 2) .. +31: each
+// lane draws one pixel's counter and the warp passes the word round by
+// shuffles, lane l keeping bit l (its row).  Rows past k and pixels past m
+// are zero.  +1 and -1 are exact in BF16, so C needs no lo part.
+__device__ __forceinline__ void draw_rademacher_tile(uint8_t* a_tile, int gw, int lane, int row0, int k, int64_t j0,
+                                                     int64_t m, const PhiloxKeys& rk) {
+    const int wi = gw & 3;
+    const int64_t jb = j0 + 32 * (gw >> 2);
+    const uint4 w = philox4x32_10(
+        make_uint4(static_cast<uint32_t>(jb + lane), static_cast<uint32_t>(row0 >> 7), 1u, 0u), rk);
+    const uint32_t word = wi == 0 ? w.x : wi == 1 ? w.y : wi == 2 ? w.z : w.w;
+    const uint32_t row = static_cast<uint32_t>(32 * wi + lane);
+    const bool row_ok = row0 + static_cast<int>(row) < k;
+#pragma unroll
+    for (int gg = 0; gg < 4; ++gg) {
+        uint32_t out[4];
+#pragma unroll
+        for (int p2 = 0; p2 < 4; ++p2) {
+            const int src = gg * 8 + 2 * p2;
+            const uint32_t b0 = (__shfl_sync(0xffffffffu, word, src) >> lane) & 1u;
+            const uint32_t b1 = (__shfl_sync(0xffffffffu, word, src + 1) >> lane) & 1u;
+            const uint32_t e0 = (row_ok && jb + src < m) ? (0x3F80u | (b0 << 15)) : 0u;
+            const uint32_t e1 = (row_ok && jb + src + 1 < m) ? (0x3F80u | (b1 << 15)) : 0u;
+            out[p2] = e0 | (e1 << 16);
+        }
+        const uint32_t chunk = static_cast<uint32_t>(4 * (gw >> 2) + gg);   // 8 pixels per 16-byte chunk
+        *reinterpret_cast<uint4*>(a_tile + tc::sw128_offset(row, chunk)) = make_uint4(out[0], out[1], out[2], out[3]);
+    }
+}
+
 // One CTA's share of C D: the rows of C in row block U.rowblk (128 mtiles
 // rows) over the 64-pixel K steps step0 .. step0+nsteps-1, against each of
 // U.nclips clips, written to U.part[g][t * k + row] (this split's partial
 // sums).  Used by the per-clip and the grouped launch.
 // U.tmap[g] maps the uint8 frames; the bytes are staged and converted to BF16
 // by warps 2-11.
+template <bool kRad>
 __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status, uint8_t* smem) {
     const int nclips = U.nclips, mtiles = U.mtiles, k = U.k;
     const int n0 = U.n[0], n1 = nclips > 1 ? U.n[1] : 0;
@@ -325,7 +361,7 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
                         for (int kk = 0; kk < 4; ++kk) {
                             const uint64_t bdesc = tc::desc_sw128(b_base + (g ? L.b_clip[1] : 0u) + kk * 32);
 #pragma unroll
-                            for (int hl = 0; hl < 2; ++hl) {
+                            for (int hl = 0; hl < (kRad ? 1 : 2); ++hl) {
                                 const uint64_t adesc = tc::desc_sw128(a_base + (mt * 2 + hl) * kTileBytes + kk * 32);
                                 tc::mma_bf16(acc, adesc, bdesc, g ? idesc1 : idesc0, (ks | kk | hl) ? 1u : 0u);
                             }
@@ -349,7 +385,13 @@ __device__ __forceinline__ void sketch_tc_body(const SketchItem& U, int* status,
             const uint32_t u = static_cast<uint32_t>(ks / kStages);
             if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
             if (gen) {
-                draw_c_tiles(A + s * L.a_stage, gt, mtiles, row0, k, (U.step0 + ks) * kKStep, U.m, rk);
+                if constexpr (kRad) {
+                    for (int mt = 0; mt < mtiles; ++mt)
+                        draw_rademacher_tile(A + s * L.a_stage + (mt * 2) * kTileBytes, warp - 4, lane,
+                                             row0 + 128 * mt, k, (U.step0 + ks) * kKStep, U.m, rk);
+                } else {
+                    draw_c_tiles(A + s * L.a_stage, gt, mtiles, row0, k, (U.step0 + ks) * kKStep, U.m, rk);
+                }
             }
             // uint8 -> BF16: 8 pixels of one frame per item, over both clips
             if (!tc::mbar_wait(&tma_full[s], u & 1u, abort_flag, status)) break;
@@ -428,6 +470,7 @@ struct SketchArgs {
     uint2 key;
 };
 
+template <bool kRad>
 __global__ void __launch_bounds__(kThreads, 1)
 sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap0, const __grid_constant__ CUtensorMap tmap1,
                  const SketchArgs a, int* status) {
@@ -451,7 +494,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmap0, const __grid_constan
     U.mtiles = a.mtiles;
     U.k = a.k;
     U.rowblk = blockIdx.x;
-    sketch_tc_body(U, status, smem);
+    sketch_tc_body<kRad>(U, status, smem);
 }
 
 // Grouped launch: CTA b runs work item items[b] (any clip or clip pair, frame
@@ -461,7 +504,7 @@ sketch_tc_grouped_kernel(const SketchItem* __restrict__ items, int* status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const SketchItem it = items[blockIdx.x];
-    sketch_tc_body(it, status, smem);
+    sketch_tc_body<false>(it, status, smem);
 }
 
 // Grouped fixed-order reduce: element idx of the concatenated outputs belongs
@@ -520,6 +563,7 @@ __host__ __device__ inline uint32_t pack_smem_bytes() {
     return kStages * (kPackAStage + kPackBStage) + (3 * kStages + 1) * 8 + 64;
 }
 
+template <bool kRad>
 __global__ void __launch_bounds__(kThreads, 1)
 sketch_tc_packed_kernel(const __grid_constant__ PackArgs a, int* status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -609,7 +653,7 @@ sketch_tc_packed_kernel(const __grid_constant__ PackArgs a, int* status) {
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint64_t bdesc = tc::desc_sw128(b_base + slot * (kPackBStage / 2) + kk * 32);
 #pragma unroll
-                        for (int hl = 0; hl < 2; ++hl) {
+                        for (int hl = 0; hl < (kRad ? 1 : 2); ++hl) {
                             const uint64_t adesc = tc::desc_sw128(a_base + hl * kTileBytes + kk * 32);
                             tc::mma_bf16(tmem_base + slot * kAccCols, adesc, bdesc, slot ? idesc1 : idesc0,
                                          (ks | kk | hl) ? 1u : 0u);
@@ -628,7 +672,10 @@ sketch_tc_packed_kernel(const __grid_constant__ PackArgs a, int* status) {
             const int s = static_cast<int>(ks % kStages);
             const uint32_t u = static_cast<uint32_t>(ks / kStages);
             if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
-            draw_c_tiles(A + s * kPackAStage, gt, 1, row0, k, (step0 + ks) * kKStep, a.m, rk);
+            if constexpr (kRad)
+                draw_rademacher_tile(A + s * kPackAStage, warp - 4, lane, row0, k, (step0 + ks) * kKStep, a.m, rk);
+            else
+                draw_c_tiles(A + s * kPackAStage, gt, 1, row0, k, (step0 + ks) * kKStep, a.m, rk);
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&ab_full[s]);
         }
@@ -744,7 +791,8 @@ namespace {
 
 // One launch: nclips (1 or 2) clips of <= 256 frames, each its own DY.
 cdmd_status launch_sketch_tc_unit(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
-                                  const int64_t* ldd, int k, uint64_t seed, double* const* DY, cudaStream_t stream) {
+                                  const int64_t* ldd, bool rad, int k, uint64_t seed, double* const* DY,
+                                  cudaStream_t stream) {
     const int mtiles = nclips == 1 ? 2 : 1;
     CUtensorMap tmap[2];
     for (int g = 0; g < nclips; ++g) {
@@ -777,10 +825,9 @@ cdmd_status launch_sketch_tc_unit(cdmd_ctx* ctx, int nclips, const uint8_t* cons
     a.key = seed_key(seed);
     const size_t smem = smem_layout(mtiles, nclips, a.n[0], a.n[1]).total + 1024;
     if (smem > kMaxSmem) return fail(CDMD_ERR_UNSUPPORTED, "sketch: %zu bytes of shared memory per CTA", smem);
-    CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem)));
-    sketch_tc_kernel<<<dim3(rowblks, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(tmap[0], tmap[1], a,
-                                                                                             ctx->d_status);
+    auto kern = rad ? sketch_tc_kernel<true> : sketch_tc_kernel<false>;
+    CDMD_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    kern<<<dim3(rowblks, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(tmap[0], tmap[1], a, ctx->d_status);
     CDMD_CHECK_LAUNCH("sketch_tc_kernel");
     const int64_t tot = static_cast<int64_t>(k) * std::max(a.n[0], a.n[1]);
     sketch_tc_reduce_kernel<<<dim3(static_cast<unsigned>((tot + 255) / 256), nclips), 256, 0, stream>>>(
@@ -799,8 +846,8 @@ cdmd_status check_tc_video(const uint8_t* D, int64_t ldd) {
 
 cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, cdmd_ctype ctype,
                              int k, uint64_t seed, double* DY, cudaStream_t stream) {
-    if (ctype != CDMD_C_GAUSSIAN)
-        return fail(CDMD_ERR_UNSUPPORTED, "BF16X2 sketch is built for the Gaussian measurement matrix");
+    if (ctype != CDMD_C_GAUSSIAN && ctype != CDMD_C_RADEMACHER)
+        return fail(CDMD_ERR_UNSUPPORTED, "BF16X2 sketch generates GAUSSIAN or RADEMACHER C");
     cdmd_status st = check_tc_video(D, ldd);
     if (st != CDMD_OK) return st;
     // the sketch is linear in the frames: DY[t0:t1] = C D[:, t0:t1]
@@ -808,19 +855,20 @@ cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, 
         const int nc = std::min(kMaxFrames, n - t0);
         const uint8_t* Dc = D + static_cast<int64_t>(t0) * ldd;
         double* DYc = DY + static_cast<int64_t>(t0) * k;
-        st = launch_sketch_tc_unit(ctx, 1, &Dc, m, &nc, &ldd, k, seed, &DYc, stream);
+        st = launch_sketch_tc_unit(ctx, 1, &Dc, m, &nc, &ldd, ctype == CDMD_C_RADEMACHER, k, seed, &DYc, stream);
         if (st != CDMD_OK) return st;
     }
     return CDMD_OK;
 }
 
 cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
-                                    const int64_t* ldd, int k, uint64_t seed, double* const* DY, cudaStream_t stream) {
+                                    const int64_t* ldd, cdmd_ctype ctype, int k, uint64_t seed, double* const* DY,
+                                    cudaStream_t stream) {
     for (int i = 0; i < nclips; ++i) {
         cdmd_status st = check_tc_video(D[i], ldd[i]);
         if (st != CDMD_OK) return st;
     }
-    if (nclips == 1) return launch_sketch_tc(ctx, D[0], m, n[0], ldd[0], CDMD_C_GAUSSIAN, k, seed, DY[0], stream);
+    if (nclips == 1) return launch_sketch_tc(ctx, D[0], m, n[0], ldd[0], ctype, k, seed, DY[0], stream);
     // BF16 copies of every clip's frames (one HBM-bound pass each)
     const int64_t ldw = (m + 15) / 16 * 16;
     size_t elems = 0;
@@ -848,8 +896,8 @@ cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* co
                        reinterpret_cast<void**>(&part));
     if (st != CDMD_OK) return st;
     const size_t smem = pack_smem_bytes() + 1024;
-    CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_tc_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem)));
+    auto packed = ctype == CDMD_C_RADEMACHER ? sketch_tc_packed_kernel<true> : sketch_tc_packed_kernel<false>;
+    CDMD_CHECK_CUDA(cudaFuncSetAttribute(packed, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     PackArgs a{};
     a.part = part;
     a.k = k;
@@ -864,8 +912,7 @@ cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* co
         a.nslot[1] = rows > 256 ? (rows - 256 + 15) / 16 * 16 : 0;
         int maxL = 0;
         for (int i = 0; i < a.nseg; ++i) maxL = std::max(maxL, a.seg[i].L);
-        sketch_tc_packed_kernel<<<dim3(rowblks, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(
-            a, ctx->d_status);
+        packed<<<dim3(rowblks, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(a, ctx->d_status);
         CDMD_CHECK_LAUNCH("sketch_tc_packed_kernel");
         const int64_t tot = static_cast<int64_t>(maxL) * k;
         sketch_packed_reduce_kernel<<<dim3(static_cast<unsigned>((tot + 255) / 256), a.nseg), 256, 0, stream>>>(
