@@ -87,7 +87,8 @@ typedef enum {
  *   FP32    CUDA-core FP32 FMA, FP32 partial sums over pixel chunks reduced
  *           in FP64.
  *   BF16X2  tcgen05 tensor cores: uint8 pixels are exact in BF16, the real
- *           operand (C or G) is split into hi + lo BF16 parts, FP32
+ *           operand (Gaussian C or G) is split into hi + lo BF16 parts
+ *           (Rademacher C, +1 / -1, is exact and takes one product), FP32
  *           accumulation in tensor memory. */
 typedef enum { CDMD_PREC_FP32 = 0, CDMD_PREC_BF16X2 = 1 } cdmd_prec;
 
@@ -189,9 +190,11 @@ cdmd_status cdmd_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, void* stream);
 /* Dense Gaussian / Rademacher C generated in-kernel from `seed` (never
  * stored).  D: m x n frames (n >= 2), ldd >= m.  DY: k x n doubles
  * (column-major, ld = k), overwritten.  prec selects FP32 CUDA-core or
- * BF16 hi+lo tensor-core arithmetic (BF16X2 is defined for Gaussian C, needs
- * a 16-byte aligned D with ldd % 16 == 0, and sketches clips longer than 256
- * frames in 256-frame pieces, the product being linear in the frames). */
+ * tensor-core arithmetic (BF16X2: hi+lo BF16 for Gaussian C, one exact BF16
+ * product for Rademacher C, whose sketch is then exact while every partial
+ * sum stays below 2^24; needs a 16-byte aligned D with ldd % 16 == 0, and
+ * sketches clips longer than 256 frames in 256-frame pieces, the product
+ * being linear in the frames). */
 cdmd_status cdmd_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                         cdmd_ctype ctype, int k, uint64_t seed, cdmd_prec prec,
                         double* DY, void* stream);
@@ -201,11 +204,11 @@ cdmd_status cdmd_sketch(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64
  * the same pixel count m and C is drawn from the same (ctype, k, seed) as
  * cdmd_sketch draws it.  This is the case of one camera (one sensing matrix)
  * whose video is processed window by window.  With prec = CDMD_PREC_BF16X2,
- * a Gaussian C and nclips >= 2, each clip's frames are first widened to a
- * BF16 copy in the context's workspace (2 m n bytes per clip), then the
- * frames of all clips are packed 512 to a launch: each entry of C drawn
- * feeds every frame of the launch, whichever clip it belongs to.  A single
- * clip, and every other precision or C, go as cdmd_sketch would.  D[i],
+ * a Gaussian or Rademacher C and nclips >= 2, each clip's frames are first
+ * widened to a BF16 copy in the context's workspace (2 m n bytes per clip),
+ * then the frames of all clips are packed 512 to a launch: each entry of C
+ * drawn feeds every frame of the launch, whichever clip it belongs to.  A
+ * single clip, and the FP32 precision, go as cdmd_sketch would.  D[i],
  * n[i], ldd[i], DY[i] as for cdmd_sketch; the four arrays are host arrays of
  * nclips entries (D[i], DY[i] device pointers).  Results agree with
  * cdmd_sketch's up to the rounding order of the split partial sums.
