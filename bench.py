@@ -81,6 +81,56 @@ def fmeasure(pred, truth):
     return 2 * prec * rec / (prec + rec) if prec + rec > 0 else 0.0
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden", "cdmd_1080p_x200.json")
+
+
+def load_golden():
+    """The FP64 oracle's stored results for the 1920x1080x200 clip (written by
+    tests/golden/make_fullsize_1080p.py), or None if absent."""
+    if not os.path.exists(GOLDEN):
+        return None
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def golden_applies(gold, clip_seed_value):
+    if gold is None:
+        return False
+    g, w = gold["workload"], WORKLOAD
+    return (g["width"], g["height"], g["n"], g["clip_seed"], g["drift"], g["k"], g["c_seed"], g["r"], g["K"],
+            g["tau"]) == (w["width"], w["height"], w["n"], clip_seed_value, w["drift"], w["k"], w["c_seed"],
+                          w["r"], w["K"], w["tau"])
+
+
+def compare_with_golden(gold, form, lam, sel, bg_at, F):
+    """Errors of one run of the clip against the oracle's stored results:
+    eigenvalues matched one to one (relative error, all modes and modes at
+    least 1e-3 from any other), the selected set, the background at the
+    stored seeded (pixel, frame) points (relative 2-norm and max abs error;
+    bg_at(J, T) returns the run's background there) and the F-measure
+    against truth beside the oracle's."""
+    g = gold[form]
+    lam_ref = np.array([complex(a, b) for a, b in gold["lam"]])
+    idx = [int(np.argmin(np.abs(lam - x))) for x in lam_ref]
+    rel = np.abs(lam[idx] - lam_ref) / np.abs(lam_ref)
+    sep = np.array([np.min(np.abs(np.delete(lam_ref, i) - x)) >= 1e-3 for i, x in enumerate(lam_ref)])
+    rng = np.random.default_rng(gold["bg_sample_seed"])
+    m = gold["workload"]["width"] * gold["workload"]["height"]
+    J = rng.integers(0, m, gold["bg_sample_count"])
+    T = rng.integers(0, gold["workload"]["n"], gold["bg_sample_count"])
+    ref = np.array(g["bg_samples"])
+    got = bg_at(J, T)
+    return {"oracle_form": form,
+            "eig_rel_err_max_separated": float(rel[sep].max()) if sep.any() else None,
+            "eig_rel_err_max_all": float(rel.max()), "eig_separated_modes": int(sep.sum()),
+            "selection_equal": bool(len(set(idx)) == len(idx) and set(int(v) for v in sel) ==
+                                    {idx[q] for q in g["sel"]}),
+            "bg_rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "bg_max_abs_err_grey": float(np.abs(got - ref).max()),
+            "bg_points": int(len(ref)),
+            "fmeasure": F, "fmeasure_oracle": g["F"], "fmeasure_diff": abs(F - g["F"])}
+
+
 def launches_per_step(selector, K, clips=1, n=200):
     """Kernels one pipeline step over `clips` clips of n frames launches:
     sketch 2 for one clip (tiles + fixed-order reduce), or for several clips
@@ -200,12 +250,17 @@ class ClockSampler:
 # CPU oracle baseline (bounded sample)
 # ----------------------------------------------------------------------------
 
-def oracle_fps(clip, sample_px, dec=None, t_dec=None):
-    """FP64 oracle frames/s estimate on a bounded sample: the pixel-proportional
-    passes (sketch, lift, subtract) run on the first `sample_px` pixels and are
-    scaled to the frame; the small solves (independent of the frame size) run
-    on the k x n sketch of the sample.  Pass `dec`/`t_dec` to reuse a timed
-    decomposition.  Returns (fps, detail, dec, t_dec)."""
+CPU_SAMPLE_PX = WORKLOAD["width"] * 8     # pixels per oracle step (eight rows of the frame)
+
+
+def oracle_step(clip, sample_px):
+    """One step of the FP64 oracle on a bounded sample of the clip, timed
+    part by part: the sketch C D of the first `sample_px` pixels (k x n, the
+    same shape as the full clip's sketch), the small solves on that sketch
+    (the full-size problem: their cost does not depend on the pixel count),
+    then lift, background and mask of those pixels.  Returns the measured
+    seconds of each part and the full-clip estimate (pixel passes scaled by
+    m / sample_px, small solves once)."""
     from oracle import cdmd as O
     from oracle import measurement as M
     w = WORKLOAD
@@ -214,21 +269,23 @@ def oracle_fps(clip, sample_px, dec=None, t_dec=None):
     t0 = time.perf_counter()
     Cs = M.gaussian_block(w["c_seed"], np.arange(k), np.arange(sample_px))
     DY = O.sketch(Cs, Dm)
-    t_sketch = time.perf_counter() - t0
-    if dec is None:
-        t0 = time.perf_counter()
-        dec = O.decompose(DY, r, K)
-        t_dec = time.perf_counter() - t0
-    t0 = time.perf_counter()
+    t1 = time.perf_counter()
+    dec = O.decompose(DY, r, K)
+    t2 = time.perf_counter()
     Phi = O.lift(Dm, dec["G"][:, dec["sel"]])
     bg = O.background(Phi, dec["beta"], dec["lam"][dec["sel"]], n)
-    mask = O.foreground_mask(Dm, bg, w["tau"])
-    O.pack_mask(mask)
-    t_pix = time.perf_counter() - t0
+    O.pack_mask(O.foreground_mask(Dm, bg, w["tau"]))
+    t3 = time.perf_counter()
     scale = m / sample_px
-    total = (t_sketch + t_pix) * scale + t_dec
-    detail = dict(t_sketch_sample=t_sketch, t_pixel_sample=t_pix, t_decompose=t_dec, scale=scale)
-    return n / total, detail, dec, t_dec
+    parts = dict(sketch_s=t1 - t0, decompose_s=t2 - t1, pixel_passes_s=t3 - t2)
+    est = (parts["sketch_s"] + parts["pixel_passes_s"]) * scale + parts["decompose_s"]
+    return dict(measured_s=t3 - t0, parts=parts, scale=scale, full_clip_estimate_s=est)
+
+
+def oracle_sample_text(clip, sample_px, scale):
+    return (f"per step: first {sample_px} of {clip.m} pixels x {clip.n} frames (sketch, lift, background, mask), "
+            f"plus the small solves on that {WORKLOAD['k']}x{clip.n} sketch; full-clip figure = pixel passes x "
+            f"{scale:.0f} + small solves (an estimate from the measured parts)")
 
 
 def cpu_cores():
@@ -236,26 +293,33 @@ def cpu_cores():
 
 
 def run_reference(args, rank):
+    """The oracle is the reference arm.  Each step runs oracle_step for real;
+    ms_per_step is its measured time, `value` the full-clip frames/s estimate
+    from the measured parts (labelled as such)."""
     if rank != 0:
         return 0
     import videogen
     w = WORKLOAD
     clip = videogen.make_clip(w["width"], w["height"], w["n"], seed=w["clip_seed"], drift=w["drift"])
-    sample_px = w["width"] * 4
-    times, detail, dec, t_dec = [], None, None, None
-    for step in range(args.warmup + args.steps):
-        fps, detail, dec, t_dec = oracle_fps(clip, sample_px, dec, t_dec)
-        if step >= args.warmup:
-            times.append(w["n"] / fps)
-    per_clip = float(np.mean(times))
-    value = w["n"] / per_clip
-    sample = (f"first {sample_px} of {clip.m} pixels x {w['n']} frames per step, scaled x{detail['scale']:.0f}; "
-              f"small solves on the full-size {w['k']}x{w['n']} sketch of the sample")
+    steps = []
+    for i in range(args.warmup + args.steps):
+        st = oracle_step(clip, CPU_SAMPLE_PX)
+        if i >= args.warmup:
+            steps.append(st)
+    measured_ms = 1e3 * float(np.mean([st["measured_s"] for st in steps]))
+    est_s = float(np.mean([st["full_clip_estimate_s"] for st in steps]))
+    value = w["n"] / est_s
+    sample = oracle_sample_text(clip, CPU_SAMPLE_PX, steps[0]["scale"])
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_clip * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": measured_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.prec, args.selector), "m": clip.m, "n": w["n"], "k": w["k"],
                        "r": w["r"], "K": w["K"], "implementation": "FP64 CPU oracle, OMP selection"},
+            "measured": {"ms_per_step": measured_ms, "what": "one oracle step on the sample (see cpu_baseline.sample)",
+                         "parts_ms": {k2: 1e3 * float(np.mean([st["parts"][k2] for st in steps]))
+                                      for k2 in steps[0]["parts"]}},
+            "estimate": {"ms_per_clip_full": est_s * 1e3, "value_is_estimate": True,
+                         "formula": "(sketch + pixel passes) x m / sample pixels + small solves"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -686,14 +750,96 @@ def run_ours(args, rank, world, local_rank):
                 "form": (f"{cps} clips under one Rademacher C, packed 512 frames to a launch; time per clip "
                          "includes the widen passes and the reduces; one BF16 product (C exact)")}
 
+    def gather_4k_measure(reps=5):
+        """The gather workload: a 3840x2160 clip of 300 frames (8 moving
+        ellipses) rendered on the device, sketched by sparse +-1 C (density
+        1/1000) and by single-pixel C (k = 1000 pixels), then decompose
+        (r = 30, K = 10), lift of the selected modes and subtract.  Each pass
+        is timed with CUDA events on the launching stream (median of `reps`
+        runs, each after an L2 flush) against its algorithmic bytes."""
+        W4, H4, n4, k4, r4, K4 = 3840, 2160, 300, 1000, 30, 10
+        m4 = W4 * H4
+        spec = videogen.clip_spec(W4, H4, n4, 4321, n_objects=8, shape="ellipse")
+        D4 = C.cdmd_synth_clip(ctx, spec, 4321)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        hbm = float(load_peaks()[0]["hbm_gbs"])
+        out = {"workload": f"{W4}x{H4}x{n4}, 8 ellipses, k={k4}, r={r4}, K={K4}",
+               "lift_precision": "fp32 (the tensor-core lift holds at most 256 frames)"}
+        words = n4 * ((m4 + 31) // 32) * 4
+        alg = {"lift": m4 * (n4 - 1) + m4 * K4 * 8, "subtract": m4 * n4 + m4 * K4 * 8 + words}
+        for name, meas in (("sparse", C.Measure(ctx, "sparse", m4, k4, 77, 1e-3)),
+                           ("single_pixel", C.Measure(ctx, "rowsample", m4, k4, 3))):
+            alg_sk = m4 * n4 if name == "sparse" else k4 * n4
+            times = {"sketch": [], "decompose": [], "lift": [], "subtract": []}
+            for it in range(reps + 1):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+                with torch.cuda.stream(main_stream):
+                    flush.zero_()
+                    ev[0].record(main_stream)
+                    DY4 = C.cdmd_sketch_gather(ctx, D4, meas)
+                    ev[1].record(main_stream)
+                    dec4 = C.cdmd_decompose(ctx, DY4, r4, K4)
+                    ev[2].record(main_stream)
+                    flush.zero_()
+                    e_l = torch.cuda.Event(enable_timing=True)
+                    e_l.record(main_stream)
+                    Phi4 = C.cdmd_lift(ctx, D4, dec4["G"], cols=dec4["sel"], ncols=K4, prec="fp32")
+                    ev[3].record(main_stream)
+                    flush.zero_()
+                    e_s = torch.cuda.Event(enable_timing=True)
+                    e_s.record(main_stream)
+                    C.cdmd_subtract(ctx, D4, Phi4, dec4["beta"], dec4["lam"], w["tau"], cols=dec4["sel"])
+                    ev[4].record(main_stream)
+                torch.cuda.synchronize()
+                if it == 0:
+                    continue                      # warm-up (workspace growth)
+                times["sketch"].append(ev[0].elapsed_time(ev[1]))
+                times["decompose"].append(ev[1].elapsed_time(ev[2]))
+                times["lift"].append(e_l.elapsed_time(ev[3]))
+                times["subtract"].append(e_s.elapsed_time(ev[4]))
+            C.cdmd_status_sync(ctx)
+            med = {kk: float(np.median(v)) for kk, v in times.items()}
+            rec = {"ms": med, "nnz": int(meas.nnz) if name == "sparse" else None}
+            for pss, b in (("sketch", alg_sk), ("lift", alg["lift"]), ("subtract", alg["subtract"])):
+                gbs = b / (med[pss] * 1e-3) / 1e9
+                rec[pss + "_bytes"] = b
+                rec[pss + "_gbs"] = gbs
+                rec[pss + "_frac_hbm"] = gbs / hbm
+            rec["frames_per_s_single_stream"] = n4 / (sum(med.values()) * 1e-3)
+            out[name] = rec
+        del D4, flush
+        torch.cuda.empty_cache()
+        return out
+
     # the headline form and the plain FP32 + OMP form it is compared with
     forms = {"head": (args.prec, args.selector)}
     if not args.no_plain and (args.prec, args.selector) != ("fp32", "omp"):
         forms["plain"] = ("fp32", "omp")
     results = {}
+    gold = load_golden()
+    check_gold = rank == 0 and golden_applies(gold, clip_seed(rank))
+
+    def vs_oracle(selector, mk):
+        """Clip 0 of lanes[0] (the stored oracle clip) against the oracle."""
+        L = lanes[0]
+        dec = L.dec[0]
+        _, bg = C.cdmd_subtract(ctx, D, L.Phi[0], dec["beta"], dec["lam"], w["tau"], cols=dec["sel"],
+                                want_bg=True)
+        torch.cuda.synchronize()
+
+        def bg_at(J, T):
+            return bg[torch.from_numpy(T).to(dev), torch.from_numpy(J).to(dev)].double().cpu().numpy()
+        out = compare_with_golden(gold, "mlp" if selector == "mlp" else "omp",
+                                  torch.view_as_complex(dec["lam"]).cpu().numpy(), dec["sel"].cpu().numpy(), bg_at,
+                                  fmeasure(mk, clip.truth.T))
+        del bg
+        return out
+
     for label, (prec, selector) in forms.items():
         total_ms, passes, clocks = timed(prec, selector, args.steps, args.warmup, sample_clocks=(label == "head"))
         results[label] = dict(total_ms=total_ms, passes=passes, clocks=clocks, mask=C.unpack_mask(mask, m))
+        if check_gold:
+            results[label]["vs_oracle"] = vs_oracle(selector, results[label]["mask"])
     fallbacks = None
     if args.selector == "mlp":
         fallbacks = sum(C.cdmd_selector_fallbacks(L.ctx, reset=True, stream=L.stream) for L in lanes)
@@ -766,7 +912,8 @@ def run_ours(args, rank, world, local_rank):
     rank_line = auto_rank_measure()
     rad_line = rademacher_measure() if args.prec == "bf16x2" else None
 
-    batch_line = run_batch_measure(C, SEL, torch, dev, args, model) if args.batch else None
+    batch_line = run_batch_measure(C, SEL, torch, dev, args, model) if not args.no_batch else None
+    gather_line = gather_4k_measure() if not args.no_gather else None
 
     if rank != 0:
         if dist is not None:
@@ -781,15 +928,26 @@ def run_ours(args, rank, world, local_rank):
     peaks, peak_src = load_peaks()
     sketch_ms = float(head["passes"][0])
     if args.prec == "bf16x2":
-        achieved = 2.0 * counts["sketch_flops"] / (sketch_ms * 1e-3) / 1e12     # hi + lo tensor products
+        # the method's work, 2 k m n per clip (C D); the hi + lo split doubles
+        # the tensor products the kernel issues, reported apart as pipe work
+        achieved = counts["sketch_flops"] / (sketch_ms * 1e-3) / 1e12
         peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        hbm_gbs = float(peaks["hbm_gbs"])
+        t_ideal = max(counts["sketch_flops"] / (peak * 1e12), counts["sketch_bytes"] / (hbm_gbs * 1e9))
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": t_ideal / (sketch_ms * 1e-3),
+                "ideal_ms": t_ideal * 1e3, "measured_ms": sketch_ms,
+                "flops_per_launch_unit": "2 k m n per clip (method's flops; hi + lo products not counted)",
+                "tensor_pipe_tflops_hi_lo": 2.0 * achieved,
+                "tensor_pipe_frac_hi_lo": 2.0 * achieved / peak,
                 "traffic": dram_traffic("sketch_tc.cu"),
                 "kernel": ("sketch (tcgen05 BF16 hi+lo" + (f", {cps} clips under one C packed 512 frames to a "
                                                            "launch; time per clip includes the widen passes and "
                                                            "the reduces)" if cps > 1
                                                            else "; time includes the reduce)")),
-                "peak_source": f"{peak_src} bf16 sustained"}
+                "peak_source": (f"{peak_src} bf16 sustained (cuBLAS BF16 GEMM under the power cap, "
+                                "MEASURED_PEAKS.json); frac = max(flop time at that peak, byte time at measured "
+                                "HBM) / measured time")}
     else:
         fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         achieved = counts["sketch_flops"] / (sketch_ms * 1e-3) / 1e12
@@ -832,6 +990,10 @@ def run_ours(args, rank, world, local_rank):
     line["accuracy"] = {"fmeasure_vs_truth": fmeasure(head["mask"], truth),
                         "selector": args.selector, "selector_fallbacks": fallbacks,
                         "selector_model": os.path.relpath(SEL.DEFAULT_MODEL, ROOT) if args.selector == "mlp" else None}
+    if "vs_oracle" in head:
+        line["accuracy"]["vs_oracle"] = head["vs_oracle"]
+        line["accuracy"]["vs_oracle_note"] = ("clip 0 of the step against the FP64 oracle's stored results for the "
+                                              "same uint8 clip (" + os.path.relpath(GOLDEN, ROOT) + ")")
     if "plain" in results:
         plain = results["plain"]
         agree = plain["mask"] == head["mask"]
@@ -841,6 +1003,8 @@ def run_ours(args, rank, world, local_rank):
                               "per_pass_ms": {nm: float(v) for nm, v in
                                               zip(["sketch", "decompose", "lift", "subtract"], plain["passes"])},
                               "mask_agreement_vs_head": float(agree.mean())}
+        if "vs_oracle" in plain:
+            line["accuracy"]["plain_fp32_omp_vs_oracle"] = plain["vs_oracle"]
     med_us, med_mask = results["median"]
     med_bytes = 2 * n * ((m + 31) // 32) * 4
     line["postpass"] = {"kernel": "median3x3 (bit-sliced 3x3 median of each mask frame, zero padding)",
@@ -870,12 +1034,15 @@ def run_ours(args, rank, world, local_rank):
         line["rademacher_sketch"] = rad_line
     if batch_line is not None:
         line["batch"] = batch_line
+    if gather_line is not None:
+        line["gather_4k"] = gather_line
     if not args.no_cpu:
-        fps, detail, _, _ = oracle_fps(clip, w["width"] * 8)
-        line["cpu_baseline"] = {"value": fps, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                                "sample": (f"first {w['width'] * 8} of {m} pixels x {n} frames, pixel passes "
-                                           f"scaled x{detail['scale']:.0f}; FP64 small solves on the sample's "
-                                           f"{k}x{n} sketch; numpy elementwise single-threaded, BLAS multi-threaded")}
+        st = oracle_step(clip, CPU_SAMPLE_PX)
+        line["cpu_baseline"] = {"value": w["n"] / st["full_clip_estimate_s"], "unit": UNIT, "cores": cpu_cores(),
+                                "kind": "oracle", "sample": oracle_sample_text(clip, CPU_SAMPLE_PX, st["scale"]),
+                                "measured_s": st["measured_s"],
+                                "parts_s": st["parts"], "value_is_estimate": True,
+                                "threads": "numpy elementwise single-threaded, BLAS multi-threaded"}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -907,8 +1074,10 @@ def main():
     ap.add_argument("--clips-per-step", type=int, choices=range(1, 9), default=WORKLOAD["clips_per_step"],
                     help="clips per step, all under one C (>= 2: their frames are packed 512 to a sketch "
                          "launch, so one draw of C feeds all of them)")
-    ap.add_argument("--batch", action="store_true",
-                    help="also measure a batch of 64 clips of mixed size (grouped launches, graph, autotuner)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batch of 64 clips of mixed size (grouped launches, graph, autotuner)")
+    ap.add_argument("--no-gather", action="store_true",
+                    help="skip the 3840x2160x300 gather workload (sparse and single-pixel C)")
     ap.add_argument("--size", default=None,
                     help="WxH of a smaller clip for profiling captures (default: the 1920x1080 workload)")
     ap.add_argument("--sm-limit", type=int, default=136,

@@ -171,6 +171,17 @@ cdmd_status cdmd_status_sync(cdmd_ctx* ctx, void* stream);
  * CDMD_ERR_INVALID_ARG for a NULL ctx or limit_us outside the range. */
 cdmd_status cdmd_selftest_wait(cdmd_ctx* ctx, uint32_t limit_us, void* stream);
 
+/* The FP64 reciprocal and reciprocal square root the small solves use on
+ * their latency-critical paths (Newton-Raphson from the hardware
+ * approximations, two steps), applied to n doubles: rcp[i] = 1/a[i],
+ * rsqrt[i] = 1/sqrt(a[i]) (either output may be NULL).  The paper has no
+ * counterpart; this lets a test bound their error against IEEE division and
+ * square root.  Inputs must be normal positive numbers whose reciprocal is
+ * normal (subnormals are flushed to zero).  Device arrays, enqueued on
+ * `stream`.  CDMD_ERR_INVALID_ARG for a NULL ctx, n < 0 or a NULL a. */
+cdmd_status cdmd_selftest_recip(cdmd_ctx* ctx, const double* a, int64_t n, double* rcp, double* rsqrt,
+                                void* stream);
+
 /* ---- measurement matrices (Section 3.3) ---------------------------------- */
 
 /* Exact number of non-zeros of the SPARSE matrix for (m, k, seed, density),

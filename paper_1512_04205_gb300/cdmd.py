@@ -40,7 +40,7 @@ EXPORTED = ["cdmd_create", "cdmd_destroy", "cdmd_last_error", "cdmd_status_strin
             "cdmd_batch_run", "cdmd_batch_status_sync", "cdmd_batch_views", "cdmd_batch_tuning",
             "cdmd_batch_destroy", "cdmd_copy", "cdmd_sketch_shared", "cdmd_run_shared", "cdmd_run_host_shared",
             "cdmd_selftest_wait", "cdmd_median3x3", "cdmd_snapshot_gram", "cdmd_decompose_gram",
-            "cdmd_run_exact", "cdmd_decompose_auto"]
+            "cdmd_run_exact", "cdmd_decompose_auto", "cdmd_selftest_recip"]
 BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_GROUPED = 1, 2, 4
 
 
@@ -110,6 +110,7 @@ def load_library(path=LIB_PATH):
                                vp],
         "cdmd_run_shared": [vp, ctypes.c_int, vp, i64, vp, vp, ctypes.POINTER(cdmd_params), vp, vp],
         "cdmd_selftest_wait": [vp, ctypes.c_uint32, vp],
+        "cdmd_selftest_recip": [vp, vp, i64, vp, vp, vp],
         "cdmd_median3x3": [vp, vp, i64, i64, ctypes.c_int, vp, vp],
         "cdmd_snapshot_gram": [vp, vp, i64, ctypes.c_int, i64, vp, vp],
         "cdmd_decompose_gram": [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [vp] * 7,
@@ -254,8 +255,14 @@ def cdmd_sketch_noalloc(D, k, seed, ctype="gaussian", DY=None, stream=None):
     DY is given)."""
     import torch
     n, m, ldd = _video(D)
+    if D.device.index != torch.cuda.current_device():
+        raise ValueError("cdmd_sketch_noalloc runs on the current device (cuda:%d); D is on %s"
+                         % (torch.cuda.current_device(), D.device))
     if DY is None:
         DY = torch.empty((n, k), dtype=torch.float64, device=D.device)
+    elif (DY.dtype != torch.float64 or tuple(DY.shape) != (n, k) or not DY.is_contiguous()
+          or DY.device != D.device):
+        raise ValueError("DY must be a contiguous float64 tensor (n, k) = (%d, %d) on %s" % (n, k, D.device))
     _check(load_library().cdmd_sketch_noalloc(_ptr(D), m, n, ldd, CTYPES[ctype], int(k), int(seed) & (2**64 - 1),
                                               _ptr(DY), _stream(stream)))
     return DY
@@ -511,12 +518,43 @@ def cdmd_selftest_wait(ctx, limit_us, stream=None):
     _check(ctx.lib.cdmd_selftest_wait(ctx.handle, int(limit_us), _stream(stream)))
 
 
+def cdmd_selftest_recip(ctx, a, stream=None):
+    """The small solves' FP64 reciprocal and reciprocal square root applied
+    to a float64 device tensor; returns (1/a, 1/sqrt(a))."""
+    import torch
+    if a.dtype != torch.float64 or not a.is_cuda or not a.is_contiguous():
+        raise ValueError("a must be a contiguous float64 CUDA tensor")
+    r = torch.empty_like(a)
+    q = torch.empty_like(a)
+    _check(ctx.lib.cdmd_selftest_recip(ctx.handle, _ptr(a), int(a.numel()), _ptr(r), _ptr(q), _stream(stream)))
+    return r, q
+
+
 def cdmd_workspace_views(ctx):
     """Raw device pointers of the last cdmd_run's intermediates."""
     ptrs = [ctypes.c_void_p() for _ in range(8)]
     _check(ctx.lib.cdmd_workspace_views(ctx.handle, *[ctypes.byref(p) for p in ptrs]))
     keys = ["DY", "sigma", "lambda", "G", "beta", "sel", "nsel", "Phi"]
     return {k: p.value for k, p in zip(keys, ptrs)}
+
+
+def workspace_tensors(ctx, m, n, k, r, K, stream=None):
+    """Device copies of the last cdmd_run's intermediates on ctx (the last
+    clip of a cdmd_run_shared): DY (n, k), sigma (r,), lam (r, 2), G
+    (r, n-1, 2), beta (r, 2), sel (K,), nsel (1,), Phi (m, K, 2) float32."""
+    import torch
+    v = cdmd_workspace_views(ctx)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    shapes = dict(DY=((n, k), torch.float64), sigma=((r,), torch.float64), lambda_=((r, 2), torch.float64),
+                  G=((r, n - 1, 2), torch.float64), beta=((r, 2), torch.float64), sel=((K,), torch.int32),
+                  nsel=((1,), torch.int32), Phi=((m, K, 2), torch.float32))
+    out = {}
+    for name, (shape, dtype) in shapes.items():
+        key = "lambda" if name == "lambda_" else name
+        t = torch.empty(shape, dtype=dtype, device=dev)
+        _check(ctx.lib.cdmd_copy(_ptr(t), ctypes.c_void_p(v[key]), t.numel() * t.element_size(), _stream(stream)))
+        out["lam" if key == "lambda" else key] = t
+    return out
 
 
 def unpack_mask(mask, m):

@@ -170,6 +170,16 @@ cdmd_status cdmd_selftest_wait(cdmd_ctx* ctx, uint32_t limit_us, void* stream) {
     return launch_selftest_wait(ctx, static_cast<uint64_t>(limit_us) * 1000ull, static_cast<cudaStream_t>(stream));
 }
 
+cdmd_status cdmd_selftest_recip(cdmd_ctx* ctx, const double* a, int64_t n, double* rcp, double* rsqrt,
+                                void* stream) {
+    clear_error();
+    CDMD_REQUIRE(ctx != nullptr, "ctx is NULL");
+    CDMD_REQUIRE(n >= 0, "n must be >= 0 (got %lld)", static_cast<long long>(n));
+    CDMD_REQUIRE(n == 0 || a != nullptr, "a is NULL");
+    DeviceGuard g(ctx->device);
+    return launch_selftest_recip(a, n, rcp, rsqrt, static_cast<cudaStream_t>(stream));
+}
+
 cdmd_status cdmd_measure_sparse_nnz(cdmd_ctx* ctx, int64_t m, int k, uint64_t seed, double density, int64_t* nnz,
                                     void* stream) {
     clear_error();

@@ -46,6 +46,37 @@ __device__ __forceinline__ void record_status(int* status, int code) {
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
 // 32x32->64 bit products with Weyl-bumped round keys.
 // ---------------------------------------------------------------------------
+// 1/a and 1/sqrt(a) in FP64 by the Newton-Raphson method: start from the
+// hardware's approximate reciprocal (rcp.approx.ftz.f64) or reciprocal square
+// root (rsqrt.approx.ftz.f64) and take two Newton steps for the root of
+// f(x) = 1/x - a, x <- x (2 - a x) = x + x (1 - a x), or of f(y) = 1/y^2 - a,
+// y <- y (3 - a y^2) / 2 = y + y (1/2 - (a/2) y^2).  Each step roughly doubles
+// the number of correct bits, so two steps from the approximation reach FP64
+// rounding level (a few ulp; bounded by a GPU test against IEEE division and
+// square root).  Zero and subnormal inputs are flushed (ftz); callers pass
+// normal positive values.  They replace a division or square root (hundreds of
+// cycles in FP64 on this GPU) on the latency-critical paths of the small solves.
+__device__ __forceinline__ double rcp64(double a) {
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(a));
+    double e = fma(-a, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-a, x, 1.0);
+    x = fma(x, e, x);
+    return x;
+}
+
+__device__ __forceinline__ double rsqrt64(double a) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+    const double h = 0.5 * a;
+    double t = fma(-h * y, y, 0.5);
+    y = fma(y, t, y);
+    t = fma(-h * y, y, 0.5);
+    y = fma(y, t, y);
+    return y;
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 key) {
 #pragma unroll
     for (int rnd = 0; rnd < 10; ++rnd) {
@@ -242,6 +273,7 @@ cdmd_status launch_subtract_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n
                                int ncols, const void* lam_t, const void* amp, int nc_pad, float tau, cdmd_bgmode mode,
                                uint32_t* mask, cudaStream_t stream);
 cdmd_status launch_selftest_wait(cdmd_ctx* ctx, uint64_t limit_ns, cudaStream_t stream);
+cdmd_status launch_selftest_recip(const double* a, int64_t n, double* r, double* q, cudaStream_t stream);
 cdmd_status launch_gram_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, double* R,
                            cudaStream_t stream);
 cdmd_status launch_decompose_auto(cdmd_ctx* ctx, const double* DY, int k, int n, int r_max, int K,

@@ -79,29 +79,6 @@ __device__ double block_sum(double v, double* red) {
     return out;
 }
 
-// 1/a and 1/sqrt(a) to full FP64 precision: hardware approximation refined by
-// two Newton steps (each step doubles the number of correct bits).
-__device__ __forceinline__ double rcp64(double a) {
-    double x;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(a));
-    double e = fma(-a, x, 1.0);
-    x = fma(x, e, x);
-    e = fma(-a, x, 1.0);
-    x = fma(x, e, x);
-    return x;
-}
-
-__device__ __forceinline__ double rsqrt64(double a) {
-    double y;
-    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-    const double h = 0.5 * a;
-    double t = fma(-h * y, y, 0.5);
-    y = fma(y, t, y);
-    t = fma(-h * y, y, 0.5);
-    y = fma(y, t, y);
-    return y;
-}
-
 // complex helpers
 struct cd {
     double x, y;

@@ -20,7 +20,25 @@ __global__ void __launch_bounds__(32) selftest_wait_kernel(uint64_t limit_ns, in
     __syncwarp();
 }
 
+// r[i] = rcp64(a[i]), q[i] = rsqrt64(a[i]): the small solves' reciprocal and
+// reciprocal square root, exposed so that a test can bound their error.
+__global__ void selftest_recip_kernel(const double* __restrict__ a, int64_t n, double* __restrict__ r,
+                                      double* __restrict__ q) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = a[i];
+    if (r) r[i] = rcp64(x);
+    if (q) q[i] = rsqrt64(x);
+}
+
 }  // namespace
+
+cdmd_status launch_selftest_recip(const double* a, int64_t n, double* r, double* q, cudaStream_t stream) {
+    if (n == 0) return CDMD_OK;
+    selftest_recip_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(a, n, r, q);
+    CDMD_CHECK_LAUNCH("selftest_recip_kernel");
+    return CDMD_OK;
+}
 
 cdmd_status launch_selftest_wait(cdmd_ctx* ctx, uint64_t limit_ns, cudaStream_t stream) {
     selftest_wait_kernel<<<1, 32, 0, stream>>>(limit_ns, ctx->d_status);
