@@ -18,6 +18,16 @@ pure function of (seed, row i, pixel j) through Philox4x32-10:
   a clear bit is +1, a set bit is -1.
 * Sparse (density 1/s): counter (j, i//4, 2, 0), word w = word i%4; the entry
   is non-zero iff w < floor(2^32 / s); then +1 if w is even, else -1.
+* SRFT (subsampled randomized Fourier transform, C = R F D): D diagonal with
+  entries d_j = exp(i theta_j) uniform on the complex unit circle,
+  theta_j = 2 pi U(w0), w0 word 0 of counter (j, 0, 5, 0); F the unnormalised
+  m-point DFT, F(f, j) = exp(-2 pi i f j / m); R keeps q = ceil(k/2) distinct
+  frequencies s_0 < s_1 < ... drawn from [0, m) by Floyd's sampling on
+  counters (t, 0, 6, 0) (as for the single-pixel rows).  The real sketch rows
+  are the real and imaginary parts of those complex measurements:
+  row 2a = Re(F D)[s_a, :] = cos(theta_j - 2 pi s_a j / m),
+  row 2a+1 = Im(F D)[s_a, :] = sin(theta_j - 2 pi s_a j / m)
+  (with odd k the last frequency keeps only its real row).
 * Single pixel: Floyd's sampling of k distinct pixel indices in [0, m).  For
   t = m-k .. m-1 draw v uniform in [0, t] as the high 64 bits of
   (w1 * 2^32 + w0) * (t + 1), with (w0, w1) the first two words of counter
@@ -36,6 +46,8 @@ STREAM_GAUSSIAN = 0
 STREAM_RADEMACHER = 1
 STREAM_SPARSE = 2
 STREAM_ROWSAMPLE = 3
+STREAM_SRFT_PHASE = 5
+STREAM_SRFT_FREQ = 6
 
 TWO_M32 = 2.0 ** -32
 
@@ -116,15 +128,17 @@ def sparse_block(seed, rows, cols, density):
     return np.where(w < thr, np.where(w % 2 == 0, 1.0, -1.0), 0.0)
 
 
-def rowsample_indices(seed, k, m):
-    """k distinct pixel indices in [0, m), increasing (Floyd's algorithm)."""
+def floyd_sample(seed, k, m, stream):
+    """k distinct integers in [0, m), increasing: Floyd's algorithm with the
+    step-t draw v = floor(((w1 << 32) | w0) (t + 1) / 2^64) from words 0, 1 of
+    counter (t, 0, stream, 0)."""
     if not 0 < k <= m:
         raise ValueError("need 0 < k <= m")
     key = seed_key(seed)
     ts = np.arange(m - k, m, dtype=np.int64)
     ctr = np.zeros((k, 4), dtype=np.uint32)
     ctr[:, 0] = ts.astype(np.uint32)
-    ctr[:, 2] = STREAM_ROWSAMPLE
+    ctr[:, 2] = stream
     words = philox4x32_10(ctr, key)
     chosen = set()
     for t, w in zip(ts.tolist(), words.tolist()):
@@ -132,6 +146,41 @@ def rowsample_indices(seed, k, m):
         v = (u64 * (t + 1)) >> 64
         chosen.add(t if v in chosen else v)
     return np.array(sorted(chosen), dtype=np.int64)
+
+
+def rowsample_indices(seed, k, m):
+    """k distinct pixel indices in [0, m), increasing (Floyd's algorithm)."""
+    return floyd_sample(seed, k, m, STREAM_ROWSAMPLE)
+
+
+def srft_frequencies(seed, k, m):
+    """The ceil(k/2) DFT rows R keeps, increasing (Floyd's algorithm)."""
+    return floyd_sample(seed, (int(k) + 1) // 2, m, STREAM_SRFT_FREQ)
+
+
+def srft_phases(seed, cols):
+    """theta_j in [0, 2 pi) of the diagonal D for pixels cols (FP64)."""
+    cols = np.asarray(cols, dtype=np.int64)
+    ctr = np.zeros((len(cols), 4), dtype=np.uint32)
+    ctr[:, 0] = cols.astype(np.uint32)
+    ctr[:, 2] = STREAM_SRFT_PHASE
+    w = philox4x32_10(ctr, seed_key(seed))[:, 0]
+    return 2.0 * np.pi * uniform_open01(w)
+
+
+def srft_block(seed, rows, cols, m, k):
+    """C[rows][:, cols] of the real SRFT sketch (k rows, m pixels), FP64.
+
+    The phase 2 pi s j / m is reduced exactly in integers (s j mod m) before
+    the angle is formed."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    freqs = srft_frequencies(seed, k, m)
+    theta = srft_phases(seed, cols)
+    s = freqs[rows // 2]
+    red = (s[:, None].astype(object) * cols[None, :].astype(object)) % int(m)
+    ang = theta[None, :] - 2.0 * np.pi * red.astype(np.float64) / float(m)
+    return np.where((rows % 2 == 0)[:, None], np.cos(ang), np.sin(ang))
 
 
 def measurement_matrix(ctype, seed, k, m, density=None):
@@ -144,6 +193,8 @@ def measurement_matrix(ctype, seed, k, m, density=None):
         return rademacher_block(seed, rows, cols)
     if ctype == "sparse":
         return sparse_block(seed, rows, cols, density)
+    if ctype == "srft":
+        return srft_block(seed, rows, cols, m, k)
     if ctype == "rowsample":
         c = np.zeros((k, m))
         c[np.arange(k), rowsample_indices(seed, k, m)] = 1.0
