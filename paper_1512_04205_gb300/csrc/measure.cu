@@ -10,10 +10,12 @@
 // FP64 reduction sums.
 //
 // ROWSAMPLE (single-pixel measurements): Floyd's sampling of k distinct
-// pixels, drawn on the host from the same Philox definition; the sketch is a
-// plain gather of k rows of D.
-#include <unordered_set>
-#include <vector>
+// pixels from the same Philox definition, on the device: the k draws in
+// parallel, then one thread walks them in order against a hash set (the
+// algorithm is sequential: whether t is taken depends on the earlier picks),
+// then a rank sort puts the picks in increasing order.  No host round trip,
+// so the build can be captured in a CUDA graph.  The sketch is a plain gather
+// of k rows of D.
 
 #include "cdmd_internal.cuh"
 
@@ -22,6 +24,7 @@ namespace {
 
 constexpr uint32_t kStreamSparse = 2u;
 constexpr uint32_t kStreamRowsample = 3u;
+constexpr uint32_t kStreamSrftFreq = 6u;
 
 // floor(2^32 * density) as a 64-bit integer: entry non-zero iff word < it.
 __host__ __device__ inline uint64_t sparse_threshold(double density) {
@@ -162,19 +165,75 @@ __global__ void rowsample_sketch_kernel(const uint8_t* __restrict__ D, int n, in
     DY[idx] = static_cast<double>(D[static_cast<int64_t>(t) * ldd + rows[i]]);
 }
 
-// Host copy of Philox4x32-10 for the single-pixel draw.
-uint4 philox_host(uint4 c, uint2 key) {
-    for (int rnd = 0; rnd < 10; ++rnd) {
-        if (rnd > 0) {
-            key.x += 0x9E3779B9u;
-            key.y += 0xBB67AE85u;
+// Floyd's sampling of k distinct integers in [0, m), step 1 (parallel): the
+// draw of step t = m-k+i, v = floor(((w1 << 32) | w0) (t + 1) / 2^64) from
+// words 0, 1 of Philox counter (t, 0, stream, 0) (stream 3: single-pixel rows;
+// stream 6: the SRFT's kept frequencies); v is uniform in [0, t].
+__global__ void rowsample_draw_kernel(int64_t m, int k, uint2 key, uint32_t stream_id, int64_t* __restrict__ draws) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    const int64_t t = m - k + i;
+    const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(t), 0u, stream_id, 0u), key);
+    const uint64_t u64 = (static_cast<uint64_t>(w.y) << 32) | w.x;
+    draws[i] = static_cast<int64_t>(__umul64hi(u64, static_cast<uint64_t>(t + 1)));
+}
+
+// Open-addressing set of non-negative int64 keys (empty slot = -1), linear
+// probing from a multiplicative hash; 2^bits slots, at least twice the keys.
+__device__ __forceinline__ uint32_t set_slot(int64_t key, int bits) {
+    return static_cast<uint32_t>((static_cast<uint64_t>(key) * 0x9E3779B97F4A7C15ull) >> (64 - bits));
+}
+
+// Floyd's sampling, step 2 (one CTA): clear the set, then thread 0 takes the
+// draws in order: step t keeps v unless v is already taken, else t (t itself
+// is never taken before step t: earlier draws are <= their own t < t).  The
+// set lives in dynamic shared memory when `table` is NULL, else in `table`.
+__global__ void rowsample_floyd_kernel(int64_t m, int k, const int64_t* __restrict__ draws, int64_t* table,
+                                       int bits, int64_t* __restrict__ picks) {
+    extern __shared__ int64_t smem_table[];
+    int64_t* set = table != nullptr ? table : smem_table;
+    const uint32_t slots = 1u << bits;
+    for (uint32_t s = threadIdx.x; s < slots; s += blockDim.x) set[s] = -1;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const uint32_t mask = slots - 1u;
+    for (int i = 0; i < k; ++i) {
+        const int64_t t = m - k + i;
+        const int64_t v = draws[i];
+        uint32_t s = set_slot(v, bits);
+        bool taken = false;
+        for (;;) {                                  // ends: the set is at most half full
+            const int64_t e = set[s];
+            if (e == -1) break;
+            if (e == v) { taken = true; break; }
+            s = (s + 1u) & mask;
         }
-        const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
-        const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
-        c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ key.x, static_cast<uint32_t>(p1),
-                       static_cast<uint32_t>(p0 >> 32) ^ c.w ^ key.y, static_cast<uint32_t>(p0));
+        int64_t pick = v;
+        if (taken) {
+            pick = t;
+            s = set_slot(t, bits);
+            while (set[s] != -1) s = (s + 1u) & mask;
+        }
+        set[s] = pick;
+        picks[i] = pick;
     }
-    return c;
+}
+
+// Floyd's sampling, step 3: rows[rank] = pick, rank = number of smaller picks
+// (the picks are distinct), so rows come out in increasing order.
+__global__ void rank_sort_kernel(const int64_t* __restrict__ picks, int k, int64_t* __restrict__ rows) {
+    __shared__ int64_t tile[1024];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t mine = i < k ? picks[i] : 0;
+    int rank = 0;
+    for (int base = 0; base < k; base += 1024) {
+        const int cnt = min(1024, k - base);
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) tile[q] = picks[base + q];
+        __syncthreads();
+        for (int q = 0; q < cnt; ++q) rank += tile[q] < mine ? 1 : 0;
+    }
+    if (i < k) rows[rank] = mine;
 }
 
 }  // namespace
@@ -189,24 +248,34 @@ cdmd_status launch_measure_sparse_count(cdmd_ctx* ctx, int64_t m, int k, uint64_
 }
 
 cdmd_status launch_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, cudaStream_t stream) {
-    if (meas->ctype == CDMD_C_ROWSAMPLE) {
+    if (meas->ctype == CDMD_C_ROWSAMPLE || meas->ctype == CDMD_C_SRFT) {
+        // ROWSAMPLE: k pixels of [0, m); SRFT: ceil(k/2) frequencies of [0, m)
+        const bool srft = meas->ctype == CDMD_C_SRFT;
         const int64_t m = meas->m;
-        const int k = meas->k;
-        const uint2 key = seed_key(meas->seed);
-        std::unordered_set<int64_t> chosen;
-        chosen.reserve(static_cast<size_t>(k) * 2);
-        for (int64_t t = m - k; t < m; ++t) {
-            const uint4 w = philox_host(make_uint4(static_cast<uint32_t>(t), 0u, kStreamRowsample, 0u), key);
-            const unsigned __int128 u64 = (static_cast<unsigned __int128>(w.y) << 32) | w.x;
-            const int64_t v = static_cast<int64_t>((u64 * static_cast<unsigned __int128>(t + 1)) >> 64);
-            if (chosen.count(v)) chosen.insert(t);
-            else chosen.insert(v);
-        }
-        std::vector<int64_t> rows(chosen.begin(), chosen.end());
-        std::sort(rows.begin(), rows.end());
-        CDMD_CHECK_CUDA(cudaMemcpyAsync(meas->rows, rows.data(), rows.size() * sizeof(int64_t),
-                                        cudaMemcpyHostToDevice, stream));
-        CDMD_CHECK_CUDA(cudaStreamSynchronize(stream));   // rows lives on the host stack
+        const int k = srft ? (meas->k + 1) / 2 : meas->k;
+        int bits = 1;
+        while ((1ll << bits) < 2ll * k) ++bits;
+        const size_t slots = static_cast<size_t>(1) << bits;
+        constexpr size_t kSmemTable = static_cast<size_t>(96) << 10;   // set in shared memory up to 96 KB
+        const bool in_smem = slots * sizeof(int64_t) <= kSmemTable;
+        int64_t* scratch = nullptr;
+        const size_t words = 2 * static_cast<size_t>(k) + (in_smem ? 0 : slots);
+        cdmd_status st = ensure_buffer(ctx, BUF_SMALL, words * sizeof(int64_t), reinterpret_cast<void**>(&scratch));
+        if (st != CDMD_OK) return st;
+        int64_t* draws = scratch;
+        int64_t* picks = draws + k;
+        int64_t* table = in_smem ? nullptr : picks + k;
+        rowsample_draw_kernel<<<static_cast<unsigned>((k + 255) / 256), 256, 0, stream>>>(
+            m, k, seed_key(meas->seed), srft ? kStreamSrftFreq : kStreamRowsample, draws);
+        CDMD_CHECK_LAUNCH("rowsample_draw_kernel");
+        const size_t smem = in_smem ? slots * sizeof(int64_t) : 0;
+        if (smem > 48 * 1024)
+            CDMD_CHECK_CUDA(cudaFuncSetAttribute(rowsample_floyd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(smem)));
+        rowsample_floyd_kernel<<<1, 1024, smem, stream>>>(m, k, draws, table, bits, picks);
+        CDMD_CHECK_LAUNCH("rowsample_floyd_kernel");
+        rank_sort_kernel<<<static_cast<unsigned>((k + 255) / 256), 256, 0, stream>>>(picks, k, meas->rows);
+        CDMD_CHECK_LAUNCH("rank_sort_kernel");
         return CDMD_OK;
     }
     // SPARSE: count -> scan -> fill
@@ -237,6 +306,7 @@ cdmd_status launch_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, cudaStream_t
 cdmd_status launch_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                                  const cdmd_measure* meas, double* DY, cudaStream_t stream) {
     const int k = meas->k;
+    if (meas->ctype == CDMD_C_SRFT) return launch_sketch_srft(ctx, D, m, n, ldd, meas, DY, stream);
     if (meas->ctype == CDMD_C_ROWSAMPLE) {
         const int64_t tot = static_cast<int64_t>(k) * n;
         rowsample_sketch_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, stream>>>(D, n, ldd, k, meas->rows, DY);

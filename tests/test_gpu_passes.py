@@ -70,9 +70,35 @@ def test_sparse_measurement_csc_matches_oracle(C, ctx):
 
 
 def test_rowsample_indices_match_oracle(C, ctx):
-    for m, k, seed in [(8_294_400, 1000, 3), (50, 50, 1), (1000, 7, 9)]:
+    # the last case keeps Floyd's set in global memory (2^15 slots > 96 KB)
+    for m, k, seed in [(8_294_400, 1000, 3), (50, 50, 1), (1000, 7, 9), (2, 1, 4), (20_000, 19_990, 8),
+                       (300_000, 12_000, 5)]:
         meas = C.Measure(ctx, "rowsample", m, k, seed)
         np.testing.assert_array_equal(meas.rows.cpu().numpy(), M.rowsample_indices(seed, k, m))
+
+
+def test_rowsample_build_is_graph_capturable(C, ctx):
+    """The single-pixel build runs on the device with no host round trip, so
+    it can be captured in a CUDA graph and replayed."""
+    m, k, seed = 8_294_400, 1000, 3
+    side = torch.cuda.Stream()
+    rows = torch.full((k,), -1, dtype=torch.int64, device="cuda")
+    st = C.cdmd_measure()
+    st.ctype, st.k, st.m, st.seed, st.density = C.CTYPES["rowsample"], k, m, seed, 0.0
+    st.rows = rows.data_ptr()
+    with torch.cuda.stream(side):
+        C._check(ctx.lib.cdmd_measure_build(ctx.handle, C.ctypes.byref(st), C._stream(side)))   # sizes the workspace
+    side.synchronize()
+    rows.fill_(-1)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        C._check(ctx.lib.cdmd_measure_build(ctx.handle, C.ctypes.byref(st), C._stream(side)))
+    torch.cuda.synchronize()
+    rows.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(rows.cpu().numpy(), M.rowsample_indices(seed, k, m))
 
 
 # --------------------------------------------------------------------- sketch
