@@ -455,7 +455,7 @@ def run_study(args):
     density = float(np.log(m) / m)      # sparsity factor s = m / log(m) (Section 4, evaluation settings)
     rng = np.random.default_rng(7)
     rows = []
-    for ctype in ("gaussian", "sparse", "rowsample"):
+    for ctype in ("gaussian", "sparse", "rowsample", "srft"):
         for p in S["p"]:
             r_max = min(32, p, n - 1)
             times, fs, ranks, build_ms = [], [], [], []
@@ -496,12 +496,13 @@ def run_study(args):
                          "F_min": float(np.min(fs)), "F_max": float(np.max(fs)),
                          "rank_median": float(np.median(ranks)),
                          "build_ms": float(np.median(build_ms)) if build_ms else None})
-    line = {"study": "measurement matrices (Gaussian, sparse, single pixel) against the number of samples p",
+    line = {"study": ("measurement matrices (Gaussian, sparse, single pixel, SRFT) against the number of "
+                      "samples p"),
             "workload": f"synthetic {S['width']}x{S['height']}x{S['n']}, seed {S['clip_seed']}",
             "timing": ("CUDA events around sketch + decompose + lift (mask excluded), median over "
                        f"{S['seeds']} draws of C after one warm-up draw; the Gaussian C is drawn in the sketch "
-                       "kernel, sparse and single-pixel C are built on the device beforehand (build_ms, host "
-                       "timed, not in ms)"),
+                       "kernel, sparse and single-pixel C and the SRFT's kept frequencies are built on the device "
+                       "beforehand (build_ms, host timed, not in ms); the SRFT sketch is an FFT pass"),
             "sparse_density": density, "precision": args.prec, "selector": "omp", "rank": "automatic",
             "K": S["K"], "tau": S["tau"], "draws_of_C": S["seeds"], "bootstrap": S["boot"], "rows": rows}
     print(json.dumps(line), flush=True)

@@ -75,12 +75,24 @@ typedef enum {
  *               smallest selected pixel): for t = m-k .. m-1 the draw is
  *               v = floor(((w1 << 32) | w0) * (t+1) / 2^64) from words 0,1 of
  *               counter (t, 0, 3, 0); v is taken unless already taken, else t.
+ *   SRFT        subsampled randomized Fourier transform C = R F D (Section
+ *               3.3, after Woolfe et al.): D = diag(exp(i theta_j)) with
+ *               theta_j = 2 pi U(w0), w0 word 0 of counter (j, 0, 5, 0); F the
+ *               unnormalised m-point DFT, F(f, j) = exp(-2 pi i f j / m); R
+ *               keeps q = ceil(k/2) distinct frequencies s_0 < s_1 < ... drawn
+ *               from [0, m) by Floyd's sampling as for ROWSAMPLE but on
+ *               counters (t, 0, 6, 0).  The real sketch rows are the real and
+ *               imaginary parts of the kept complex measurements: row 2a =
+ *               Re(F D)[s_a, :], row 2a+1 = Im(F D)[s_a, :] (odd k: the last
+ *               frequency keeps its real row only).  Applied by an FFT, never
+ *               formed.
  * The key of every counter is (seed & 0xffffffff, seed >> 32). */
 typedef enum {
     CDMD_C_GAUSSIAN = 0,
     CDMD_C_RADEMACHER = 1,
     CDMD_C_SPARSE = 2,
-    CDMD_C_ROWSAMPLE = 3
+    CDMD_C_ROWSAMPLE = 3,
+    CDMD_C_SRFT = 4
 } cdmd_ctype;
 
 /* Arithmetic of the two contractions (sketch and lift).
@@ -114,10 +126,11 @@ typedef enum { CDMD_SEL_OMP = 0, CDMD_SEL_LSTSQ = 1, CDMD_SEL_MLP = 2 } cdmd_sel
 
 typedef struct cdmd_ctx cdmd_ctx;
 
-/* Gather-form measurement matrix, device arrays owned by the caller.
+/* Gather / transform measurement matrix, device arrays owned by the caller.
  *   SPARSE     CSC by pixel: col_ptr[m+1] (int64), row_idx[nnz] (int32):
  *              bits 0..30 = row i, bit 31 set = entry -1 (clear = +1).
  *   ROWSAMPLE  rows[k] (int64): the selected pixel of row i, increasing.
+ *   SRFT       rows[ceil(k/2)] (int64): the kept frequencies, increasing.
  * cdmd_measure_build fills it; its capacity fields say how large the caller's
  * arrays are. */
 typedef struct {
@@ -190,10 +203,13 @@ cdmd_status cdmd_selftest_recip(cdmd_ctx* ctx, const double* a, int64_t n, doubl
 cdmd_status cdmd_measure_sparse_nnz(cdmd_ctx* ctx, int64_t m, int k, uint64_t seed,
                                     double density, int64_t* nnz, void* stream);
 
-/* Fill a SPARSE or ROWSAMPLE cdmd_measure (fields ctype, k, m, seed, density
- * and the arrays must be set).  Enqueued on `stream`.  ROWSAMPLE needs
- * 1 <= k <= m; SPARSE needs 0 < density <= 1 and nnz_capacity >= the count
- * from cdmd_measure_sparse_nnz (else CDMD_ERR_INVALID_ARG). */
+/* Fill a SPARSE, ROWSAMPLE or SRFT cdmd_measure (fields ctype, k, m, seed,
+ * density and the arrays must be set).  Enqueued on `stream`; ROWSAMPLE and
+ * SRFT are drawn on the device with no host round trip (graph-capturable
+ * once the context's workspace has been sized by a first call).  ROWSAMPLE
+ * needs 1 <= k <= m; SRFT needs ceil(k/2) <= m and k <= 8192; SPARSE needs
+ * 0 < density <= 1 and nnz_capacity >= the count from
+ * cdmd_measure_sparse_nnz (else CDMD_ERR_INVALID_ARG). */
 cdmd_status cdmd_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, void* stream);
 
 /* ---- pass (a): sketch  DY = C D  (Algorithm 1 steps 2-3, Eq. YCX) -------- */
@@ -230,8 +246,13 @@ cdmd_status cdmd_sketch_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* 
                                uint64_t seed, cdmd_prec prec, double* const* DY, void* stream);
 
 /* Sparse or single-pixel C applied as a gather (one pass over D; exact
- * integer sums).  meas must have been filled by cdmd_measure_build for the
- * same m.  DY as for cdmd_sketch with k = meas->k. */
+ * integer sums), or SRFT C applied by a fast transform (one pass over D: an
+ * FFT of length N2 down the N1 strided columns of each frame, m = N1 N2 with
+ * N2 the largest divisor of m up to 1024 whose prime factors are 2, 3 and 5,
+ * then one twiddled sum over the columns per kept frequency; FP32 arithmetic,
+ * FP64 sums of the column-group partials).  meas must have been filled by
+ * cdmd_measure_build for the same m.  DY as for cdmd_sketch with
+ * k = meas->k. */
 cdmd_status cdmd_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                                const cdmd_measure* meas, double* DY, void* stream);
 

@@ -171,14 +171,16 @@ def srft_phases(seed, cols):
 def srft_block(seed, rows, cols, m, k):
     """C[rows][:, cols] of the real SRFT sketch (k rows, m pixels), FP64.
 
-    The phase 2 pi s j / m is reduced exactly in integers (s j mod m) before
-    the angle is formed."""
+    The phase 2 pi s j / m is reduced exactly in integers (s j mod m, exact
+    in int64 for m < 2^31) before the angle is formed."""
+    if not 0 < m < 2 ** 31:
+        raise ValueError("need 0 < m < 2^31")
     rows = np.asarray(rows, dtype=np.int64)
     cols = np.asarray(cols, dtype=np.int64)
     freqs = srft_frequencies(seed, k, m)
     theta = srft_phases(seed, cols)
     s = freqs[rows // 2]
-    red = (s[:, None].astype(object) * cols[None, :].astype(object)) % int(m)
+    red = (s[:, None] * cols[None, :]) % np.int64(m)
     ang = theta[None, :] - 2.0 * np.pi * red.astype(np.float64) / float(m)
     return np.where((rows % 2 == 0)[:, None], np.cos(ang), np.sin(ang))
 

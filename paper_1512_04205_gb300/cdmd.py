@@ -25,7 +25,7 @@ CDMD_OK = 0
 STATUS_NAMES = {0: "CDMD_OK", 1: "CDMD_ERR_INVALID_ARG", 2: "CDMD_ERR_CUDA", 3: "CDMD_ERR_NOMEM",
                 4: "CDMD_ERR_NOT_CONVERGED", 5: "CDMD_ERR_RANK_DEFICIENT", 6: "CDMD_ERR_NONFINITE",
                 7: "CDMD_ERR_UNSUPPORTED", 8: "CDMD_ERR_TIMEOUT"}
-CTYPES = {"gaussian": 0, "rademacher": 1, "sparse": 2, "rowsample": 3}
+CTYPES = {"gaussian": 0, "rademacher": 1, "sparse": 2, "rowsample": 3, "srft": 4}
 PRECS = {"fp32": 0, "bf16x2": 1}
 BGMODES = {"modulus": 0, "real": 1, "static": 2}
 SELECTORS = {"omp": 0, "lstsq": 1, "mlp": 2}
@@ -269,7 +269,7 @@ def cdmd_sketch_noalloc(D, k, seed, ctype="gaussian", DY=None, stream=None):
 
 
 class Measure:
-    """Device-resident SPARSE or ROWSAMPLE measurement matrix."""
+    """Device-resident SPARSE, ROWSAMPLE or SRFT measurement matrix."""
 
     def __init__(self, ctx, ctype, m, k, seed, density=0.0, stream=None):
         import torch
@@ -289,8 +289,11 @@ class Measure:
         elif ctype == "rowsample":
             self.rows = torch.empty(int(k), dtype=torch.int64, device=dev)
             s.rows = self.rows.data_ptr()
+        elif ctype == "srft":
+            self.rows = torch.empty((int(k) + 1) // 2, dtype=torch.int64, device=dev)   # kept frequencies
+            s.rows = self.rows.data_ptr()
         else:
-            raise ValueError("Measure holds SPARSE or ROWSAMPLE matrices")
+            raise ValueError("Measure holds SPARSE, ROWSAMPLE or SRFT matrices")
         _check(ctx.lib.cdmd_measure_build(ctx.handle, ctypes.byref(s), _stream(stream)))
 
 

@@ -213,6 +213,10 @@ cdmd_status cdmd_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, void* stream) 
     if (meas->ctype == CDMD_C_ROWSAMPLE) {
         CDMD_REQUIRE(meas->k <= meas->m, "ROWSAMPLE needs k <= m");
         CDMD_REQUIRE(meas->rows != nullptr, "meas->rows is NULL");
+    } else if (meas->ctype == CDMD_C_SRFT) {
+        CDMD_REQUIRE((static_cast<int64_t>(meas->k) + 1) / 2 <= meas->m, "SRFT needs ceil(k/2) <= m");
+        CDMD_REQUIRE(meas->k <= 8192, "SRFT supports k <= 8192");
+        CDMD_REQUIRE(meas->rows != nullptr, "meas->rows is NULL");
     } else if (meas->ctype == CDMD_C_SPARSE) {
         CDMD_REQUIRE(meas->density > 0.0 && meas->density <= 1.0, "density must be in (0, 1]");
         CDMD_REQUIRE(meas->col_ptr != nullptr && meas->row_idx != nullptr, "CSC arrays are NULL");
@@ -223,7 +227,7 @@ cdmd_status cdmd_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, void* stream) 
         CDMD_REQUIRE(meas->nnz_capacity >= nnz, "nnz_capacity %lld < nnz %lld", static_cast<long long>(meas->nnz_capacity),
                      static_cast<long long>(nnz));
     } else {
-        return fail(CDMD_ERR_INVALID_ARG, "cdmd_measure_build takes SPARSE or ROWSAMPLE");
+        return fail(CDMD_ERR_INVALID_ARG, "cdmd_measure_build takes SPARSE, ROWSAMPLE or SRFT");
     }
     return launch_measure_build(ctx, meas, static_cast<cudaStream_t>(stream));
 }
@@ -284,7 +288,8 @@ cdmd_status cdmd_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n
     CDMD_REQUIRE(DY != nullptr, "DY is NULL");
     CDMD_REQUIRE(meas->m == m, "meas was built for m = %lld, video has m = %lld", static_cast<long long>(meas->m),
                  static_cast<long long>(m));
-    CDMD_REQUIRE(meas->ctype == CDMD_C_SPARSE || meas->ctype == CDMD_C_ROWSAMPLE, "meas must be SPARSE or ROWSAMPLE");
+    CDMD_REQUIRE(meas->ctype == CDMD_C_SPARSE || meas->ctype == CDMD_C_ROWSAMPLE || meas->ctype == CDMD_C_SRFT,
+                 "meas must be SPARSE, ROWSAMPLE or SRFT");
     if (meas->ctype == CDMD_C_SPARSE) {
         CDMD_REQUIRE(meas->col_ptr && meas->row_idx, "CSC arrays are NULL");
         CDMD_REQUIRE(static_cast<size_t>(meas->k) * 16 * sizeof(int32_t) <= 200 * 1024,

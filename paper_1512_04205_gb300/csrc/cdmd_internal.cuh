@@ -290,6 +290,8 @@ cdmd_status launch_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int
 cdmd_status launch_measure_sparse_count(cdmd_ctx* ctx, int64_t m, int k, uint64_t seed,
                                         double density, int64_t* d_counts, cudaStream_t stream);
 cdmd_status launch_measure_build(cdmd_ctx* ctx, cdmd_measure* meas, cudaStream_t stream);
+cdmd_status launch_sketch_srft(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
+                               const cdmd_measure* meas, double* DY, cudaStream_t stream);
 cdmd_status launch_decompose(cdmd_ctx* ctx, const double* DY, int k, int n, int r, int K,
                              cdmd_selector selector, double* sigma, double* lambda, double* G,
                              double* PhiY, double* beta, int32_t* sel, int32_t* nsel,
