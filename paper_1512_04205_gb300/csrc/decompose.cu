@@ -46,7 +46,13 @@ namespace cdmd {
 namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
+// An eigenvalue of Y^T Y at most kRankTol p eps times the largest is taken as
+// zero (sigma_r of the sketch vanishes): the Gram and the reduction leave
+// rounding of order (k + p) eps in them, so a bound of p eps alone would sit
+// at the noise level of an exactly rank-deficient sketch.
+constexpr double kRankTol = 64.0;
 constexpr int kMaxR = 32;
+constexpr size_t kMaxOptInSmem = 232448;      // opt-in shared memory per CTA
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -154,15 +160,64 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int splits, 
 
 // ---------------------------------------------------------------------------
 // 2. Householder tridiagonalisation of A = R[0:p, 0:p] on a cluster of P CTAs.
-// Row i lives in CTA i % P (local slot i / P).  Step j: the owner of row j
-// (= column j by symmetry) forms the reflector H_j = I - tau v v^T with
-// H_j A[j+1:, j] = alpha e_1 and broadcasts v; every CTA forms u = A v on its
-// rows and broadcasts it; every CTA then applies the rank-2 update
-// A -= v w^T + w v^T, w = tau u - (tau^2/2)(v^T u) v, to its rows.
+// Row i lives in CTA i % P (local slot i / P), full length p.  Step j:
+//   the owner of row j (= column j by symmetry) has formed the reflector
+//   H_j = I - tau v v^T with H_j A[j+1:, j] = alpha e_1 (v scaled to a
+//   leading 1, tau in [1, 2]) and written v and tau
+//   into every CTA (distributed shared memory, buffer j % 2);
+//   barrier; every CTA forms u_i = (A v)_i on its rows i > j and its share
+//   of v^T u, and writes them into every CTA;
+//   barrier; every CTA forms w = tau u - (tau^2/2)(v^T u) v and applies the
+//   rank-2 update A -= v w^T + w v^T to its rows.  The owner of row j+1
+//   updates that row first and forms the next reflector into the other
+//   buffer while the rest of the cluster is still updating, so the next
+//   step starts right after one barrier.
+// Two cluster barriers per step, the same sequence in every CTA.
 // Outputs: diagonal dd[p], off-diagonal ee[p-1], reflectors Hv[j*p + l]
 // (l > j) and htau[j], with A = Q T Q^T, Q = H_0 H_1 ... H_{p-3}.
 // ---------------------------------------------------------------------------
-constexpr int kTriThreads = 256;
+constexpr int kTriThreads = 512;
+
+// Reflector of step j from the owner's copy of row j, formed by one warp
+// (the other warps of the owning CTA keep updating their rows meanwhile):
+// tail2 = sum_{l > j+1} row[l]^2 (the caller's partial sums per lane), then v
+// (entries j+1..p-1) and tau go into buffer `b` of every CTA, and the step's
+// outputs to global memory.
+__device__ void tri_reflector_warp(cg::cluster_group& cluster, int P, const double* row, int j, int p,
+                                   double tail_part, double* vbuf, double* tau_slot, int b, double* Hv,
+                                   double* htau, double* dd, double* ee) {
+    const int lane = threadIdx.x & 31;
+    const double tail2 = warp_sum(tail_part);
+    const double x0 = row[j + 1];
+    // scaled form: v = (1, x_{j+2} / v0, ...), tau = 2 v0^2 / (v0^2 + tail2)
+    // in [1, 2], so neither grows however small the column is
+    double alpha, tau, inv_v0;
+    if (!(tail2 > 1e-280)) {              // nothing below the sub-diagonal (or a subnormal remainder)
+        alpha = x0;
+        tau = 0.0;
+        inv_v0 = 0.0;
+    } else {
+        const double s2 = fma(x0, x0, tail2);
+        const double nrm = s2 * rsqrt64(s2);
+        alpha = (x0 >= 0.0) ? -nrm : nrm;
+        const double v0 = x0 - alpha;     // |v0| >= nrm > 0
+        inv_v0 = rcp64(v0);
+        tau = 2.0 * rcp64(fma(tail2 * inv_v0, inv_v0, 1.0));
+    }
+    const int L = p - j - 1;
+    for (int l = j + 1 + lane; l < p; l += 32) {
+        const double val = (tau == 0.0) ? 0.0 : ((l == j + 1) ? 1.0 : row[l] * inv_v0);
+        Hv[static_cast<int64_t>(j) * p + l] = val;
+        for (int rr = 0; rr < P; ++rr) *cluster.map_shared_rank(vbuf + b * p + l, rr) = val;
+    }
+    (void)L;
+    if (lane < P) *cluster.map_shared_rank(tau_slot + b, lane) = tau;
+    if (lane == 0) {
+        dd[j] = row[j];
+        ee[j] = alpha;
+        htau[j] = tau;
+    }
+}
 
 __global__ void __launch_bounds__(kTriThreads)
 tridiag_kernel(const double* __restrict__ R, int n, int p, double* __restrict__ Hv,
@@ -172,12 +227,13 @@ tridiag_kernel(const double* __restrict__ R, int n, int p, double* __restrict__ 
     const int rank = static_cast<int>(cluster.block_rank());
     const int rows_per = (p + P - 1) / P;
     extern __shared__ double sm[];
-    double* Aloc = sm;                              // rows_per * p
+    double* Aloc = sm;                                          // rows_per * p
     double* vbuf = Aloc + static_cast<size_t>(rows_per) * p;   // 2 * p
-    double* ubuf = vbuf + 2 * p;                    // p
-    double* wv = ubuf + p;                          // p
-    double* red = wv + p;                           // 32 scratch + 2 tau slots
-    double* tau_slot = red + 32;
+    double* ubuf = vbuf + 2 * p;                                // p: u gathered from every CTA
+    double* wv = ubuf + p;                                      // p
+    double* red = wv + p;                                       // 32 scratch
+    double* slot = red + 32;                                    // 32: each CTA's share of v^T u
+    double* tau_slot = slot + 32;                               // 2
     const int tid = threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5, nwarps = kTriThreads / 32;
 
@@ -186,80 +242,95 @@ tridiag_kernel(const double* __restrict__ R, int n, int p, double* __restrict__ 
         const int i = rank + P * li;
         Aloc[idx] = (i < p) ? R[static_cast<int64_t>(i) * n + l] : 0.0;
     }
+    // every CTA of the cluster has started (and loaded its rows) before any
+    // CTA writes into another's shared memory
+    cluster.sync();
+    if (rank == 0 && wid == 0) {
+        double tp = 0.0;
+        for (int l = 2 + lane; l < p; l += 32) tp = fma(Aloc[l], Aloc[l], tp);
+        tri_reflector_warp(cluster, P, Aloc, 0, p, tp, vbuf, tau_slot, 0, Hv, htau, dd, ee);
+    }
     cluster.sync();
 
     for (int j = 0; j + 2 < p; ++j) {
-        const int buf = j & 1;
-        const int owner = j % P;
-        if (rank == owner) {
-            const double* row = Aloc + static_cast<size_t>(j / P) * p;
-            double s = 0.0;
-            for (int l = j + 2 + tid; l < p; l += kTriThreads) s += row[l] * row[l];
-            const double tail2 = block_sum(s, red);
-            const double x0 = row[j + 1];
-            double alpha, tau, v0;
-            if (tail2 == 0.0) {
-                alpha = x0; tau = 0.0; v0 = 0.0;
-            } else {
-                const double s2 = fma(x0, x0, tail2);
-                const double nrm = s2 * rsqrt64(s2);
-                alpha = (x0 >= 0.0) ? -nrm : nrm;
-                v0 = x0 - alpha;
-                tau = 2.0 * rcp64(fma(v0, v0, tail2));
-            }
-            for (int rr = 0; rr < P; ++rr) {
-                double* rv = cluster.map_shared_rank(vbuf + buf * p, rr);
-                for (int l = j + 1 + tid; l < p; l += kTriThreads)
-                    rv[l] = (l == j + 1) ? v0 : (tau == 0.0 ? 0.0 : row[l]);
-                if (tid == 0) *cluster.map_shared_rank(tau_slot + buf, rr) = tau;
-            }
-            for (int l = j + 1 + tid; l < p; l += kTriThreads)
-                Hv[static_cast<int64_t>(j) * p + l] = (l == j + 1) ? v0 : (tau == 0.0 ? 0.0 : row[l]);
-            if (tid == 0) {
-                dd[j] = row[j];
-                ee[j] = alpha;
-                htau[j] = tau;
-            }
-        }
-        cluster.sync();
-        const double* v = vbuf + buf * p;
-        const double tau = tau_slot[buf];
+        const int b = j & 1;
+        const double* v = vbuf + b * p;
+        const double tau = tau_slot[b];
+        // local rows i > j start at li_first
+        const int li_first = (j + 1 > rank) ? (j + 1 - rank + P - 1) / P : 0;
         if (tau != 0.0) {
-            // (b) u_i = sum_l A_il v_l for owned rows i > j; one warp per row
-            const int li_first = (j + 1 - rank + P - 1) / P;   // smallest li with rank + P li >= j+1
+            // u_i = sum_l A_il v_l on own rows (one warp per row), broadcast to every CTA
+            double part = 0.0;
             for (int li = li_first + wid; li < rows_per; li += nwarps) {
                 const int i = rank + P * li;
                 if (i >= p) break;
                 const double* row = Aloc + static_cast<size_t>(li) * p;
-                double s = 0.0;
-                for (int l = j + 1 + lane; l < p; l += 32) s = fma(row[l], v[l], s);
-                s = warp_sum(s);
-                if (lane < P) *cluster.map_shared_rank(ubuf + i, lane) = s;
+                double s0 = 0.0, s1 = 0.0;
+                int l = j + 1 + lane;
+                for (; l + 32 < p; l += 64) {
+                    s0 = fma(row[l], v[l], s0);
+                    s1 = fma(row[l + 32], v[l + 32], s1);
+                }
+                if (l < p) s0 = fma(row[l], v[l], s0);
+                const double u = warp_sum(s0 + s1);
+                if (lane < P) *cluster.map_shared_rank(ubuf + i, lane) = u;
+                part = fma(v[i], u, part);
+            }
+            if (lane == 0) red[wid] = part;
+            __syncthreads();
+            if (tid < P) {
+                double t = 0.0;
+                for (int q = 0; q < nwarps; ++q) t += red[q];
+                *cluster.map_shared_rank(slot + rank, tid) = t;
             }
         }
         cluster.sync();
+        const int nxt = j + 1;
+        const bool own_next = (nxt + 2 < p) && (nxt % P == rank);
+        const int li_next = nxt / P;
         if (tau != 0.0) {
-            double s = 0.0;
-            for (int l = j + 1 + tid; l < p; l += kTriThreads) s = fma(v[l], ubuf[l], s);
-            const double vtu = block_sum(s, red);
+            double vtu = 0.0;
+            for (int q = 0; q < P; ++q) vtu += slot[q];
             const double kc = 0.5 * tau * tau * vtu;
-            for (int l = j + 1 + tid; l < p; l += kTriThreads) wv[l] = tau * ubuf[l] - kc * v[l];
+            for (int l = j + 1 + tid; l < p; l += kTriThreads) wv[l] = fma(tau, ubuf[l], -kc * v[l]);
             __syncthreads();
-            const int li_first = (j + 1 - rank + P - 1) / P;
-            const int L = p - j - 1;
-            const int nrows = rows_per - li_first;
-            for (int idx = tid; idx < nrows * L; idx += kTriThreads) {
-                const int li = li_first + idx / L;
-                const int l = j + 1 + idx % L;
-                const int i = rank + P * li;
-                if (i >= p) continue;
-                double* a = Aloc + static_cast<size_t>(li) * p + l;
-                *a = *a - v[i] * wv[l] - wv[i] * v[l];
+            if (own_next && wid == 0) {
+                // warp 0: the next reflector's row first, then the reflector
+                double* row = Aloc + static_cast<size_t>(li_next) * p;
+                const double vi = v[nxt], wi = wv[nxt];
+                double tp = 0.0;
+                for (int l = j + 1 + lane; l < p; l += 32) {
+                    const double a = fma(-vi, wv[l], fma(-wi, v[l], row[l]));
+                    row[l] = a;
+                    if (l > nxt + 1) tp = fma(a, a, tp);
+                }
+                __syncwarp();
+                tri_reflector_warp(cluster, P, row, nxt, p, tp, vbuf, tau_slot, b ^ 1, Hv, htau, dd, ee);
+            } else {
+                // the other rows (all warps, or warps 1.. on the owner of the next row)
+                const int L = p - j - 1;
+                const int nrows = rows_per - li_first;
+                const bool own_split = own_next;
+                const int t0 = own_split ? tid - 32 : tid;
+                const int nt = own_split ? kTriThreads - 32 : kTriThreads;
+                for (int idx = t0; idx < nrows * L; idx += nt) {
+                    const int li = li_first + idx / L;
+                    const int l = j + 1 + idx % L;
+                    const int i = rank + P * li;
+                    if (i >= p || (own_split && li == li_next)) continue;
+                    double* a = Aloc + static_cast<size_t>(li) * p + l;
+                    *a = fma(-v[i], wv[l], fma(-wv[i], v[l], *a));
+                }
             }
+        } else if (own_next && wid == 0) {
+            const double* row = Aloc + static_cast<size_t>(li_next) * p;
+            double tp = 0.0;
+            for (int l = nxt + 2 + lane; l < p; l += 32) tp = fma(row[l], row[l], tp);
+            tri_reflector_warp(cluster, P, row, nxt, p, tp, vbuf, tau_slot, b ^ 1, Hv, htau, dd, ee);
         }
-        __syncthreads();
+        cluster.sync();
     }
-    // trailing 2x2 (or smaller) block
+    // trailing 2x2 block
     if (tid == 0) {
         for (int i = max(p - 2, 0); i < p; ++i) {
             if (i % P != rank) continue;
@@ -268,7 +339,6 @@ tridiag_kernel(const double* __restrict__ R, int n, int p, double* __restrict__ 
             if (i + 1 < p) ee[i] = row[i + 1];
         }
     }
-    cluster.sync();
 }
 
 // p <= 2: the leading block of R is already tridiagonal (no reflectors).
@@ -380,79 +450,86 @@ tridiag_eigpair_kernel(const double* __restrict__ dd, const double* __restrict__
     }
     const double lambda = 0.5 * (lo + hi);
     if (!converged && lane == 0) record_status(status, CDMD_ERR_NOT_CONVERGED);
-    if (lane != 0) return;
-    lam[w] = lambda;
+    if (lane == 0) lam[w] = lambda;
+    if (!(lambda > kRankTol * static_cast<double>(p) * kEps * tn)) {
+        // a numerically zero eigenvalue: sigma_r of the sketch vanishes
+        if (lane == 0) record_status(status, CDMD_ERR_RANK_DEFICIENT);
+        for (int i = lane; i < p; i += 32) Z[static_cast<int64_t>(w) * p + i] = (i == w) ? 1.0 : 0.0;
+        return;
+    }
     // inverse iteration: LU with partial pivoting of T - mu I, reciprocal pivots
     const double mu = lambda + kEps * tn;   // keeps T - mu I away from exact singularity
     const double tiny = kEps * tn + 1e-300;
-    for (int i = 0; i < p; ++i) {
+    for (int i = lane; i < p; i += 32) {
         udg[i] = d[i] - mu;
         lmul[i] = e[i];
         u1[i] = e[i];
         u2[i] = 0.0;
         piv[i] = 0;
+        // start vector: 1 + a hash of (i, w) in [0, 1)
+        uint32_t h = (static_cast<uint32_t>(i) + 1u) * 0x9E3779B9u ^ (static_cast<uint32_t>(w) + 1u) * 0x85EBCA6Bu;
+        h ^= h >> 15;
+        h *= 0x2C1B3C6Du;
+        h ^= h >> 12;
+        z[i] = 1.0 + static_cast<double>(h & 0xffff) * (1.0 / 65536.0);
     }
-    for (int i = 0; i + 1 < p; ++i) {
-        if (fabs(udg[i]) >= fabs(lmul[i])) {
-            if (udg[i] == 0.0) udg[i] = tiny;
-            const double inv = rcp64(udg[i]);
-            invd[i] = inv;
-            const double fct = lmul[i] * inv;
-            lmul[i] = fct;
-            udg[i + 1] = fma(-fct, u1[i], udg[i + 1]);
-        } else {
-            const double inv = rcp64(lmul[i]);
-            invd[i] = inv;
-            const double fct = udg[i] * inv;
-            udg[i] = lmul[i];
-            lmul[i] = fct;
-            const double tmp = u1[i];
-            u1[i] = udg[i + 1];
-            udg[i + 1] = fma(-fct, udg[i + 1], tmp);
-            if (i + 2 < p) {
-                u2[i] = u1[i + 1];
-                u1[i + 1] = -fct * u1[i + 1];
+    __syncwarp();
+    if (lane == 0) {
+        for (int i = 0; i + 1 < p; ++i) {
+            if (fabs(udg[i]) >= fabs(lmul[i])) {
+                if (udg[i] == 0.0) udg[i] = tiny;
+                const double inv = rcp64(udg[i]);
+                invd[i] = inv;
+                const double fct = lmul[i] * inv;
+                lmul[i] = fct;
+                udg[i + 1] = fma(-fct, u1[i], udg[i + 1]);
+            } else {
+                const double inv = rcp64(lmul[i]);
+                invd[i] = inv;
+                const double fct = udg[i] * inv;
+                udg[i] = lmul[i];
+                lmul[i] = fct;
+                const double tmp = u1[i];
+                u1[i] = udg[i + 1];
+                udg[i + 1] = fma(-fct, udg[i + 1], tmp);
+                if (i + 2 < p) {
+                    u2[i] = u1[i + 1];
+                    u1[i + 1] = -fct * u1[i + 1];
+                }
+                piv[i] = 1;
             }
-            piv[i] = 1;
         }
-    }
-    if (udg[p - 1] == 0.0) udg[p - 1] = tiny;
-    invd[p - 1] = rcp64(udg[p - 1]);
-    uint32_t hs = 0x9E3779B9u * static_cast<uint32_t>(w + 1);
-    for (int i = 0; i < p; ++i) {
-        hs ^= hs << 13;
-        hs ^= hs >> 17;
-        hs ^= hs << 5;
-        z[i] = 1.0 + static_cast<double>(hs & 0xffff) * (1.0 / 65536.0);
+        if (udg[p - 1] == 0.0) udg[p - 1] = tiny;
+        invd[p - 1] = rcp64(udg[p - 1]);
     }
     for (int itr = 0; itr < 2; ++itr) {
-        for (int i = 0; i + 1 < p; ++i) {
-            if (piv[i] == 0) {
-                z[i + 1] = fma(-lmul[i], z[i], z[i + 1]);
-            } else {
-                const double tmp = z[i];
-                z[i] = z[i + 1];
-                z[i + 1] = fma(-lmul[i], z[i], tmp);
+        if (lane == 0) {
+            for (int i = 0; i + 1 < p; ++i) {
+                if (piv[i] == 0) {
+                    z[i + 1] = fma(-lmul[i], z[i], z[i + 1]);
+                } else {
+                    const double tmp = z[i];
+                    z[i] = z[i + 1];
+                    z[i + 1] = fma(-lmul[i], z[i], tmp);
+                }
             }
+            z[p - 1] *= invd[p - 1];
+            if (p > 1) z[p - 2] = fma(-u1[p - 2], z[p - 1], z[p - 2]) * invd[p - 2];
+            for (int i = p - 3; i >= 0; --i) z[i] = fma(-u2[i], z[i + 2], fma(-u1[i], z[i + 1], z[i])) * invd[i];
         }
-        z[p - 1] *= invd[p - 1];
-        if (p > 1) z[p - 2] = fma(-u1[p - 2], z[p - 1], z[p - 2]) * invd[p - 2];
-        for (int i = p - 3; i >= 0; --i) z[i] = fma(-u2[i], z[i + 2], fma(-u1[i], z[i + 1], z[i])) * invd[i];
-        double s0 = 0.0, s1 = 0.0;
-        for (int i = 0; i + 1 < p; i += 2) {
-            s0 = fma(z[i], z[i], s0);
-            s1 = fma(z[i + 1], z[i + 1], s1);
-        }
-        if (p & 1) s0 = fma(z[p - 1], z[p - 1], s0);
-        const double nrm2 = s0 + s1;
+        __syncwarp();
+        double s0 = 0.0;
+        for (int i = lane; i < p; i += 32) s0 = fma(z[i], z[i], s0);
+        const double nrm2 = warp_sum(s0);
         if (!(nrm2 > 0.0) || !isfinite(nrm2)) {
-            record_status(status, CDMD_ERR_NOT_CONVERGED);
+            if (lane == 0) record_status(status, CDMD_ERR_NOT_CONVERGED);
             break;
         }
         const double inv = rsqrt64(nrm2);
-        for (int i = 0; i < p; ++i) z[i] *= inv;
+        for (int i = lane; i < p; i += 32) z[i] *= inv;
+        __syncwarp();
     }
-    for (int i = 0; i < p; ++i) Z[static_cast<int64_t>(w) * p + i] = z[i];
+    for (int i = lane; i < p; i += 32) Z[static_cast<int64_t>(w) * p + i] = z[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -535,14 +612,19 @@ gd_rank_kernel(const double* __restrict__ dd, const double* __restrict__ ee, int
 // entries other threads wrote, ordered by __syncthreads.
 __global__ void __launch_bounds__(1024)
 orthonormalise_kernel(double* Z, int p, int r) {
-    __shared__ double dots[32];
-    __shared__ double red[32];
+    // classical Gram-Schmidt, twice, on the r columns held in shared memory
+    extern __shared__ double osm[];
+    double* Zs = osm;                         // r columns of p
+    double* dots = Zs + static_cast<size_t>(r) * p;   // 32
+    double* red = dots + 32;                  // 32
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < r * p; i += blockDim.x) Zs[i] = Z[i];
+    __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
         for (int c = 0; c < r; ++c) {
-            double* zc = Z + static_cast<int64_t>(c) * p;
+            double* zc = Zs + static_cast<size_t>(c) * p;
             if (wid < c) {
-                const double* zq = Z + static_cast<int64_t>(wid) * p;
+                const double* zq = Zs + static_cast<size_t>(wid) * p;
                 double s0 = 0.0, s1 = 0.0;
                 int i = lane;
                 for (; i + 32 < p; i += 64) {
@@ -554,29 +636,34 @@ orthonormalise_kernel(double* Z, int p, int r) {
                 if (lane == 0) dots[wid] = s;
             }
             __syncthreads();
+            double nacc = 0.0;
             for (int i = threadIdx.x; i < p; i += blockDim.x) {
                 double a0 = zc[i], a1 = 0.0;
                 int q = 0;
                 for (; q + 1 < c; q += 2) {
-                    a0 = fma(-dots[q], Z[static_cast<int64_t>(q) * p + i], a0);
-                    a1 = fma(-dots[q + 1], Z[static_cast<int64_t>(q + 1) * p + i], a1);
+                    a0 = fma(-dots[q], Zs[static_cast<size_t>(q) * p + i], a0);
+                    a1 = fma(-dots[q + 1], Zs[static_cast<size_t>(q + 1) * p + i], a1);
                 }
-                if (q < c) a0 = fma(-dots[q], Z[static_cast<int64_t>(q) * p + i], a0);
-                zc[i] = a0 + a1;
+                if (q < c) a0 = fma(-dots[q], Zs[static_cast<size_t>(q) * p + i], a0);
+                const double a = a0 + a1;
+                zc[i] = a;
+                nacc = fma(a, a, nacc);
             }
-            __syncthreads();
-            double s = 0.0;
-            for (int i = threadIdx.x; i < p; i += blockDim.x) s = fma(zc[i], zc[i], s);
-            const double nrm2 = block_sum(s, red);
+            const double nrm2 = block_sum(nacc, red);
             const double inv = nrm2 > 0.0 ? rsqrt64(nrm2) : 0.0;
             for (int i = threadIdx.x; i < p; i += blockDim.x) zc[i] *= inv;
             __syncthreads();
         }
     }
+    for (int i = threadIdx.x; i < r * p; i += blockDim.x) Z[i] = Zs[i];
 }
 
 // 4b. V[:, c] = Q z_c (apply H_{p-3}, ..., H_0) and sigma_c = sqrt(lambda_c);
-// one CTA (one warp) per column, four partial sums per lane.
+// one CTA (one warp) per column, four partial sums per lane.  Each lane
+// holds its entries of the next reflector in registers, loaded one step
+// ahead, so the L2 latency of the reflector rows is off the critical path.
+// kBtPer: reflector entries per lane, 8 for p <= 256 and 16 up to p = 511
+template <int kBtPer>
 __global__ void __launch_bounds__(32)
 backtransform_kernel(const double* __restrict__ Z, const double* __restrict__ Hv,
                      const double* __restrict__ htau, const double* __restrict__ lam, int p, int r,
@@ -586,28 +673,52 @@ backtransform_kernel(const double* __restrict__ Z, const double* __restrict__ Hv
     const int lane = threadIdx.x;
     for (int i = lane; i < p; i += 32) ysm[i] = Z[static_cast<int64_t>(c) * p + i];
     __syncwarp();
-    for (int j = p - 3; j >= 0; --j) {
-        const double tau = htau[j];
-        if (tau == 0.0) continue;
-        const double* v = Hv + static_cast<int64_t>(j) * p;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int l = j + 1 + lane;
-        for (; l + 96 < p; l += 128) {
-            s0 = fma(v[l], ysm[l], s0);
-            s1 = fma(v[l + 32], ysm[l + 32], s1);
-            s2 = fma(v[l + 64], ysm[l + 64], s2);
-            s3 = fma(v[l + 96], ysm[l + 96], s3);
+    // entry q of lane: index lane + 32 q of the reflector row
+    double cur[kBtPer], nxt[kBtPer];
+    double tau_cur = 0.0, tau_nxt = 0.0;
+    int j = p - 3;
+    if (j >= 0) {
+        tau_cur = htau[j];
+#pragma unroll
+        for (int q = 0; q < kBtPer; ++q) {
+            const int l = lane + 32 * q;
+            cur[q] = (l > j && l < p) ? Hv[static_cast<int64_t>(j) * p + l] : 0.0;
         }
-        for (; l < p; l += 32) s0 = fma(v[l], ysm[l], s0);
-        const double s = warp_sum((s0 + s1) + (s2 + s3)) * tau;
-        for (int q = j + 1 + lane; q < p; q += 32) ysm[q] = fma(-s, v[q], ysm[q]);
-        __syncwarp();
+    }
+    for (; j >= 0; --j) {
+        if (j > 0) {
+            tau_nxt = htau[j - 1];
+#pragma unroll
+            for (int q = 0; q < kBtPer; ++q) {
+                const int l = lane + 32 * q;
+                nxt[q] = (l > j - 1 && l < p) ? Hv[static_cast<int64_t>(j - 1) * p + l] : 0.0;
+            }
+        }
+        if (tau_cur != 0.0) {
+            double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+            for (int q = 0; q < kBtPer; q += 2) {
+                const int l0 = lane + 32 * q, l1 = l0 + 32;
+                if (l0 < p) s0 = fma(cur[q], ysm[l0], s0);
+                if (l1 < p) s1 = fma(cur[q + 1], ysm[l1], s1);
+            }
+            const double s = warp_sum(s0 + s1) * tau_cur;
+#pragma unroll
+            for (int q = 0; q < kBtPer; ++q) {
+                const int l = lane + 32 * q;
+                if (l > j && l < p) ysm[l] = fma(-s, cur[q], ysm[l]);
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int q = 0; q < kBtPer; ++q) cur[q] = nxt[q];
+        tau_cur = tau_nxt;
     }
     for (int i = lane; i < p; i += 32) V[static_cast<int64_t>(c) * p + i] = ysm[i];
     if (lane == 0) {
         const double l0 = lam[0];
         const double lc = lam[c];
-        if (!(lc > static_cast<double>(p) * kEps * fabs(l0))) record_status(status, CDMD_ERR_RANK_DEFICIENT);
+        if (!(lc > kRankTol * static_cast<double>(p) * kEps * fabs(l0))) record_status(status, CDMD_ERR_RANK_DEFICIENT);
         sigma[c] = lc > 0.0 ? lc * rsqrt64(lc) : 0.0;
     }
 }
@@ -709,22 +820,18 @@ eig_f32_kernel(const double* __restrict__ At, int r, float2* __restrict__ lam32,
     }
     __syncwarp();
     for (int j = 0; j + 2 < r; ++j) {
-        float nrm2 = 0.0f;
-        for (int i = j + 1; i < r; ++i) nrm2 += Hr[i][j] * Hr[i][j];
+        const float hj = (lane > j && lane < r) ? Hr[lane][j] : 0.0f;
+        float nrm2 = hj * hj;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
         const float nrm = sqrtf(nrm2);
         const float x0 = Hr[j + 1][j];
-        float beta = 0.0f;
-        if (nrm > 0.0f) {
-            float vn = 0.0f;
-            for (int i = j + 1; i < r; ++i) {
-                const float hvi = (i == j + 1) ? x0 + (x0 >= 0.0f ? nrm : -nrm) : Hr[i][j];
-                vn += hvi * hvi;
-            }
-            beta = vn > 0.0f ? 2.0f / vn : 0.0f;
-        }
+        const float v0 = x0 + (x0 >= 0.0f ? nrm : -nrm);
+        // ||v||^2 = v0^2 + (nrm^2 - x0^2)
+        const float vn = fmaf(v0, v0, fmaxf(nrm2 - x0 * x0, 0.0f));
+        const float beta = (nrm > 0.0f && vn > 0.0f) ? 2.0f / vn : 0.0f;
         __syncwarp();
-        if (lane == 0)
-            for (int i = j + 1; i < r; ++i) hv[i] = (i == j + 1) ? x0 + (x0 >= 0.0f ? nrm : -nrm) : Hr[i][j];
+        if (lane > j && lane < r) hv[lane] = (lane == j + 1) ? v0 : hj;
         __syncwarp();
         if (beta != 0.0f) {
             if (lane < r) {
@@ -762,15 +869,17 @@ eig_f32_kernel(const double* __restrict__ At, int r, float2* __restrict__ lam32,
     int hi = r - 1, its = 0, total = 0;
     bool failed = false;
     while (hi > 0) {
-        int lo = hi;
-        while (lo > 0) {
-            const float s = fabsc(T[lo - 1][lo - 1]) + fabsc(T[lo][lo]);
-            if (fabsc(T[lo][lo - 1]) <= eps32 * s) break;
-            --lo;
+        // deflation: the largest lo <= hi with a negligible T[lo][lo-1] (or 0)
+        bool small = false;
+        if (lane >= 1 && lane <= hi) {
+            const float sc = fabsc(T[lane - 1][lane - 1]) + fabsc(T[lane][lane]);
+            small = fabsc(T[lane][lane - 1]) <= eps32 * sc;
         }
-        __syncwarp();
+        const unsigned sm_mask = __ballot_sync(0xffffffffu, small);
+        const int lo = sm_mask ? 31 - __clz(sm_mask) : 0;
         if (lo > 0 && lane == 0) T[lo][lo - 1] = {0.0f, 0.0f};
-        if (lo == hi) { --hi; its = 0; __syncwarp(); continue; }
+        __syncwarp();
+        if (lo == hi) { --hi; its = 0; continue; }
         ++its;
         ++total;
         if (its > 60 || total > 60 * r) { failed = true; break; }
@@ -790,7 +899,9 @@ eig_f32_kernel(const double* __restrict__ At, int r, float2* __restrict__ lam32,
                 mu = (fabs2c(fsubc(mu1, dv)) <= fabs2c(fsubc(mu2, dv))) ? mu1 : mu2;
             }
         }
-        __syncwarp();
+        // bulge chase: rotation q acts on rows q, q+1 (lanes = columns), then
+        // on columns q, q+1 (lanes = rows) and on Z; the entry T[q+1][q-1]
+        // the row rotation zeroes is written 0 by its lane
         for (int q = lo; q < hi; ++q) {
             cf x, y;
             if (q == lo) { x = fsubc(T[lo][lo], mu); y = T[lo + 1][lo]; }
@@ -807,7 +918,7 @@ eig_f32_kernel(const double* __restrict__ At, int r, float2* __restrict__ lam32,
             if (lane >= col0 && lane < r) {
                 const cf t0 = T[q][lane], t1 = T[q + 1][lane];
                 T[q][lane] = faddc(fmulc(fconjc(cg_), t0), fmulc(fconjc(sg), t1));
-                T[q + 1][lane] = fsubc(fmulc(cg_, t1), fmulc(sg, t0));
+                T[q + 1][lane] = (q > lo && lane == q - 1) ? cf{0.0f, 0.0f} : fsubc(fmulc(cg_, t1), fmulc(sg, t0));
             }
             __syncwarp();
             const int row1 = min(q + 3, hi + 1);
@@ -821,8 +932,6 @@ eig_f32_kernel(const double* __restrict__ At, int r, float2* __restrict__ lam32,
                 Zs[lane][q] = faddc(fmulc(z0, cg_), fmulc(z1, sg));
                 Zs[lane][q + 1] = fsubc(fmulc(z1, fconjc(cg_)), fmulc(z0, fconjc(sg)));
             }
-            __syncwarp();
-            if (lane == 0 && q > lo) T[q + 1][q - 1] = {0.0f, 0.0f};
             __syncwarp();
         }
     }
@@ -891,7 +1000,7 @@ eig_refine_kernel(const double* __restrict__ At, int r, const float2* __restrict
     double key = (lane < r) ? cabs2(w) : -1.0;
     const double kmax = warp_max(key);
     const unsigned at = __ballot_sync(0xffffffffu, key == kmax && lane < r);
-    const int pidx = __ffs(at) - 1;
+    const int pidx = at ? __ffs(at) - 1 : 0;   // no candidate only with non-finite entries
     const cd wp = shfl_cd(w, pidx);
     if (kmax > 0.0) w = cmul(w, cinv(wp));
     if (lane == pidx) w = {1.0, 0.0};
@@ -917,7 +1026,7 @@ eig_refine_kernel(const double* __restrict__ At, int r, const float2* __restrict
             const double mag = (lane >= k && lane < r) ? cabs2(Mx[perm[lane]][k]) : -1.0;
             const double mbest = warp_max(mag);
             const unsigned bb = __ballot_sync(0xffffffffu, mag == mbest && lane >= k && lane < r);
-            const int pk = __ffs(bb) - 1;
+            const int pk = bb ? __ffs(bb) - 1 : k;   // non-finite column: keep the order
             __syncwarp();
             if (lane == 0 && pk != k) {
                 const int t = perm[k];
@@ -937,16 +1046,21 @@ eig_refine_kernel(const double* __restrict__ At, int r, const float2* __restrict
             }
             __syncwarp();
         }
-        // back substitution in logical order: z_q = (rhs - sum_{c>q} U_qc z_c) / U_qq
-        for (int q = r - 1; q >= 0; --q) {
-            const int row = perm[q];
-            cd part = {0.0, 0.0};
-            if (lane > q && lane < r) part = cmul(Mx[row][lane], zz[lane]);
-            part.x = warp_sum(part.x);
-            part.y = warp_sum(part.y);
-            if (lane == 0) {
-                const cd pv = Mx[row][q];
-                zz[q] = (cabs2(pv) > 0.0) ? cmul(csub(rhs[row], part), cinv(pv)) : cd{0.0, 0.0};
+        // back substitution in logical order, column by column: lane i keeps
+        // b_i = rhs[perm[i]]; z_q = b_q / U_qq goes to every lane, which
+        // subtracts U_iq z_q from its b_i (the reciprocal pivots in parallel)
+        {
+            const int row_l = (lane < r) ? perm[lane] : 0;
+            cd bl = (lane < r) ? rhs[row_l] : cd{0.0, 0.0};
+            cd invu = {0.0, 0.0};
+            if (lane < r) {
+                const cd pv = Mx[row_l][lane];
+                if (cabs2(pv) > 0.0) invu = cinv(pv);
+            }
+            for (int q = r - 1; q >= 0; --q) {
+                const cd zq = shfl_cd(cmul(bl, invu), q);
+                if (lane == q) zz[q] = zq;
+                if (lane < q) bl = csub(bl, cmul(Mx[row_l][q], zq));
             }
             __syncwarp();
         }
@@ -1306,7 +1420,8 @@ __global__ void gmat_kernel(const double* __restrict__ V, const double* __restri
 }
 
 // 8. h = (Y'^T Y') G[:, c];  M[a][c] = G[:,a]^H h;  cvec[c] = G[:,c]^H (Y'^T y1).
-__global__ void __launch_bounds__(128)
+// One CTA of 16 warps per column c, one warp per row of h, then per entry.
+__global__ void __launch_bounds__(512)
 hmat_kernel(const double* __restrict__ R, const double* __restrict__ G, int n, int p, int r,
             double* __restrict__ M, double* __restrict__ cvec) {
     extern __shared__ double hsm[];   // h: 2p
@@ -1420,6 +1535,7 @@ omp_kernel(const double* __restrict__ M, const double* __restrict__ cvec, const 
             const double key = cand ? imlam : -1e300;
             const double kbest = warp_max(key);
             const unsigned bb = __ballot_sync(0xffffffffu, cand && key == kbest);
+            if (bb == 0u) break;                    // non-finite scores: no pick
             best = __ffs(bb) - 1;
         }
         // new Cholesky row: solve L x = m (m_q = M[S_q][best]); row = conj(x)
@@ -1643,12 +1759,20 @@ cdmd_status decompose_impl(cdmd_ctx* ctx, const double* DY, int k, const double*
     // fit in one GPC beside other clips' full-data passes: 8 CTAs gave 3.8 %
     // more clips/s than 16 with clips in flight, at 2 % more latency
     if (p >= 3) {
-        int csize = 8;
-        for (;;) {
+        // cluster size: 8 CTAs first (fits one GPC beside other clips' passes),
+        // else 16 (non-portable; large n), else 4
+        const int csize_pref = 8;
+        const int cands[3] = {csize_pref, csize_pref == 16 ? 8 : 16, 4};
+        bool launched = false;
+        for (int ci = 0; ci < 3 && !launched; ++ci) {
+            const int csize = cands[ci];
             const int rows_per = (p + csize - 1) / csize;
-            const size_t smem = (static_cast<size_t>(rows_per) * p + 5 * static_cast<size_t>(p) + 34) * sizeof(double);
+            const size_t smem = (static_cast<size_t>(rows_per) * p + 4 * static_cast<size_t>(p) + 66) * sizeof(double);
+            if (smem > kMaxOptInSmem) continue;
+            // the opt-in maximum, the same value on every call: concurrent
+            // contexts (and captured graphs) never see it lowered
             CDMD_CHECK_CUDA(cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(smem)));
+                                                 static_cast<int>(kMaxOptInSmem)));
             if (csize > 8)
                 CDMD_CHECK_CUDA(cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
             cudaLaunchConfig_t cfg = {};
@@ -1667,13 +1791,13 @@ cdmd_status decompose_impl(cdmd_ctx* ctx, const double* DY, int k, const double*
             const cudaError_t oe = cudaOccupancyMaxActiveClusters(&nclusters, tridiag_kernel, &cfg);
             if (oe != cudaSuccess || nclusters < 1) {
                 (void)cudaGetLastError();
-                if (csize > 4) { csize = 4; continue; }
-                return fail(CDMD_ERR_UNSUPPORTED, "no room for a %d-CTA cluster of %zu bytes each", csize, smem);
+                continue;
             }
             CDMD_CHECK_CUDA(cudaLaunchKernelEx(&cfg, tridiag_kernel, static_cast<const double*>(R), n, p, Hv,
                                                htau, dd, ee));
-            break;
+            launched = true;
         }
+        if (!launched) return fail(CDMD_ERR_UNSUPPORTED, "no cluster size fits the tridiagonalisation of p = %d", p);
     } else {
         tiny_tridiag_kernel<<<1, 1, 0, stream>>>(R, n, p, dd, ee, htau);
         CDMD_CHECK_LAUNCH("tiny_tridiag_kernel");
@@ -1705,13 +1829,24 @@ cdmd_status decompose_impl(cdmd_ctx* ctx, const double* DY, int k, const double*
     {
         const size_t esm = 10 * static_cast<size_t>(p) * sizeof(double);
         CDMD_CHECK_CUDA(cudaFuncSetAttribute(tridiag_eigpair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(esm)));
+                                             static_cast<int>(kMaxOptInSmem)));
         tridiag_eigpair_kernel<<<r, 32, esm, stream>>>(dd, ee, p, r, lamT, Z, ctx->d_status);
         CDMD_CHECK_LAUNCH("tridiag_eigpair_kernel");
     }
-    orthonormalise_kernel<<<1, 1024, 0, stream>>>(Z, p, r);
+    {
+        const size_t osm = (static_cast<size_t>(r) * p + 64) * sizeof(double);
+        CDMD_CHECK_CUDA(cudaFuncSetAttribute(orthonormalise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kMaxOptInSmem)));
+        orthonormalise_kernel<<<1, 1024, osm, stream>>>(Z, p, r);
+    }
     CDMD_CHECK_LAUNCH("orthonormalise_kernel");
-    backtransform_kernel<<<r, 32, p * sizeof(double), stream>>>(Z, Hv, htau, lamT, p, r, V, sigma, ctx->d_status);
+    static_assert(32 * 16 >= 511, "the back-transform covers p = n - 1 <= 511 (n <= 512)");
+    if (p <= 256)
+        backtransform_kernel<8><<<r, 32, p * sizeof(double), stream>>>(Z, Hv, htau, lamT, p, r, V, sigma,
+                                                                       ctx->d_status);
+    else
+        backtransform_kernel<16><<<r, 32, p * sizeof(double), stream>>>(Z, Hv, htau, lamT, p, r, V, sigma,
+                                                                        ctx->d_status);
     CDMD_CHECK_LAUNCH("backtransform_kernel");
     // 4. A~ and its eigen-decomposition
     bmat_kernel<<<dim3((p + 7) / 8, r), 256, 0, stream>>>(R, V, n, p, B);
@@ -1733,7 +1868,7 @@ cdmd_status decompose_impl(cdmd_ctx* ctx, const double* DY, int k, const double*
     // 5. G, Gram-form quantities, selection
     gmat_kernel<<<(p * r + 127) / 128, 128, 0, stream>>>(V, sigma, W, p, r, G);
     CDMD_CHECK_LAUNCH("gmat_kernel");
-    hmat_kernel<<<r, 128, 2 * p * sizeof(double), stream>>>(R, G, n, p, r, M, cvec);
+    hmat_kernel<<<r, 512, 2 * p * sizeof(double), stream>>>(R, G, n, p, r, M, cvec);
     CDMD_CHECK_LAUNCH("hmat_kernel");
     ctx->last_M = M;
     ctx->last_cvec = cvec;
