@@ -292,8 +292,8 @@ cdmd_status cdmd_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n
                  "meas must be SPARSE, ROWSAMPLE or SRFT");
     if (meas->ctype == CDMD_C_SPARSE) {
         CDMD_REQUIRE(meas->col_ptr && meas->row_idx, "CSC arrays are NULL");
-        CDMD_REQUIRE(static_cast<size_t>(meas->k) * 16 * sizeof(int32_t) <= 200 * 1024,
-                     "SPARSE gather supports k <= %d", static_cast<int>(200 * 1024 / 64));
+        CDMD_REQUIRE(static_cast<size_t>(meas->k) * 17 * sizeof(int32_t) <= 232448,
+                     "SPARSE gather supports k <= %d", static_cast<int>(232448 / 68));
     } else {
         CDMD_REQUIRE(meas->rows != nullptr, "meas->rows is NULL");
     }
@@ -480,9 +480,7 @@ cdmd_status run_from(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t 
     // OMP: lift and subtract only the selected modes (sel, -1 padded);
     // LSTSQ: every mode carries an amplitude, so all r are used.
     const int32_t* cols = (p->selector == CDMD_SEL_LSTSQ) ? nullptr : sel;
-    // the tensor-core lift covers n <= 256 frames; longer clips lift in FP32
-    const cdmd_prec lift_prec = (p->prec == CDMD_PREC_BF16X2 && n > 256) ? CDMD_PREC_FP32 : p->prec;
-    st = cdmd_lift(ctx, D, m, n, ldd, Gm, r, cols, ncols, lift_prec, Phi, stream);
+    st = cdmd_lift(ctx, D, m, n, ldd, Gm, r, cols, ncols, p->prec, Phi, stream);
     if (st != CDMD_OK) return st;
     return cdmd_subtract(ctx, D, m, n, ldd, Phi, ncols, cols, beta, lambda, r, p->tau, p->bgmode, mask, nullptr,
                          stream);

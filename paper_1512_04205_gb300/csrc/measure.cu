@@ -107,18 +107,24 @@ __global__ void sparse_fill_kernel(int64_t m, int k, uint2 key, uint64_t thr, co
 }
 
 // One pass over D: CTA (slab, split) accumulates sign * D[t, j] into an
-// integer tile acc[i][t - t0] for its pixels.
-constexpr int kGatherThreads = 256;
-constexpr int kSlab = 16;
+// integer tile acc[i][t - t0] for its pixels.  A thread owns a pixel: it
+// loads the slab's frames of that pixel (a warp reads one 32-byte sector per
+// frame) and adds them into the rows of the pixel's non-zeros.  The tile's
+// row stride is kSlab + 1 words, so the atomic adds of a warp (random rows,
+// same frame) spread over the banks instead of meeting in two.
+constexpr int kGatherThreads = 512;
+constexpr size_t kGatherSmemMax = 232448;   // opt-in shared memory per CTA
 
+template <int kSlab>
 __global__ void __launch_bounds__(kGatherThreads)
 sparse_sketch_kernel(const uint8_t* __restrict__ D, int64_t m, int n, int64_t ldd, int k,
                      const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                      int64_t pix_per_split, int32_t* __restrict__ part) {
-    extern __shared__ int32_t acc[];   // [k][kSlab]
+    constexpr int kSlabStride = kSlab + 1;
+    extern __shared__ int32_t acc[];   // [k][kSlabStride]
     const int t0 = blockIdx.x * kSlab;
     const int nt = min(kSlab, n - t0);
-    for (int idx = threadIdx.x; idx < k * kSlab; idx += kGatherThreads) acc[idx] = 0;
+    for (int idx = threadIdx.x; idx < k * kSlabStride; idx += kGatherThreads) acc[idx] = 0;
     __syncthreads();
     const int64_t pbeg = static_cast<int64_t>(blockIdx.y) * pix_per_split;
     const int64_t pend = min(m, pbeg + pix_per_split);
@@ -132,7 +138,7 @@ sparse_sketch_kernel(const uint8_t* __restrict__ D, int64_t m, int n, int64_t ld
             const uint32_t code = static_cast<uint32_t>(row_idx[e]);
             const int i = static_cast<int>(code & 0x7fffffffu);
             const bool neg = (code & 0x80000000u) != 0u;
-            int32_t* row = acc + i * kSlab;
+            int32_t* row = acc + i * kSlabStride;
 #pragma unroll
             for (int t = 0; t < kSlab; ++t)
                 if (t < nt) atomicAdd(row + t, neg ? -x[t] : x[t]);
@@ -142,7 +148,7 @@ sparse_sketch_kernel(const uint8_t* __restrict__ D, int64_t m, int n, int64_t ld
     int32_t* dst = part + static_cast<int64_t>(blockIdx.y) * k * n;
     for (int idx = threadIdx.x; idx < k * nt; idx += kGatherThreads) {
         const int i = idx / nt, t = idx % nt;
-        dst[static_cast<int64_t>(i) * n + t0 + t] = acc[i * kSlab + t];
+        dst[static_cast<int64_t>(i) * n + t0 + t] = acc[i * kSlabStride + t];
     }
 }
 
@@ -313,9 +319,11 @@ cdmd_status launch_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int
         CDMD_CHECK_LAUNCH("rowsample_sketch_kernel");
         return CDMD_OK;
     }
-    const int slabs = (n + kSlab - 1) / kSlab;
-    // about four CTAs per SM in total
-    int64_t splits = std::max<int64_t>(1, (4LL * ctx->num_sms + slabs - 1) / slabs);
+    // frames per slab: 32 while the k x 33 integer tile fits, else 16
+    const int slab = (static_cast<size_t>(k) * 33 * sizeof(int32_t) <= kGatherSmemMax) ? 32 : 16;
+    const int slabs = (n + slab - 1) / slab;
+    // about two CTAs per SM in total (the tile takes up to ~130 KB)
+    int64_t splits = std::max<int64_t>(1, (2LL * ctx->num_sms + slabs - 1) / slabs);
     splits = std::min<int64_t>(splits, std::max<int64_t>(1, m / 4096));
     const int64_t pps = (m + splits - 1) / splits;
     splits = (m + pps - 1) / pps;
@@ -323,11 +331,19 @@ cdmd_status launch_sketch_gather(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int
     cdmd_status st = ensure_buffer(ctx, BUF_SKETCH_PARTIAL, static_cast<size_t>(splits) * k * n * sizeof(int32_t),
                                    reinterpret_cast<void**>(&part));
     if (st != CDMD_OK) return st;
-    const size_t smem = static_cast<size_t>(k) * kSlab * sizeof(int32_t);
-    CDMD_CHECK_CUDA(cudaFuncSetAttribute(sparse_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem)));
-    sparse_sketch_kernel<<<dim3(slabs, static_cast<unsigned>(splits)), kGatherThreads, smem, stream>>>(
-        D, m, n, ldd, k, meas->col_ptr, meas->row_idx, pps, part);
+    const size_t smem = static_cast<size_t>(k) * (slab + 1) * sizeof(int32_t);
+    const dim3 grid(slabs, static_cast<unsigned>(splits));
+    if (slab == 32) {
+        CDMD_CHECK_CUDA(cudaFuncSetAttribute(sparse_sketch_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kGatherSmemMax)));
+        sparse_sketch_kernel<32><<<grid, kGatherThreads, smem, stream>>>(D, m, n, ldd, k, meas->col_ptr, meas->row_idx,
+                                                                          pps, part);
+    } else {
+        CDMD_CHECK_CUDA(cudaFuncSetAttribute(sparse_sketch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kGatherSmemMax)));
+        sparse_sketch_kernel<16><<<grid, kGatherThreads, smem, stream>>>(D, m, n, ldd, k, meas->col_ptr, meas->row_idx,
+                                                                          pps, part);
+    }
     CDMD_CHECK_LAUNCH("sparse_sketch_kernel");
     const int64_t tot = static_cast<int64_t>(k) * n;
     sparse_reduce_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, stream>>>(part, static_cast<int>(splits), k, n, DY);
