@@ -765,7 +765,9 @@ def run_ours(args, rank, world, local_rank):
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
         hbm = float(load_peaks()[0]["hbm_gbs"])
         out = {"workload": f"{W4}x{H4}x{n4}, 8 ellipses, k={k4}, r={r4}, K={K4}",
-               "lift_precision": "fp32 (the tensor-core lift holds at most 256 frames)"}
+               "lift_precision": (f"{args.prec} (tensor cores: two frame chunks of at most 255, the second adding "
+                                  "into Phi)" if args.prec == "bf16x2" else args.prec),
+               "subtract": "tensor cores, two frame chunks of 150"}
         words = n4 * ((m4 + 31) // 32) * 4
         alg = {"lift": m4 * (n4 - 1) + m4 * K4 * 8, "subtract": m4 * n4 + m4 * K4 * 8 + words}
         for name, meas in (("sparse", C.Measure(ctx, "sparse", m4, k4, 77, 1e-3)),
@@ -784,7 +786,7 @@ def run_ours(args, rank, world, local_rank):
                     flush.zero_()
                     e_l = torch.cuda.Event(enable_timing=True)
                     e_l.record(main_stream)
-                    Phi4 = C.cdmd_lift(ctx, D4, dec4["G"], cols=dec4["sel"], ncols=K4, prec="fp32")
+                    Phi4 = C.cdmd_lift(ctx, D4, dec4["G"], cols=dec4["sel"], ncols=K4, prec=args.prec)
                     ev[3].record(main_stream)
                     flush.zero_()
                     e_s = torch.cuda.Event(enable_timing=True)

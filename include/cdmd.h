@@ -329,7 +329,9 @@ cdmd_status cdmd_decompose_auto(cdmd_ctx* ctx, const double* DY, int k, int n, i
  * ncols modes listed in `cols` (device int32, NULL = modes 0..ncols-1; a
  * negative entry yields a zero column).  G: (n-1) x r complex double.
  * Phi: m x ncols complex float, pixel-major.  ncols <= 64.  BF16X2 needs a
- * 16-byte aligned D, ldd % 16 == 0 and n <= 256 (else CDMD_ERR_UNSUPPORTED). */
+ * 16-byte aligned D and ldd % 16 == 0 (else CDMD_ERR_INVALID_ARG); clips
+ * longer than 256 frames are lifted in chunks of at most 255 frames of X',
+ * the later chunks adding into Phi (the product is linear in the frames). */
 cdmd_status cdmd_lift(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                       const double* G, int r, const int32_t* cols, int ncols,
                       cdmd_prec prec, float* Phi, void* stream);
@@ -381,9 +383,7 @@ typedef struct {
 /* Sketch -> decompose -> lift of the selected modes -> subtract, on device
  * buffers, enqueued on `stream`; intermediates live in the context's
  * workspace and stay valid until the next call on the context (see
- * cdmd_workspace_views).  mask as described above.  With BF16X2, clips longer
- * than 256 frames take the FP32 lift (the tensor-core lift holds all n-1
- * frames of a pixel tile in one operand). */
+ * cdmd_workspace_views).  mask as described above. */
 cdmd_status cdmd_run(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                      const cdmd_params* p, uint32_t* mask, void* stream);
 

@@ -163,8 +163,7 @@ cdmd_status run_clip(cdmd_batch* b, int i) {
                         q.nsel, s);
     if (st != CDMD_OK) return st;
     const int32_t* cols = (b->p.selector == CDMD_SEL_LSTSQ) ? nullptr : q.sel;
-    const cdmd_prec lift_prec = (b->p.prec == CDMD_PREC_BF16X2 && c.n > 256) ? CDMD_PREC_FP32 : b->p.prec;
-    st = cdmd_lift(ctx, c.D, c.m, c.n, c.ldd, q.G, c.r, cols, ncols, lift_prec, q.Phi, s);
+    st = cdmd_lift(ctx, c.D, c.m, c.n, c.ldd, q.G, c.r, cols, ncols, b->p.prec, q.Phi, s);
     if (st != CDMD_OK) return st;
     if (!grouped(b))
         st = cdmd_subtract(ctx, c.D, c.m, c.n, c.ldd, q.Phi, ncols, cols, q.beta, q.lambda, c.r, b->p.tau,

@@ -14,8 +14,10 @@
 //               two TMEM accumulators
 //   warps 8-11  tcgen05.ld the accumulator (one pixel per thread), add hi + lo
 //               and store Phi (complex64, pixel-major)
-// G (the B operand) is converted once per CTA.  At most 16 modes per launch;
-// the launcher loops over groups of 16.  Waits are bounded as in the sketch.
+// G (the B operand) is converted once per CTA.  At most 16 modes and 255
+// frames per launch; the launcher loops over groups of 16 modes and over
+// frame chunks (later chunks add into Phi).  Waits are bounded as in the
+// sketch.
 #include "tc_common.cuh"
 
 namespace cdmd {
@@ -58,9 +60,9 @@ __device__ __forceinline__ uint16_t bf16_rn_bits(float x) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-lift_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, const double* __restrict__ G, int r,
-               const int32_t* __restrict__ cols, int col0, int nmodes, int ncols_total, int64_t ntiles,
-               float* __restrict__ Phi, int* status) {
+lift_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, const double* __restrict__ G, int ldg,
+               int r, const int32_t* __restrict__ cols, int col0, int nmodes, int ncols_total, int64_t ntiles,
+               int accumulate, float* __restrict__ Phi, int* status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const LiftLayout L = lift_layout(n, nmodes);
@@ -104,7 +106,7 @@ lift_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, const
         if (c < nmodes && t < p) {
             const int s = cols ? cols[col0 + c] : col0 + c;
             if (s >= 0 && s < r) {
-                const float g = static_cast<float>(G[2 * (static_cast<int64_t>(s) * p + t) + (part >> 1)]);
+                const float g = static_cast<float>(G[2 * (static_cast<int64_t>(s) * ldg + t) + (part >> 1)]);
                 const uint16_t hb = bf16_rn_bits(g);
                 const float hf = __uint_as_float(static_cast<uint32_t>(hb) << 16);
                 val = (part & 1) ? (g - hf) : hf;
@@ -230,9 +232,15 @@ lift_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, const
                     for (int q4 = 0; q4 < 4; ++q4) {
                         const int c = c0 / 4 + q4;
                         if (c < nmodes) {
-                            const float re = __uint_as_float(rv[4 * q4]) + __uint_as_float(rv[4 * q4 + 1]);
-                            const float im = __uint_as_float(rv[4 * q4 + 2]) + __uint_as_float(rv[4 * q4 + 3]);
-                            *reinterpret_cast<float2*>(Phi + 2 * (j * ncols_total + col0 + c)) = make_float2(re, im);
+                            float re = __uint_as_float(rv[4 * q4]) + __uint_as_float(rv[4 * q4 + 1]);
+                            float im = __uint_as_float(rv[4 * q4 + 2]) + __uint_as_float(rv[4 * q4 + 3]);
+                            float2* dst = reinterpret_cast<float2*>(Phi + 2 * (j * ncols_total + col0 + c));
+                            if (accumulate) {
+                                const float2 prev = *dst;
+                                re += prev.x;
+                                im += prev.y;
+                            }
+                            *dst = make_float2(re, im);
                         }
                     }
                 }
@@ -258,23 +266,38 @@ lift_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, const
 
 cdmd_status launch_lift_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const double* G, int r,
                            const int32_t* cols, int ncols, float* Phi, cudaStream_t stream) {
-    if (n > 256) return fail(CDMD_ERR_UNSUPPORTED, "BF16X2 lift needs n <= 256 (got %d)", n);
     if ((reinterpret_cast<uintptr_t>(D) & 15) != 0 || (ldd & 15) != 0)
         return fail(CDMD_ERR_INVALID_ARG, "BF16X2 lift needs a 16-byte aligned video and ldd %% 16 == 0");
-    CUtensorMap tmap;
-    cdmd_status st = make_video_tmap(&tmap, D, m, n, ldd, kPix, n - 1);
-    if (st != CDMD_OK) return st;
+    // frames of X' in chunks of at most 255 (the operand tile and the tensor
+    // copy box hold one chunk); the product is linear in the frames, so
+    // chunks after the first add into Phi.  Chunk q covers X' frames
+    // [t0, t0 + cnt) = video frames t0+1 .. t0+cnt, seen as a clip of cnt+1
+    // frames starting at frame t0, with G rows t0.. (leading dimension n-1).
+    const int pt = n - 1;
+    const int nch = (pt + 254) / 255;
+    const int per = (pt + nch - 1) / nch;
     const int64_t ntiles = (m + kPix - 1) / kPix;
     const unsigned grid = static_cast<unsigned>(std::min<int64_t>(ntiles, ctx->num_sms));
-    for (int col0 = 0; col0 < ncols; col0 += kMaxModes) {
-        const int nmodes = std::min(kMaxModes, ncols - col0);
-        const LiftLayout L = lift_layout(n, nmodes);
-        const size_t smem = L.total + 1024;
-        CDMD_CHECK_CUDA(cudaFuncSetAttribute(lift_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem)));
-        lift_tc_kernel<<<grid, kThreads, smem, stream>>>(tmap, m, n, G, r, cols, col0, nmodes, ncols, ntiles, Phi,
-                                                          ctx->d_status);
-        CDMD_CHECK_LAUNCH("lift_tc_kernel");
+    for (int q = 0; q < nch; ++q) {
+        const int t0 = q * per;
+        const int cnt = std::min(per, pt - t0);
+        const int nq = cnt + 1;
+        const uint8_t* Dq = D + static_cast<int64_t>(t0) * ldd;
+        CUtensorMap tmap;
+        cdmd_status st = make_video_tmap(&tmap, Dq, m, nq, ldd, kPix, nq - 1);
+        if (st != CDMD_OK) return st;
+        for (int col0 = 0; col0 < ncols; col0 += kMaxModes) {
+            const int nmodes = std::min(kMaxModes, ncols - col0);
+            const LiftLayout L = lift_layout(nq, nmodes);
+            const size_t smem = L.total + 1024;
+            CDMD_CHECK_CUDA(cudaFuncSetAttribute(lift_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 232448));
+            (void)smem;
+            lift_tc_kernel<<<grid, kThreads, L.total + 1024, stream>>>(tmap, m, nq, G + 2 * static_cast<int64_t>(t0),
+                                                                         pt, r, cols, col0, nmodes, ncols, ntiles,
+                                                                         q > 0 ? 1 : 0, Phi, ctx->d_status);
+            CDMD_CHECK_LAUNCH("lift_tc_kernel");
+        }
     }
     return CDMD_OK;
 }

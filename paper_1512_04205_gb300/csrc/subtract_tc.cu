@@ -385,7 +385,7 @@ subtract_tc_grouped_kernel(const SubTcClip* __restrict__ clips, const SubtractIt
 
 bool subtract_tc_supported(int n, int ncols, cdmd_bgmode mode, const uint8_t* D, int64_t ldd, int64_t m,
                            const float* bg) {
-    return bg == nullptr && (mode == CDMD_BG_MODULUS || mode == CDMD_BG_REAL) && n >= 32 && n <= 256 &&
+    return bg == nullptr && (mode == CDMD_BG_MODULUS || mode == CDMD_BG_REAL) && n >= 32 && n <= 1024 &&
            ncols >= 1 && ncols <= kMaxModes && (reinterpret_cast<uintptr_t>(D) % 16 == 0) && (ldd % 16 == 0) &&
            m <= 0x7fffffffLL - kPix;
 }
@@ -419,33 +419,43 @@ cdmd_status launch_subtract_tc_grouped(const SubTcClip* clips, const SubtractIte
 cdmd_status launch_subtract_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const float* Phi,
                                int ncols, const void* lam_t, const void* amp, int nc_pad, float tau, cdmd_bgmode mode,
                                uint32_t* mask, cudaStream_t stream) {
-    CUtensorMap tmap;
-    cdmd_status st = make_video_tmap(&tmap, D, m, n, ldd, kPix, n);
-    if (st != CDMD_OK) return st;
-    SubTcArgs a{};
-    a.Phi = reinterpret_cast<const float2*>(Phi);
-    a.lam_t = static_cast<const float2*>(lam_t);
-    a.amp = static_cast<const float2*>(amp);
-    a.mask = mask;
-    a.m = m;
-    a.words_per_frame = (m + 31) / 32;
-    a.ntiles = (m + kPix - 1) / kPix;
-    a.n = n;
-    a.ncols = ncols;
-    a.nc_pad = nc_pad;
-    a.tau = tau;
-    const size_t smem = sub_layout(n).total + 1024;
-    const unsigned grid = static_cast<unsigned>(std::min<int64_t>(a.ntiles, ctx->num_sms));
-    if (mode == CDMD_BG_REAL) {
-        CDMD_CHECK_CUDA(cudaFuncSetAttribute(subtract_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem)));
-        subtract_tc_kernel<true><<<grid, kThreads, smem, stream>>>(tmap, a, ctx->d_status);
-    } else {
-        CDMD_CHECK_CUDA(cudaFuncSetAttribute(subtract_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem)));
-        subtract_tc_kernel<false><<<grid, kThreads, smem, stream>>>(tmap, a, ctx->d_status);
+    // frames in chunks of at most 256 (the MMA N and the tensor copy box);
+    // frames are independent here, so chunk q is the clip of frames
+    // t0 .. t0+cnt-1 with its rows of the lambda^t table and of the mask
+    const int nch = (n + 255) / 256;
+    const int per = (n + nch - 1) / nch;
+    const int64_t wpf = (m + 31) / 32;
+    for (int q = 0; q < nch; ++q) {
+        const int t0 = q * per;
+        const int cnt = std::min(per, n - t0);
+        CUtensorMap tmap;
+        cdmd_status st = make_video_tmap(&tmap, D + static_cast<int64_t>(t0) * ldd, m, cnt, ldd, kPix, cnt);
+        if (st != CDMD_OK) return st;
+        SubTcArgs a{};
+        a.Phi = reinterpret_cast<const float2*>(Phi);
+        a.lam_t = static_cast<const float2*>(lam_t) + static_cast<int64_t>(t0) * nc_pad;
+        a.amp = static_cast<const float2*>(amp);
+        a.mask = mask + static_cast<int64_t>(t0) * wpf;
+        a.m = m;
+        a.words_per_frame = wpf;
+        a.ntiles = (m + kPix - 1) / kPix;
+        a.n = cnt;
+        a.ncols = ncols;
+        a.nc_pad = nc_pad;
+        a.tau = tau;
+        const size_t smem = sub_layout(cnt).total + 1024;
+        const unsigned grid = static_cast<unsigned>(std::min<int64_t>(a.ntiles, ctx->num_sms));
+        if (mode == CDMD_BG_REAL) {
+            CDMD_CHECK_CUDA(cudaFuncSetAttribute(subtract_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 232448));
+            subtract_tc_kernel<true><<<grid, kThreads, smem, stream>>>(tmap, a, ctx->d_status);
+        } else {
+            CDMD_CHECK_CUDA(cudaFuncSetAttribute(subtract_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 232448));
+            subtract_tc_kernel<false><<<grid, kThreads, smem, stream>>>(tmap, a, ctx->d_status);
+        }
+        CDMD_CHECK_LAUNCH("subtract_tc_kernel");
     }
-    CDMD_CHECK_LAUNCH("subtract_tc_kernel");
     return CDMD_OK;
 }
 

@@ -336,10 +336,12 @@ def test_sketch_bf16x2_rejects_unaligned_stride(C, ctx):
 # ------------------------------------------------------- lift, tensor cores
 
 @pytest.mark.parametrize("w,h,n,r,modes", [(160, 120, 100, 10, [9, -1, 0, 2]), (97, 61, 37, 13, list(range(13))),
-                                           (33, 9, 256, 30, list(range(29, 9, -1))), (300, 40, 2, 1, [0])])
+                                           (33, 9, 256, 30, list(range(29, 9, -1))), (300, 40, 2, 1, [0]),
+                                           (48, 20, 300, 12, list(range(12))), (40, 16, 511, 6, [5, 0, 3])])
 def test_lift_bf16x2(C, ctx, w, h, n, r, modes):
     # G in BF16 hi+lo (2^-16 relative), pixels exact: each Phi column within
-    # 5e-5 of the FP64 oracle in 2-norm.
+    # 5e-5 of the FP64 oracle in 2-norm.  Clips past 256 frames are lifted in
+    # chunks of at most 255 frames, the later chunks adding into Phi.
     clip = videogen.make_clip(w, h, n, seed=n + r)
     m = clip.m
     ldd = (m + 15) // 16 * 16

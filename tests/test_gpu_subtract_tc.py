@@ -1,5 +1,6 @@
 """Pass (c) on the tensor cores (mask-only MODULUS / REAL calls with
-32 <= n <= 256 frames, up to 16 modes and a 16-byte aligned video) against
+32 <= n <= 1024 frames, taken 256 at most to a launch, up to 16 modes and a
+16-byte aligned video) against
 the FP64 oracle's background formula and threshold.
 
 The background is a small GEMM in 3xTF32 (about 2^-19 relative per term),
@@ -62,9 +63,10 @@ def _modes(m, r, seed):
 
 
 # (W, H, n, r): a ragged pixel count (not a multiple of 32 or 128), the
-# smallest n, odd n, the bench's n, the largest n; 1 to 16 modes
+# smallest n, odd n, the bench's n, the largest single launch, and clips
+# past 256 frames (taken in frame chunks: 129 + 128, 150 + 150); 1 to 16 modes
 CASES = [(61, 37, 32, 1), (61, 37, 45, 3), (97, 61, 200, 10), (128, 96, 256, 16), (40, 33, 111, 7),
-         (300, 41, 64, 12)]
+         (300, 41, 64, 12), (64, 20, 257, 4), (160, 31, 300, 9)]
 
 
 @pytest.mark.parametrize("mode", ["modulus", "real"])
