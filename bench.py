@@ -814,6 +814,70 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         return out
 
+    def selector_eval(n_clips=10):
+        """The learned selector on held-out clips of the workload's size
+        (seeds outside its training and calibration ranges), against OMP on
+        the same BF16 hi+lo sketch: fallbacks, identical selections, the
+        background difference of the two forms (relative 2-norm on 20,000
+        seeded pixels x all frames) and the F-measure of each against the
+        generator's truth."""
+        sctx = C.Context(local_rank)
+        octx = C.Context(local_rank)
+        if model is None:
+            return None
+        C.cdmd_selector_load(sctx, model)
+        C.cdmd_selector_fallbacks(sctx, reset=True)
+        J = torch.from_numpy(np.unique(np.random.default_rng(12).integers(0, m, 20_000))).to(dev)
+        shifts = torch.arange(32, device=dev, dtype=torch.int32)
+
+        def fm(mask_words, truth_dev):
+            bits = ((mask_words.unsqueeze(-1) >> shifts) & 1).reshape(n, -1)[:, :m].bool()
+            tp = int((bits & truth_dev).sum())
+            fp = int((bits & ~truth_dev).sum())
+            fn = int((~bits & truth_dev).sum())
+            pr = tp / max(tp + fp, 1)
+            rc = tp / max(tp + fn, 1)
+            return 2 * pr * rc / (pr + rc) if pr + rc > 0 else 0.0
+
+        def form(cx, Dc, dec):
+            Phi = C.cdmd_lift(cx, Dc, dec["G"], cols=dec["sel"], ncols=K, prec=args.prec)
+            mask_w = C.cdmd_subtract(cx, Dc, Phi, dec["beta"], dec["lam"], w["tau"], cols=dec["sel"])
+            _, bgf = C.cdmd_subtract(cx, Dc, Phi, dec["beta"], dec["lam"], w["tau"], cols=dec["sel"], want_bg=True)
+            out = (mask_w, bgf[:, J].double())
+            del bgf
+            return out
+
+        rows = []
+        for i in range(n_clips):
+            sd = 7_000_000 + i
+            spec = videogen.clip_spec(w["width"], w["height"], n, sd, drift=w["drift"])
+            Dc = C.cdmd_synth_clip(octx, spec, sd)
+            DYc = C.cdmd_sketch(octx, Dc, k, w["c_seed"], prec=args.prec)
+            dm = C.cdmd_decompose(sctx, DYc, r, K, selector="mlp")
+            do = C.cdmd_decompose(octx, DYc, r, K, selector="omp")
+            mm, bm = form(sctx, Dc, dm)
+            mo, bo = form(octx, Dc, do)
+            C.cdmd_status_sync(sctx)
+            C.cdmd_status_sync(octx)
+            truth = torch.from_numpy(videogen.truth_from_spec(spec)).to(dev)
+            rows.append({"seed": sd,
+                         "same_set": sorted(dm["sel"].tolist()) == sorted(do["sel"].tolist()),
+                         "bg_rel_diff_learned_vs_omp": float(torch.linalg.norm(bm - bo) / torch.linalg.norm(bo)),
+                         "F_learned": fm(mm, truth), "F_omp": fm(mo, truth)})
+            del Dc, truth
+        fb = C.cdmd_selector_fallbacks(sctx)
+        torch.cuda.empty_cache()
+        return {"clips": n_clips, "size": f"{w['width']}x{w['height']}x{n}, k={k}, r={r}, K={K}",
+                "seeds": "7000000 + i (outside training 1000000.. and calibration 1120000..)",
+                "fallbacks": fb, "fallback_rate": fb / n_clips,
+                "identical_selections": sum(q["same_set"] for q in rows),
+                "F_learned_mean": float(np.mean([q["F_learned"] for q in rows])),
+                "F_omp_mean": float(np.mean([q["F_omp"] for q in rows])),
+                "bg_rel_diff_max": float(max(q["bg_rel_diff_learned_vs_omp"] for q in rows)),
+                "per_clip": rows,
+                "note": ("background error against the FP64 oracle's OMP result: tests/test_gpu_selector_1080p.py; "
+                         "both forms use the same sketch")}
+
     # the headline form and the plain FP32 + OMP form it is compared with
     forms = {"head": (args.prec, args.selector)}
     if not args.no_plain and (args.prec, args.selector) != ("fp32", "omp"):
@@ -917,6 +981,7 @@ def run_ours(args, rank, world, local_rank):
 
     batch_line = run_batch_measure(C, SEL, torch, dev, args, model) if not args.no_batch else None
     gather_line = gather_4k_measure() if not args.no_gather else None
+    sel_line = selector_eval() if (args.selector == "mlp" and not args.no_selector_eval) else None
 
     if rank != 0:
         if dist is not None:
@@ -1039,6 +1104,8 @@ def run_ours(args, rank, world, local_rank):
         line["batch"] = batch_line
     if gather_line is not None:
         line["gather_4k"] = gather_line
+    if sel_line is not None:
+        line["selector_eval"] = sel_line
     if not args.no_cpu:
         st = oracle_step(clip, CPU_SAMPLE_PX)
         line["cpu_baseline"] = {"value": w["n"] / st["full_clip_estimate_s"], "unit": UNIT, "cores": cpu_cores(),
@@ -1079,6 +1146,8 @@ def main():
                          "launch, so one draw of C feeds all of them)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batch of 64 clips of mixed size (grouped launches, graph, autotuner)")
+    ap.add_argument("--no-selector-eval", action="store_true",
+                    help="skip the learned selector's evaluation on held-out clips of the workload's size")
     ap.add_argument("--no-gather", action="store_true",
                     help="skip the 3840x2160x300 gather workload (sparse and single-pixel C)")
     ap.add_argument("--size", default=None,

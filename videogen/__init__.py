@@ -26,7 +26,7 @@ the transpose of the paper's m x n video matrix.
 """
 import numpy as np
 
-__all__ = ["make_clip", "clip_spec", "Clip", "CONFIGS"]
+__all__ = ["make_clip", "clip_spec", "truth_from_spec", "Clip", "CONFIGS"]
 
 
 class Clip:
@@ -176,6 +176,21 @@ def make_clip(width, height, n, seed, n_sinusoids=6, n_objects=3,
     params = dict(n_sinusoids=n_sinusoids, n_objects=n_objects, shape=shape,
                   drift=drift, noise_sigma=noise_sigma)
     return Clip(frames, truth, W, H, seed, params)
+
+
+def truth_from_spec(spec):
+    """Ground-truth foreground (n, m) bool of the clip a spec describes: the
+    pixels whose centre lies inside an object in that frame (what make_clip
+    returns as truth), without rendering the frames."""
+    W, H, n = spec["width"], spec["height"], spec["n"]
+    truth = np.zeros((n, H * W), dtype=bool)
+    for t in range(n):
+        tmask = np.zeros((H, W), dtype=bool)
+        for state in spec["objects"][t]:
+            inside, (y0, y1, x0, x1) = _cover(state, W, H, spec["shape"])
+            tmask[y0:y1, x0:x1] |= inside
+        truth[t] = tmask.reshape(-1)
+    return truth
 
 
 # Workload shapes (width, height, n, generator options, method parameters).
