@@ -748,8 +748,9 @@ def run_ours(args, rank, world, local_rank):
         peak = float(load_peaks()[0].get("bf16_tflops_sustained", load_peaks()[0]["bf16_tflops"]))
         return {"sketch_ms_per_clip": ms, "tflops": tf, "frac": tf / peak, "peak_tflops": peak,
                 "bytes_gbs": m * n / (ms * 1e-3) / 1e9,
-                "form": (f"{cps} clips under one Rademacher C, packed 512 frames to a launch; time per clip "
-                         "includes the widen passes and the reduces; one BF16 product (C exact)")}
+                "form": (f"{cps} clips under one Rademacher C, packed 512 frames to a launch; the uint8 frames "
+                         "converted to FP16 inside the kernel (no BF16 copies); time per clip includes the reduces; "
+                         "one FP16 product (C exact)")}
 
     def gather_4k_measure(reps=5):
         """The gather workload: a 3840x2160 clip of 300 frames (8 moving

@@ -99,7 +99,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 key) {
 struct PhiloxKeys {
     uint32_t x[10], y[10];
 };
-__device__ __forceinline__ PhiloxKeys philox_round_keys(uint2 key) {
+__host__ __device__ __forceinline__ PhiloxKeys philox_round_keys(uint2 key) {
     PhiloxKeys k;
 #pragma unroll
     for (int rnd = 0; rnd < 10; ++rnd) {
@@ -187,6 +187,7 @@ struct Buffer {
 
 enum BufferId {
     BUF_SKETCH_PARTIAL = 0,   // sketch split partials (float)
+    BUF_SKETCH_WIDE,          // BF16 copies of the frames of clips sketched together
     BUF_GRAM,                 // snapshot Gram split partials (float)
     BUF_EIG,                  // eigen-solver scratch (double)
     BUF_SMALL,                // small-solve scratch (double)
@@ -199,7 +200,6 @@ enum BufferId {
     BUF_SELECTOR,             // selector model blob, pick order, accept flag, fallback count
     BUF_MLP_PARTS,            // selector training: per-warp partial gradients
     BUF_RELABEL,              // selector training: OMP against a second target
-    BUF_SKETCH_WIDE,          // BF16 copies of the frames of a clip pair sketched together
     BUF_RUN_GRAM,             // cdmd_run_exact: the n x n snapshot Gram (double)
     BUF_COUNT
 };
@@ -260,7 +260,7 @@ cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, 
                              cdmd_ctype ctype, int k, uint64_t seed, double* DY,
                              cudaStream_t stream);
 // Several clips of the same pixel count sketched with one C (same k, seed):
-// consecutive clips share the generator two at a time where they fit.
+// up to 512 frames of them share each draw of C.
 cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
                                     const int64_t* ldd, cdmd_ctype ctype, int k, uint64_t seed, double* const* DY,
                                     cudaStream_t stream);

@@ -49,13 +49,6 @@ constexpr uint32_t kGTmemCols = 512;
 
 __host__ __device__ inline int gpad16(int n) { return (n + 15) / 16 * 16; }
 
-// Both FP16 halves of x minus 1024 (exact for halves 1024 .. 2047).
-__device__ __forceinline__ uint32_t sub_1024_f16x2(uint32_t x) {
-    uint32_t r;
-    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(0x64006400u));
-    return r;
-}
-
 __host__ __device__ inline uint32_t gram_smem_bytes() {
     return kGBuf * kGBTile + kGStg * kGStaging + (2 * kGStg + 2 * kGBuf + 1) * 8 + 64;
 }
@@ -188,8 +181,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__
                 for (int h = 0; h < 4; ++h) {
                     const uint32_t word = h == 0 ? raw.x : h == 1 ? raw.y : h == 2 ? raw.z : raw.w;
                     // halves 0x6400 | b = 1024 + b for bytes (0, 1) and (2, 3), then minus 1024, exact
-                    w[h * 2 + 0] = sub_1024_f16x2(__byte_perm(word, 0x64646464u, 0x4140u));
-                    w[h * 2 + 1] = sub_1024_f16x2(__byte_perm(word, 0x64646464u, 0x4342u));
+                    w[h * 2 + 0] = tc::sub_1024_f16x2(__byte_perm(word, 0x64646464u, 0x4140u));
+                    w[h * 2 + 1] = tc::sub_1024_f16x2(__byte_perm(word, 0x64646464u, 0x4342u));
                 }
                 // two 16-byte chunks of the swizzled row; a quarter warp covers
                 // an even and an odd row, so its eight stores hit distinct banks

@@ -21,10 +21,16 @@
 //              two 256-row slots; each segment's tensor copy lands in the B
 //              operand directly, so the conversion is done once per clip and
 //              not again in every row block.
-// In both, warp 1 issues tcgen05.mma (M 128, N = frames per slot padded to
-// 16, K 16, hi and lo) into the accumulators and commits to the stage's
-// barrier, and warps 4-11 draw the C block (rows x 64 pixels) from Philox,
-// split into BF16 hi / lo A tiles.
+//   packed, Rademacher C   the same packing, but the +1 / -1 entries are
+//              exact in FP16: one product, and sixteen warps convert the
+//              uint8 bytes (loaded into registers two K steps ahead) to FP16
+//              B tiles in the kernel, so no BF16 copy is made.  With the
+//              Gaussian draw the in-kernel conversion costs more issue slots
+//              than the widen pass, which overlaps other clips' launches.
+// In the per-clip and the Gaussian packed form, warp 1 issues tcgen05.mma
+// (M 128, N = frames per slot padded to 16, K 16, hi and lo) into the
+// accumulators and commits to the stage's barrier, and warps 4-11 draw the C
+// block (rows x 64 pixels) from Philox, split into BF16 hi / lo A tiles.
 // After the last K step warps 4-7 read the accumulators (tcgen05.ld) and write
 // FP32 partials [split][frame][row]; a second kernel sums the splits in FP64.
 // Every mbarrier wait is bounded in time; on a timeout the CTA records
@@ -563,7 +569,6 @@ __host__ __device__ inline uint32_t pack_smem_bytes() {
     return kStages * (kPackAStage + kPackBStage) + (3 * kStages + 1) * 8 + 64;
 }
 
-template <bool kRad>
 __global__ void __launch_bounds__(kThreads, 1)
 sketch_tc_packed_kernel(const __grid_constant__ PackArgs a, int* status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -653,7 +658,7 @@ sketch_tc_packed_kernel(const __grid_constant__ PackArgs a, int* status) {
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint64_t bdesc = tc::desc_sw128(b_base + slot * (kPackBStage / 2) + kk * 32);
 #pragma unroll
-                        for (int hl = 0; hl < (kRad ? 1 : 2); ++hl) {
+                        for (int hl = 0; hl < 2; ++hl) {
                             const uint64_t adesc = tc::desc_sw128(a_base + hl * kTileBytes + kk * 32);
                             tc::mma_bf16(tmem_base + slot * kAccCols, adesc, bdesc, slot ? idesc1 : idesc0,
                                          (ks | kk | hl) ? 1u : 0u);
@@ -672,10 +677,7 @@ sketch_tc_packed_kernel(const __grid_constant__ PackArgs a, int* status) {
             const int s = static_cast<int>(ks % kStages);
             const uint32_t u = static_cast<uint32_t>(ks / kStages);
             if (u >= 1 && !tc::mbar_wait(&mma_done[s], (u - 1) & 1u, abort_flag, status)) break;
-            if constexpr (kRad)
-                draw_rademacher_tile(A + s * kPackAStage, warp - 4, lane, row0, k, (step0 + ks) * kKStep, a.m, rk);
-            else
-                draw_c_tiles(A + s * kPackAStage, gt, 1, row0, k, (step0 + ks) * kKStep, a.m, rk);
+            draw_c_tiles(A + s * kPackAStage, gt, 1, row0, k, (step0 + ks) * kKStep, a.m, rk);
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&ab_full[s]);
         }
@@ -761,6 +763,341 @@ __global__ void widen_kernel(const uint8_t* __restrict__ D, int64_t m, int64_t l
     dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
 }
 
+// ---------------------------------------------------------------------------
+// Packed form for the Rademacher C, straight from the uint8 frames.  The
+// entries +1 / -1 are exact in FP16, so one product suffices and the B tiles
+// are built in the kernel: each of warps 1-16 loads the bytes of four B rows
+// (16 pixels each) into registers two 64-pixel K steps ahead and converts
+// them to FP16 (the byte permute 0x6400 | b = 1024 + b, then one packed
+// subtract of 1024) in the 128-byte swizzled K-major layout.  With only a
+// Philox counter per 32 pixels to draw, the Gaussian form's widened BF16
+// copies would leave this kernel bound by their tensor copies (eight
+// row-block CTAs each read every BF16 tile); reading the bytes halves that
+// traffic and needs no copy of the frames.
+//   warp 0       tensor-memory allocation; lane 0 issues tcgen05.mma per K
+//                step (per slot four K16 quarters) into 2 x 256 FP32 columns
+//   warps 1-16   per K step: the C tile (row g / 4, 16 pixels) into the A
+//                stage, four B rows into the B stage; 2 operand stages.
+//                Lane 0 waits for a stage and arrives for its warp.
+//   warps 1-16   after the last K step: the accumulators to FP32 partials
+//                [split][B row][k]; a reduce per segment sums the splits in
+//                FP64 into the clip's DY columns f0 .. f0 + L - 1.
+// Rows no segment covers read as zero: the B stages are cleared once and
+// those rows are never written.
+// ---------------------------------------------------------------------------
+constexpr int kRadRows = 512;
+constexpr int kRadMaxSeg = 8;
+constexpr int kRThreads = 544;                           // warp 0 + 16 generator warps
+constexpr int kRGenWarps = 16;                           // warps 1-16
+constexpr int kRKStep = 64;                              // pixels per K step
+constexpr int kRBuf = 2;                                 // operand stages = K steps of bytes in flight
+constexpr uint32_t kRAStage = 128u * 128u;               // 128 rows x 128 bytes of FP16
+constexpr uint32_t kRSlotBytes = 256u * 128u;            // one 256-row slot of B
+constexpr uint32_t kRBStage = 2u * kRSlotBytes;          // 512 rows x 128 bytes of FP16
+
+struct RadSeg {
+    double* DY;             // the clip's DY (frame-major, k per frame)
+    const uint8_t* D;       // the segment's first frame
+    int64_t ldd;            // bytes between frames
+    int row0, L, f0;        // B rows row0 .. row0 + L - 1 hold frames f0 .. f0 + L - 1
+    int pad;
+};
+
+struct RadArgs {
+    RadSeg seg[kRadMaxSeg];
+    PhiloxKeys rk;               // round keys of the seed (constant for the launch)
+    float* part;                 // [splits][kRadRows][k]
+    int nseg, k;
+    int nslot[2];                // rows of each slot the MMAs cover (multiples of 16, 0 = unused)
+    int64_t m;
+    int steps_per_split, total_steps;
+};
+
+__host__ __device__ inline uint32_t rad_smem_bytes() {
+    return kRBuf * (kRAStage + kRBStage) + (2 * kRBuf + 1) * 8 + 64;
+}
+
+// 16 bytes of a B row at pixel j (16-byte aligned), streaming; pixels at or
+// past m and rows no segment covers (src == nullptr) read as zero.
+__device__ __forceinline__ uint4 load_row16(const uint8_t* src, int64_t j, int64_t m) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (src == nullptr || j >= m) return v;
+    const uint8_t* p = src + j;
+    if (j + 16 <= m) {
+        asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "l"(p));
+        return v;
+    }
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+        if (j + e < m) w[e >> 2] |= static_cast<uint32_t>(p[e]) << (8 * (e & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// The same where the whole 16 bytes are below m (every split but the one
+// holding the ragged end of the frame).
+__device__ __forceinline__ uint4 load_row16_full(const uint8_t* src, int64_t j) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (src != nullptr)
+        asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "l"(src + j));
+    return v;
+}
+
+// 16 uint8 pixels as FP16 into two 16-byte chunks (off_a, off_a ^ 16 apart
+// by the swizzle) of a B row.
+__device__ __forceinline__ void convert_row16(uint8_t* b_stage, uint32_t off_a, uint32_t off_b, uint4 raw) {
+    uint32_t w[8];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const uint32_t word = h == 0 ? raw.x : h == 1 ? raw.y : h == 2 ? raw.z : raw.w;
+        w[h * 2 + 0] = tc::sub_1024_f16x2(__byte_perm(word, 0x64646464u, 0x4140u));
+        w[h * 2 + 1] = tc::sub_1024_f16x2(__byte_perm(word, 0x64646464u, 0x4342u));
+    }
+    *reinterpret_cast<uint4*>(b_stage + off_a) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(b_stage + off_b) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// One Rademacher item as FP16 +1 / -1: row r = g / 4 of the tile, pixels
+// j0 + 16 (g mod 4) .. + 15, two 16-byte chunks.  Entry (i, j) is bit
+// (i % 128) % 32 of word (i % 128) / 32 of the Philox counter (j, i / 128,
+// 1, 0): clear = +1, set = -1.  Lane l draws the counters of pixels j0 + l
+// and j0 + 32 + l (every row of a warp lies in one word) and the warp passes
+// the words round by shuffles.  Rows past k and pixels past m are zero.
+__device__ __forceinline__ void draw_rademacher_f16(uint8_t* a_stage, uint32_t off_a, uint32_t off_b, int lane, int r,
+                                                    int pg, int row0, int k, int64_t j0, int64_t m,
+                                                    const PhiloxKeys& rk) {
+    const uint32_t blk = static_cast<uint32_t>(row0 >> 7);
+    const uint4 wa = philox4x32_10(make_uint4(static_cast<uint32_t>(j0) + lane, blk, 1u, 0u), rk);
+    const uint4 wb = philox4x32_10(make_uint4(static_cast<uint32_t>(j0) + 32u + lane, blk, 1u, 0u), rk);
+    const int wi = r >> 5;
+    const uint32_t word_a = wi == 0 ? wa.x : wi == 1 ? wa.y : wi == 2 ? wa.z : wa.w;
+    const uint32_t word_b = wi == 0 ? wb.x : wi == 1 ? wb.y : wi == 2 ? wb.z : wb.w;
+    const bool row_ok = row0 + r < k;
+    const bool hi_half = pg >= 2;                   // pixels 32 .. 63 of the step
+    uint32_t out[8];
+#pragma unroll
+    for (int p2 = 0; p2 < 8; ++p2) {
+        const int src = 16 * (pg & 1) + 2 * p2;     // lane of the counter
+        const uint32_t a0 = __shfl_sync(0xffffffffu, word_a, src), a1 = __shfl_sync(0xffffffffu, word_a, src + 1);
+        const uint32_t b0 = __shfl_sync(0xffffffffu, word_b, src), b1 = __shfl_sync(0xffffffffu, word_b, src + 1);
+        const uint32_t s0 = ((hi_half ? b0 : a0) >> (r & 31)) & 1u;
+        const uint32_t s1 = ((hi_half ? b1 : a1) >> (r & 31)) & 1u;
+        const int64_t jp = j0 + 16 * pg + 2 * p2;
+        const uint32_t e0 = (row_ok && jp < m) ? (0x3C00u | (s0 << 15)) : 0u;
+        const uint32_t e1 = (row_ok && jp + 1 < m) ? (0x3C00u | (s1 << 15)) : 0u;
+        out[p2] = e0 | (e1 << 16);
+    }
+    *reinterpret_cast<uint4*>(a_stage + off_a) = make_uint4(out[0], out[1], out[2], out[3]);
+    *reinterpret_cast<uint4*>(a_stage + off_b) = make_uint4(out[4], out[5], out[6], out[7]);
+}
+
+__global__ void __launch_bounds__(kRThreads, 1)
+sketch_rad_u8_kernel(const __grid_constant__ RadArgs a, int* status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t* A = smem;                                   // kRBuf x C tiles
+    uint8_t* B = smem + kRBuf * kRAStage;                // kRBuf x 512-row FP16 tiles
+    uint64_t* bars = reinterpret_cast<uint64_t*>(B + kRBuf * kRBStage);
+    uint64_t* ab_full = bars;                            // [kRBuf] A and B written
+    uint64_t* mma_done = bars + kRBuf;                   // [kRBuf] read by the MMAs
+    uint64_t* accum_done = bars + 2 * kRBuf;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum_done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int k = a.k;
+    const int split = blockIdx.y;
+    const int row0 = blockIdx.x * 128;
+    const int nslot0 = a.nslot[0], nslot1 = a.nslot[1];
+    const int step0 = split * a.steps_per_split;
+    int nsteps = a.total_steps - step0;
+    if (nsteps > a.steps_per_split) nsteps = a.steps_per_split;
+    if (nsteps < 0) nsteps = 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kRBuf; ++s) {
+            tc::mbar_init(&ab_full[s], kRGenWarps);
+            tc::mbar_init(&mma_done[s], 1);
+        }
+        tc::mbar_init(accum_done, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    // rows no segment covers must read as zero: clear the B stages once
+    for (uint32_t off = tid * 16u; off < kRBuf * kRBStage; off += kRThreads * 16u)
+        *reinterpret_cast<uint4*>(B + off) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_proxy_async_smem();
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc0 = tc::idesc_f16_f32(128, nslot0 > 0 ? nslot0 : 16);
+            const uint32_t idesc1 = tc::idesc_f16_f32(128, nslot1 > 0 ? nslot1 : 16);
+            int s = 0;
+            uint32_t ph = 0;
+            for (int ks = 0; ks < nsteps; ++ks) {
+                if (!tc::mbar_wait(&ab_full[s], ph, abort_flag, status)) break;
+                tc::tc_fence_after();
+                const uint32_t a_base = tc::smem_u32(A + s * kRAStage);
+                const uint32_t b_base = tc::smem_u32(B + s * kRBStage);
+#pragma unroll
+                for (int slot = 0; slot < 2; ++slot) {
+                    if ((slot ? nslot1 : nslot0) == 0) continue;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t bdesc = tc::desc_sw128(b_base + slot * kRSlotBytes + kk * 32);
+                        const uint64_t adesc = tc::desc_sw128(a_base + kk * 32);
+                        tc::mma_f16(tmem_base + slot * kAccCols, adesc, bdesc, slot ? idesc1 : idesc0,
+                                    (ks | kk) ? 1u : 0u);
+                    }
+                }
+                tc::mma_commit(&mma_done[s]);
+                if (++s == kRBuf) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            tc::mma_commit(accum_done);   // fires once every MMA issued above has finished
+        }
+    } else {
+        // ---------------- generators / converters (warps 1-16) ----------------
+        const int g = tid - 32;
+        // C item and the converted B rows: row r (+ 128 t), 16 pixels pg
+        const int r = g >> 2, pg = g & 3;
+        const uint32_t off_a = tc::sw128_offset(static_cast<uint32_t>(r), static_cast<uint32_t>(2 * pg));
+        const uint32_t off_b = tc::sw128_offset(static_cast<uint32_t>(r), static_cast<uint32_t>(2 * pg + 1));
+        // B rows r + 128 t (t < 4) differ from row r by 16 KB in the layout
+        const uint8_t* src[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int row = r + 128 * t;
+            const int slot = row >> 8;
+            src[t] = nullptr;
+            if (row - 256 * slot < (slot ? nslot1 : nslot0)) {
+                for (int i = 0; i < a.nseg; ++i) {
+                    const RadSeg& sg = a.seg[i];
+                    if (row >= sg.row0 && row < sg.row0 + sg.L)
+                        src[t] = sg.D + static_cast<int64_t>(row - sg.row0) * sg.ldd + 16 * pg;
+                }
+            }
+        }
+        const int64_t m = a.m;
+        // no pixel of this split's K steps lies past m: loads need no tail checks
+        const bool full = static_cast<int64_t>(step0 + nsteps) * kRKStep <= m;
+        // bytes of K steps 0 and 1
+        uint4 buf[kRBuf][4];
+#pragma unroll
+        for (int d = 0; d < kRBuf; ++d)
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                buf[d][t] = d < nsteps ? load_row16(src[t], static_cast<int64_t>(step0 + d) * kRKStep, m)
+                                       : make_uint4(0u, 0u, 0u, 0u);
+        uint32_t ph = 0;      // parity of the current use of the stages
+        bool ok = true;
+        // after an abort the remaining steps only skip their work
+        for (int kb = 0; kb < nsteps; kb += kRBuf) {
+#pragma unroll
+            for (int s = 0; s < kRBuf; ++s) {
+                const int ks = kb + s;
+                if (ks >= nsteps) break;
+                // the stage is free once the MMAs of its previous use finished
+                // (lane 0 waits for the warp, then the warp syncs)
+                if (kb > 0 && ok) {
+                    bool free_ok = true;
+                    if (lane == 0) {
+                        free_ok = tc::mbar_wait(&mma_done[s], ph ^ 1u, abort_flag, status);
+                    }
+                    __syncwarp();
+                    ok = __shfl_sync(0xffffffffu, free_ok ? 1 : 0, 0) != 0;
+                }
+                const int64_t j0 = static_cast<int64_t>(step0 + ks) * kRKStep;
+                uint8_t* a_stage = A + s * kRAStage;
+                uint8_t* b_stage = B + s * kRBStage;
+                if (ok) {
+                    draw_rademacher_f16(a_stage, off_a, off_b, lane, r, pg, row0, k, j0, m, a.rk);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (src[t] != nullptr)
+                            convert_row16(b_stage, off_a + t * 16384u, off_b + t * 16384u, buf[s][t]);
+                }
+                // every lane's writes are ordered before the async proxy's
+                // reads, then one arrival per warp
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0 && ok) tc::mbar_arrive(&ab_full[s]);
+                // the bytes of K step ks + kRBuf into the registers just used
+                if (ks + kRBuf < nsteps && ok) {
+                    if (full) {
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) buf[s][t] = load_row16_full(src[t], j0 + kRBuf * kRKStep);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) buf[s][t] = load_row16(src[t], j0 + kRBuf * kRKStep, m);
+                    }
+                }
+            }
+            ph ^= 1u;
+        }
+        // ---------------- epilogue: partials of every used B row ----------------
+        const bool done = tc::mbar_wait(accum_done, 0u, abort_flag, status) && !*abort_flag;
+        tc::tc_fence_after();
+        if (done) {
+            const int quarter = warp & 3;
+            const int cg = (warp - 1) >> 2;                 // column group 0 .. 3
+            const int row = row0 + quarter * 32 + lane;
+            float* part = a.part + static_cast<int64_t>(split) * kRadRows * k;
+            for (int slot = 0; slot < 2; ++slot) {
+                for (int c0 = 16 * cg; c0 < (slot ? nslot1 : nslot0); c0 += 64) {
+                    uint32_t v[16];
+                    tc::tmem_ld_x16(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + slot * kAccCols + c0, v);
+                    tc::tmem_wait_ld();
+                    if (row < k) {
+#pragma unroll
+                        for (int qq = 0; qq < 16; ++qq)
+                            part[static_cast<int64_t>(slot * 256 + c0 + qq) * k + row] = __uint_as_float(v[qq]);
+                    }
+                }
+            }
+        }
+    }
+    // teardown: every MMA has finished (accum_done) before TMEM is released
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        if (*abort_flag) tc::mbar_wait(accum_done, 0u, abort_flag, status, 2000000000ull);
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+// DY of segment blockIdx.y: DY[(f0 + t) k + i] = sum_s part[s][row0 + t][i], FP64, fixed order.
+__global__ void sketch_rad_reduce_kernel(const __grid_constant__ RadArgs a, int splits, int* status) {
+    const RadSeg sg = a.seg[blockIdx.y];
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t total = static_cast<int64_t>(sg.L) * a.k;
+    if (idx >= total) return;
+    const int64_t src = static_cast<int64_t>(sg.row0) * a.k + idx;
+    const int64_t stride = static_cast<int64_t>(kRadRows) * a.k;
+    double s = 0.0;
+    for (int sp = 0; sp < splits; ++sp) s += static_cast<double>(a.part[sp * stride + src]);
+    if (!isfinite(s)) record_status(status, CDMD_ERR_NONFINITE);
+    sg.DY[static_cast<int64_t>(sg.f0) * a.k + idx] = s;
+}
+
 // DY_g[t*k + i] = sum_s part_g[(s*n_g + t)*k + i], FP64, fixed order; blockIdx.y = clip.
 __global__ void sketch_tc_reduce_kernel(const SketchArgs a, int splits, double* DY0, double* DY1, int* status) {
     const int g = blockIdx.y;
@@ -836,6 +1173,75 @@ cdmd_status launch_sketch_tc_unit(cdmd_ctx* ctx, int nclips, const uint8_t* cons
     return CDMD_OK;
 }
 
+// Shared sketch of several clips under one Rademacher C from the uint8 frames
+// (no BF16 copies); launches of up to 512 packed frames.
+cdmd_status launch_sketch_rad_u8(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
+                                 const int64_t* ldd, int k, uint64_t seed, double* const* DY, cudaStream_t stream) {
+    if (m > (static_cast<int64_t>(1) << 31) - kRKStep)
+        return fail(CDMD_ERR_UNSUPPORTED, "packed sketch: m = %lld pixels (at most 2^31 - 64)", static_cast<long long>(m));
+    const int rowblks = (k + 127) / 128;
+    const int64_t total_steps = (m + kRKStep - 1) / kRKStep;
+    int64_t splits = std::max<int64_t>(1, ctx->num_sms / rowblks);
+    splits = std::min<int64_t>(splits, total_steps);
+    const int64_t steps_per_split = (total_steps + splits - 1) / splits;
+    splits = (total_steps + steps_per_split - 1) / steps_per_split;
+    float* part = nullptr;
+    cdmd_status st = ensure_buffer(ctx, BUF_SKETCH_PARTIAL, static_cast<size_t>(splits) * kRadRows * k * sizeof(float),
+                                   reinterpret_cast<void**>(&part));
+    if (st != CDMD_OK) return st;
+    const size_t smem = rad_smem_bytes() + 1024;
+    if (smem > kMaxSmem) return fail(CDMD_ERR_UNSUPPORTED, "packed sketch: %zu bytes of shared memory per CTA", smem);
+    // the attribute is the largest any launch of this kernel uses (the same
+    // for every call, so concurrent host threads never lower it)
+    CDMD_CHECK_CUDA(cudaFuncSetAttribute(sketch_rad_u8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kMaxSmem)));
+    RadArgs a{};
+    a.part = part;
+    a.k = k;
+    a.m = m;
+    a.steps_per_split = static_cast<int>(steps_per_split);
+    a.total_steps = static_cast<int>(total_steps);
+    a.rk = philox_round_keys(seed_key(seed));
+    int rows = 0;     // B rows used so far in this launch (a multiple of 8)
+    auto flush = [&]() -> cdmd_status {
+        if (a.nseg == 0) return CDMD_OK;
+        a.nslot[0] = rows >= 256 ? 256 : (rows + 15) / 16 * 16;
+        a.nslot[1] = rows > 256 ? (rows - 256 + 15) / 16 * 16 : 0;
+        int maxL = 0;
+        for (int i = 0; i < a.nseg; ++i) maxL = std::max(maxL, a.seg[i].L);
+        sketch_rad_u8_kernel<<<dim3(rowblks, static_cast<unsigned>(splits)), kRThreads, smem, stream>>>(a, ctx->d_status);
+        CDMD_CHECK_LAUNCH("sketch_rad_u8_kernel");
+        const int64_t tot = static_cast<int64_t>(maxL) * k;
+        sketch_rad_reduce_kernel<<<dim3(static_cast<unsigned>((tot + 255) / 256), a.nseg), 256, 0, stream>>>(
+            a, static_cast<int>(splits), ctx->d_status);
+        CDMD_CHECK_LAUNCH("sketch_rad_reduce_kernel");
+        a.nseg = 0;
+        rows = 0;
+        return CDMD_OK;
+    };
+    for (int i = 0; i < nclips; ++i) {
+        for (int f = 0; f < n[i];) {
+            if (a.nseg == kRadMaxSeg || rows == kRadRows) {
+                st = flush();
+                if (st != CDMD_OK) return st;
+            }
+            const int space = 256 - (rows & 255);            // rows left in the current slot
+            const int L = std::min(n[i] - f, space);
+            RadSeg& sg = a.seg[a.nseg];
+            sg.DY = DY[i];
+            sg.D = D[i] + static_cast<int64_t>(f) * ldd[i];
+            sg.ldd = ldd[i];
+            sg.row0 = rows;
+            sg.L = L;
+            sg.f0 = f;
+            ++a.nseg;
+            rows += (L + 7) / 8 * 8;
+            f += L;
+        }
+    }
+    return flush();
+}
+
 cdmd_status check_tc_video(const uint8_t* D, int64_t ldd) {
     if ((reinterpret_cast<uintptr_t>(D) & 15) != 0 || (ldd & 15) != 0)
         return fail(CDMD_ERR_INVALID_ARG, "BF16X2 sketch needs a 16-byte aligned video and ldd %% 16 == 0");
@@ -869,6 +1275,7 @@ cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* co
         if (st != CDMD_OK) return st;
     }
     if (nclips == 1) return launch_sketch_tc(ctx, D[0], m, n[0], ldd[0], ctype, k, seed, DY[0], stream);
+    if (ctype == CDMD_C_RADEMACHER) return launch_sketch_rad_u8(ctx, nclips, D, m, n, ldd, k, seed, DY, stream);
     // BF16 copies of every clip's frames (one HBM-bound pass each)
     const int64_t ldw = (m + 15) / 16 * 16;
     size_t elems = 0;
@@ -896,7 +1303,7 @@ cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* co
                        reinterpret_cast<void**>(&part));
     if (st != CDMD_OK) return st;
     const size_t smem = pack_smem_bytes() + 1024;
-    auto packed = ctype == CDMD_C_RADEMACHER ? sketch_tc_packed_kernel<true> : sketch_tc_packed_kernel<false>;
+    auto packed = sketch_tc_packed_kernel;
     CDMD_CHECK_CUDA(cudaFuncSetAttribute(packed, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     PackArgs a{};
     a.part = part;

@@ -194,6 +194,14 @@ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t chunk16)
     return (row >> 3) * 1024u + (row & 7u) * 128u + ((chunk16 ^ (row & 7u)) << 4);
 }
 
+// Both FP16 halves of x minus 1024 (exact for halves 1024 .. 2047): with the
+// byte permute 0x6400 | b = 1024 + b, the exact FP16 value of a uint8 b.
+__device__ __forceinline__ uint32_t sub_1024_f16x2(uint32_t x) {
+    uint32_t r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(0x64006400u));
+    return r;
+}
+
 // BF16 bits of a float by truncation (exact when the float has <= 8
 // significant bits) and round-to-nearest packing of two floats.
 __device__ __forceinline__ uint32_t pack_bf16_rn(float lo_k, float hi_k) {
