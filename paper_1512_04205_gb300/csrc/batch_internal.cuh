@@ -55,6 +55,7 @@ struct GroupedPlan {
     const SubtractItem* tc_items = nullptr;
     int tc_nitems = 0;
     int tc_max_n = 0;
+    int tc_max_ncols = 0;
 };
 
 struct GroupedClip {             // what the grouped launches need of a clip
@@ -114,25 +115,23 @@ struct SubtractItem {
     int64_t tile0, ntiles;
 };
 // Tensor-core subtract of one clip inside a grouped launch (mask only,
-// MODULUS or REAL, 32 <= n <= 256, ncols <= 16, aligned video).
+// MODULUS or REAL, 32 <= n <= 256, ncols <= 16, aligned video and Phi).
 struct SubTcClip {
-    const CUtensorMap* tmap;     // box 128 pixels x n frames, global memory
+    const CUtensorMap* tmap;     // box 64 pixels x n frames, 64-byte swizzle, global memory
     const float2* Phi;           // m x ncols complex
-    const float2* lam_t;         // lambda^t table [n][nc_pad]
-    const float2* amp;           // amplitude per column
+    SubTcTable tb;               // amplitudes and lambda^t tables of the clip
     uint32_t* mask;
     int64_t m;
     int n, ncols, nc_pad;
     int pad;
 };
 size_t subtract_tc_smem(int n);
+// Views of a table built by the (grouped) table kernel, column stride nc.
+SubTcTable subtract_tc_table(void* table, int n, int nc);
 int subtract_tc_tile_pixels();
 cdmd_status make_subtract_tc_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, int n, int64_t ldd);
-cdmd_status launch_subtract_tc_grouped(const SubTcClip* clips, const SubtractItem* items, int nitems, int max_n,
+cdmd_status launch_subtract_tc_grouped(const SubTcClip* clips, const SubtractItem* items, int nitems, int max_ncols,
                                        cdmd_bgmode mode, float tau, int* status, cudaStream_t stream);
-// Device addresses of the lambda^t table and the amplitudes inside a table
-// built by the grouped table kernel (column stride nc).
-void subtract_table_ptrs(void* table, int n, int nc, const float2** lam_t, const float2** amp);
 
 size_t subtract_table_bytes_nc(int n, int nc);
 size_t subtract_tma_smem(int n, int nc);

@@ -264,13 +264,24 @@ cdmd_status launch_sketch_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, 
 cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* const* D, int64_t m, const int* n,
                                     const int64_t* ldd, cdmd_ctype ctype, int k, uint64_t seed, double* const* DY,
                                     cudaStream_t stream);
+// The subtract pass's per-clip table as the tensor-core pass reads it: the
+// amplitudes and lambda^t powers per selected column and, when the selected
+// modes are real or complete conjugate pairs (hdr[1] = 1), per real term
+// (hdr[0] terms, Phi column term_col[e], amplitude term_amp[e]).
+struct SubTcTable {
+    const int* hdr;
+    const int* term_col;
+    const float2* amp;           // beta per column
+    const float2* term_amp;      // 2 beta per pair, beta per real mode
+    const float2* lam_t;         // lambda^t per column, [n][nc_pad]
+    const float2* term_lam_t;    // lambda^t per real term, [n][nc_pad]
+};
 // Pass (c) on the tensor cores for mask-only MODULUS / REAL calls with
-// 32 <= n <= 256 frames, ncols <= 16 and a 16-byte aligned video; lam_t and
-// amp are the lambda^t table [n][nc_pad] and the amplitudes (float2 each).
+// 32 <= n <= 1024 frames, ncols <= 16, a 16-byte aligned video and Phi.
 bool subtract_tc_supported(int n, int ncols, cdmd_bgmode mode, const uint8_t* D, int64_t ldd, int64_t m,
-                           const float* bg);
+                           const float* Phi, const float* bg);
 cdmd_status launch_subtract_tc(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd, const float* Phi,
-                               int ncols, const void* lam_t, const void* amp, int nc_pad, float tau, cdmd_bgmode mode,
+                               int ncols, const SubTcTable& tb, int nc_pad, float tau, cdmd_bgmode mode,
                                uint32_t* mask, cudaStream_t stream);
 cdmd_status launch_selftest_wait(cdmd_ctx* ctx, uint64_t limit_ns, cudaStream_t stream);
 cdmd_status launch_selftest_recip(const double* a, int64_t n, double* r, double* q, cudaStream_t stream);

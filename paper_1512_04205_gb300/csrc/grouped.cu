@@ -111,13 +111,16 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
     // REAL, 32 <= n <= 256) or else in the CUDA-core kernel
     const int tc_px = subtract_tc_tile_pixels();
     std::vector<int> tc_slot(clips.size(), -1);
-    int ntc_clips = 0, tc_max_n = 0;
+    int ntc_clips = 0, tc_max_n = 0, tc_max_ncols = 0;
     int64_t tc_tiles_all = 0;
     for (size_t i = 0; i < clips.size(); ++i) {
         const GroupedClip& c = clips[i];
-        if (mode != CDMD_BG_STATIC && c.n >= 32 && c.n <= 256 && c.ncols <= 16) {
+        if (mode != CDMD_BG_STATIC && c.n >= 32 && c.n <= 256 && c.ncols <= 16 &&
+            reinterpret_cast<uintptr_t>(c.buf->Phi) % 16 == 0 && reinterpret_cast<uintptr_t>(c.D) % 16 == 0 &&
+            c.ldd % 16 == 0) {
             tc_slot[i] = ntc_clips++;
             tc_max_n = std::max(tc_max_n, c.n);
+            tc_max_ncols = std::max(tc_max_ncols, c.ncols);
             tc_tiles_all += (c.m + tc_px - 1) / tc_px;
         }
     }
@@ -258,7 +261,7 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
             SubTcClip t{};
             t.tmap = dtm_tc + q;
             t.Phi = reinterpret_cast<const float2*>(c.buf->Phi);
-            subtract_table_ptrs(dev + o_table[i], c.n, nc, &t.lam_t, &t.amp);
+            t.tb = subtract_tc_table(dev + o_table[i], c.n, nc);
             t.mask = c.mask;
             t.m = c.m;
             t.n = c.n;
@@ -306,6 +309,7 @@ cdmd_status grouped_build(GroupedPlan* g, const std::vector<GroupedClip>& clips,
     g->tc_items = reinterpret_cast<const SubtractItem*>(dev + o_tcitems);
     g->tc_nitems = static_cast<int>(tci.size());
     g->tc_max_n = tc_max_n;
+    g->tc_max_ncols = tc_max_ncols;
     return CDMD_OK;
 }
 
@@ -319,7 +323,8 @@ cdmd_status grouped_subtract(const GroupedPlan* g, cdmd_bgmode mode, float tau, 
     cdmd_status st = launch_subtract_grouped(g->sb_clips, g->sb_nclips, g->sb_items, g->sb_nitems, g->sb_nc,
                                              g->sb_max_n, mode, tau, status, stream);
     if (st != CDMD_OK || g->tc_nitems == 0) return st;
-    return launch_subtract_tc_grouped(g->tc_clips, g->tc_items, g->tc_nitems, g->tc_max_n, mode, tau, status, stream);
+    return launch_subtract_tc_grouped(g->tc_clips, g->tc_items, g->tc_nitems, g->tc_max_ncols, mode, tau, status,
+                                      stream);
 }
 
 }  // namespace cdmd

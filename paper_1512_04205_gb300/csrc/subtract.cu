@@ -4,8 +4,10 @@
 //   bg_jt = | sum_c Phi_jc beta_{s_c} lambda_{s_c}^t |   (Eq. DMDTerms, MODULUS)
 //   mask_jt = |x_jt - bg_jt| > tau                       (Eq. thres, strict)
 //
-// subtract_table_kernel (one warp) forms lambda^t for t < n by repeated FP64
-// multiplication and the amplitudes.  It also classifies the selected modes:
+// subtract_table_kernel (one block: lane = selected column, eight warps =
+// eight blocks of frames) forms lambda^t for t < n in FP64, each warp from
+// lambda^t0 by binary powering and then by repeated multiplication, and the
+// amplitudes.  It also classifies the selected modes:
 // the video is real, so the modes of a real A~ come as real eigenvalues and
 // conjugate pairs with conjugate modes and (least-squares) amplitudes, and a
 // pair contributes phi b lambda^t + conj(phi b lambda^t) = 2 Re(phi b lambda^t).
@@ -25,6 +27,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxCols = 32;
+constexpr int kTableThreads = 256;     // table kernel: 8 warps, one block of frames each
 
 // Table layout (one allocation):
 //   hdr[4] int32            nterms, real_only
@@ -61,7 +64,11 @@ __host__ __device__ inline Table table_views(void* base, int n, int nc_pad) {
 __device__ __forceinline__ void build_table(const int32_t* __restrict__ cols, int ncols, int nc_pad,
                                             const double* __restrict__ beta, const double* __restrict__ lambda, int r,
                                             int n, const Table& tb) {
-    const int c = threadIdx.x;
+    // lane c = selected column; warp w = block w of the frames (every warp
+    // classifies the columns the same way, warp 0 writes the per-column data)
+    const int c = threadIdx.x & 31;
+    const int wb = threadIdx.x >> 5;
+    const int nwb = blockDim.x >> 5;
     int s = -1;
     if (c < ncols) s = cols ? cols[c] : c;
     const bool ok = (s >= 0 && s < r);
@@ -96,25 +103,45 @@ __device__ __forceinline__ void build_table(const int32_t* __restrict__ cols, in
     const unsigned tmask = __ballot_sync(0xffffffffu, term);
     const bool real_only = __ballot_sync(0xffffffffu, lone) == 0u;
     const int u = __popc(tmask & ((1u << c) - 1u));
-    if (c == 0) {
+    if (c == 0 && wb == 0) {
         tb.hdr[0] = __popc(tmask);
         tb.hdr[1] = real_only ? 1 : 0;
     }
     if (c >= nc_pad) return;
-    tb.amp[c] = ok ? make_float2(static_cast<float>(br), static_cast<float>(bi)) : make_float2(0.f, 0.f);
     const double scale = lead ? 2.0 : 1.0;
-    if (term) {
-        tb.term_col[u] = c;
-        tb.term_amp[u] = make_float2(static_cast<float>(scale * br), static_cast<float>(scale * bi));
-    }
-    // unused real-term slots: zero amplitude, zero powers
     const int nt = __popc(tmask);
-    if (c >= nt) {
-        tb.term_col[c] = 0;
-        tb.term_amp[c] = make_float2(0.f, 0.f);
+    if (wb == 0) {
+        tb.amp[c] = ok ? make_float2(static_cast<float>(br), static_cast<float>(bi)) : make_float2(0.f, 0.f);
+        if (term) {
+            tb.term_col[u] = c;
+            tb.term_amp[u] = make_float2(static_cast<float>(scale * br), static_cast<float>(scale * bi));
+        }
+        // unused real-term slots: zero amplitude, zero powers
+        if (c >= nt) {
+            tb.term_col[c] = 0;
+            tb.term_amp[c] = make_float2(0.f, 0.f);
+        }
     }
+    // frames t0 .. t1-1 of this warp: lambda^t0 by binary powering, then
+    // repeated multiplication
+    const int per = (n + nwb - 1) / nwb;
+    const int t0 = wb * per;
+    const int t1 = t0 + per < n ? t0 + per : n;
     double pr = 1.0, pi = 0.0;
-    for (int t = 0; t < n; ++t) {
+    {
+        double xr = lr, xi = li;
+        for (int e = t0; e > 0; e >>= 1) {
+            if (e & 1) {
+                const double nr = pr * xr - pi * xi;
+                pi = pr * xi + pi * xr;
+                pr = nr;
+            }
+            const double sr = xr * xr - xi * xi;
+            xi = 2.0 * xr * xi;
+            xr = sr;
+        }
+    }
+    for (int t = t0; t < t1; ++t) {
         const float2 v = ok ? make_float2(static_cast<float>(pr), static_cast<float>(pi)) : make_float2(0.f, 0.f);
         tb.table[static_cast<int64_t>(t) * nc_pad + c] = v;
         if (term) tb.ttable[static_cast<int64_t>(t) * nc_pad + u] = v;
@@ -126,14 +153,14 @@ __device__ __forceinline__ void build_table(const int32_t* __restrict__ cols, in
     }
 }
 
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(kTableThreads)
 subtract_table_kernel(const int32_t* __restrict__ cols, int ncols, int nc_pad, const double* __restrict__ beta,
                       const double* __restrict__ lambda, int r, int n, Table tb) {
     build_table(cols, ncols, nc_pad, beta, lambda, r, n, tb);
 }
 
-// Grouped: one warp per clip, tables with the common column stride nc.
-__global__ void __launch_bounds__(32)
+// Grouped: one block per clip, tables with the common column stride nc.
+__global__ void __launch_bounds__(kTableThreads)
 subtract_table_grouped_kernel(const SubtractClip* __restrict__ clips, int nc) {
     const SubtractClip c = clips[blockIdx.x];
     build_table(c.cols, c.ncols, nc, c.beta, c.lambda, c.r, c.n, table_views(c.table, c.n, nc));
@@ -634,10 +661,11 @@ cdmd_status launch_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, i
     cdmd_status st = ensure_buffer(ctx, BUF_SUBTRACT_TABLE, table_bytes(n, nc_pad), &tbl);
     if (st != CDMD_OK) return st;
     const Table tb = table_views(tbl, n, nc_pad);
-    subtract_table_kernel<<<1, 32, 0, stream>>>(cols, ncols, nc_pad, beta, lambda, r, n, tb);
+    subtract_table_kernel<<<1, kTableThreads, 0, stream>>>(cols, ncols, nc_pad, beta, lambda, r, n, tb);
     CDMD_CHECK_LAUNCH("subtract_table_kernel");
-    if (subtract_tc_supported(n, ncols, mode, D, ldd, m, bg))
-        return launch_subtract_tc(ctx, D, m, n, ldd, Phi, ncols, tb.table, tb.amp, nc_pad, tau, mode, mask, stream);
+    if (subtract_tc_supported(n, ncols, mode, D, ldd, m, Phi, bg))
+        return launch_subtract_tc(ctx, D, m, n, ldd, Phi, ncols, subtract_tc_table(tbl, n, nc_pad), nc_pad, tau, mode,
+                                  mask, stream);
     const float2* ph = reinterpret_cast<const float2*>(Phi);
     // TMA needs a 16-byte aligned base and row stride; n <= 512 keeps the
     // lambda^t table within shared memory next to the stages
@@ -669,10 +697,16 @@ namespace cdmd {
 
 size_t subtract_table_bytes_nc(int n, int nc) { return table_bytes(n, nc); }
 
-void subtract_table_ptrs(void* table, int n, int nc, const float2** lam_t, const float2** amp) {
+SubTcTable subtract_tc_table(void* table, int n, int nc) {
     const Table t = table_views(table, n, nc);
-    *lam_t = t.table;
-    *amp = t.amp;
+    SubTcTable r;
+    r.hdr = t.hdr;
+    r.term_col = t.term_col;
+    r.amp = t.amp;
+    r.term_amp = t.term_amp;
+    r.lam_t = t.table;
+    r.term_lam_t = t.ttable;
+    return r;
 }
 size_t subtract_tma_smem(int n, int nc) { return tma_smem_bytes(n, nc); }
 int subtract_tile_pixels() { return kTmaTile; }
@@ -683,7 +717,7 @@ cdmd_status make_subtract_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, in
 
 cdmd_status launch_subtract_grouped(const SubtractClip* clips, int nclips, const SubtractItem* items, int nitems,
                                     int nc, int max_n, cdmd_bgmode mode, float tau, int* status, cudaStream_t stream) {
-    subtract_table_grouped_kernel<<<static_cast<unsigned>(nclips), 32, 0, stream>>>(clips, nc);
+    subtract_table_grouped_kernel<<<static_cast<unsigned>(nclips), kTableThreads, 0, stream>>>(clips, nc);
     CDMD_CHECK_LAUNCH("subtract_table_grouped_kernel");
     if (nitems == 0) return CDMD_OK;
     const size_t smem = tma_smem_bytes(max_n, nc);

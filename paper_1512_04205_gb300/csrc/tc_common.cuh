@@ -96,6 +96,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// Untiled bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // ---- tcgen05 -------------------------------------------------------------------
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
@@ -213,8 +222,9 @@ __device__ __forceinline__ uint32_t pack_bf16_rn(float lo_k, float hi_k) {
 }  // namespace tc
 
 // Host: build a 2-D uint8 tensor map over a frame-major video
-// (dim0 = pixels, contiguous; dim1 = frames, stride ldd bytes).
+// (dim0 = pixels, contiguous; dim1 = frames, stride ldd bytes); swizzle_bytes
+// 0 (none), 64 or 128 selects the shared-memory swizzle of the box rows.
 cdmd_status make_video_tmap(CUtensorMap* map, const uint8_t* D, int64_t m, int n, int64_t ldd, int box_x,
-                            int box_y);
+                            int box_y, int swizzle_bytes = 0);
 
 }  // namespace cdmd

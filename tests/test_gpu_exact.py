@@ -153,10 +153,14 @@ def test_exact_dmd_pipeline_matches_oracle(C, ctx, seed, prec):
     f_gpu = O.fmeasure(got, clip.truth.T)[2]
     f_ref = O.fmeasure(ref_mask, clip.truth.T)[2]
     assert abs(f_gpu - f_ref) <= 1e-3, (f_gpu, f_ref)
-    # the whole-pipeline entry point gives the same mask
+    # the whole-pipeline entry point gives the same mask; it takes the
+    # tensor-core subtract (mask only, BF16 hi + lo background), so decisions
+    # within 0.01 grey of tau may differ from the CUDA-core pass above
     mask2 = C.cdmd_run_exact(ctx, D, C.make_params(1, r, K, tau, prec=prec))
     C.cdmd_status_sync(ctx)
-    assert torch.equal(mask2, mask)
+    near = np.abs(np.abs(Dm - bg) - tau) <= 0.01
+    assert near.mean() < 1e-3
+    assert np.array_equal(C.unpack_mask(mask2, clip.m)[~near], got[~near])
 
 
 def test_exact_dmd_rejects_bad_arguments(C, ctx):

@@ -137,10 +137,15 @@ def test_mixed_precision_pipeline_160x120(C, ctx, seed):
     f_gpu = O.fmeasure(got, clip.truth.T)[2]
     f_ref = O.fmeasure(ref_mask, clip.truth.T)[2]
     assert abs(f_gpu - f_ref) <= 1e-3, (f_gpu, f_ref)
-    # the whole-pipeline entry point gives the same mask
+    # the whole-pipeline entry point gives the same mask; it takes the
+    # tensor-core subtract (mask only, BF16 hi + lo background, ~2^-16 per
+    # term), so decisions within 0.01 grey of tau may differ from the
+    # CUDA-core pass that also wrote the background above
     mask2 = C.cdmd_run(ctx, D, C.make_params(k, r, K, tau, seed=cseed, prec="bf16x2"))
     C.cdmd_status_sync(ctx)
-    assert np.array_equal(mask2.cpu().numpy(), mask.cpu().numpy())
+    near = np.abs(np.abs(Dm - bg) - tau) <= 0.01
+    assert near.mean() < 1e-3
+    assert np.array_equal(C.unpack_mask(mask2, clip.m)[~near], got[~near])
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x2"])

@@ -3,11 +3,15 @@
 16-byte aligned video) against
 the FP64 oracle's background formula and threshold.
 
-The background is a small GEMM in 3xTF32 (about 2^-19 relative per term),
-so the mask must equal the oracle's wherever |x - bg| sits more than 0.01
-grey away from tau, the same margin the CUDA-core pass meets; and it must
-equal the CUDA-core pass's mask (taken with a background output, which stays
-on that pass) there too."""
+The background is a small GEMM in BF16 hi + lo with the three leading
+products laid along K (about 2^-16 relative per term; the mode sums here stay
+below a few hundred grey levels, so the error stays below 0.01 grey), so the
+mask must equal the oracle's wherever |x - bg| sits more than 0.01 grey away
+from tau, the same margin the CUDA-core pass meets; and it must equal the
+CUDA-core pass's mask (taken with a background output, which stays on that
+pass) there too.  Selections of real modes and complete conjugate pairs take
+the real-sum form (one real term per pair, Re only); a lone complex mode
+(r >= 5 here) takes the complex form."""
 import numpy as np
 import pytest
 
