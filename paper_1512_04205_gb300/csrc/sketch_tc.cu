@@ -717,6 +717,236 @@ sketch_tc_packed_kernel(const __grid_constant__ PackArgs a, int* status) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed form on CTA pairs (cta_group::2): the CTAs of row blocks 2c and 2c + 1
+// form a cluster and one 2-SM MMA (M = 256) covers both 128-row tiles of C.
+// Each CTA draws its own tile of C (A) and holds half of every 256-row B slot
+// (rows 0-127 in the leader, rank 0; 128-255 in the other), so each copies
+// and reads half of the frames a single-CTA launch needs: the frame stages
+// shrink to 32 KB and four of them fit beside three stages of C (the draw of
+// step k + 3 then never waits for the MMAs of step k).
+//   warp 0      TMA (both CTAs): this CTA's segments of each stage, on its
+//               own stage barrier (so each CTA can drain its own copies
+//               before it leaves)
+//   warp 2      the other CTA: when its half of a stage has landed, arrives
+//               on the leader's barrier for that stage (cluster scope)
+//   warp 1      leader: the pair MMAs (N = 256 per used slot), commits to
+//               the stage barriers of both CTAs (multicast)
+//   warp 3      the other CTA: when its tile of C is drawn, arrives on the
+//               leader's barrier for that stage (cluster scope)
+//   warps 4-11  both CTAs: draw C; one arrival per warp on this CTA's
+//               barrier (a cluster-scope release costs about a thousand
+//               cycles, so only the relay threads pay it)
+//   warps 4-7   after the last K step: this CTA's accumulators (its 128
+//               rows of C x every frame column) to the FP32 partials
+// Segments never cross a 128-row half (the host cuts them there).
+// ---------------------------------------------------------------------------
+constexpr int kQAStages = 3;
+constexpr int kQBStages = 4;
+constexpr uint32_t kQBStage = kPackRows * 128u / 2u;     // this CTA's half of 512 B rows
+constexpr uint32_t kQHalf = 128u * 128u;                 // one slot's half: 128 rows x 128 bytes
+
+__host__ __device__ inline uint32_t pair_smem_bytes() {
+    return kQAStages * kPackAStage + kQBStages * kQBStage + (3 * kQAStages + 3 * kQBStages + 1) * 8 + 64;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+sketch_tc_pair_kernel(const __grid_constant__ PackArgs a, int* status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t* A = smem;
+    uint8_t* B = smem + kQAStages * kPackAStage;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(B + kQBStages * kQBStage);
+    uint64_t* tma_full = bars;                          // [kQBStages] this CTA's half landed
+    uint64_t* b_free = bars + kQBStages;                // [kQBStages] pair MMAs done with the frames
+    uint64_t* peer_ready = bars + 2 * kQBStages;        // [kQBStages] leader: the other half landed
+    uint64_t* a_full = bars + 3 * kQBStages;            // [kQAStages] leader: both tiles of C drawn
+    uint64_t* a_free = a_full + kQAStages;              // [kQAStages] pair MMAs done with C
+    uint64_t* a_local = a_free + kQAStages;             // [kQAStages] this CTA's tile of C drawn
+    uint64_t* accum_done = a_local + kQAStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum_done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int k = a.k;
+    const uint32_t crank = tc::cluster_ctarank();
+    const bool leader = crank == 0;
+    const int split = blockIdx.y;
+    const int row0 = blockIdx.x * 128;
+    const int64_t step0 = static_cast<int64_t>(split) * a.steps_per_split;
+    int64_t nsteps = a.total_steps - step0;
+    if (nsteps > a.steps_per_split) nsteps = a.steps_per_split;
+    if (nsteps < 0) nsteps = 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kQBStages; ++s) {
+            tc::mbar_init(&tma_full[s], 1);
+            tc::mbar_init(&b_free[s], 1);
+            tc::mbar_init(&peer_ready[s], 1);
+        }
+        for (int s = 0; s < kQAStages; ++s) {
+            tc::mbar_init(&a_full[s], 8 + 1);          // the leader's drawing warps + the other CTA's relay
+            tc::mbar_init(&a_free[s], 1);
+            tc::mbar_init(&a_local[s], 8);
+        }
+        tc::mbar_init(accum_done, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    // rows no segment covers must read as zero: clear this CTA's B stages once
+    for (uint32_t off = tid * 16u; off < kQBStages * kQBStage; off += kThreads * 16u)
+        *reinterpret_cast<uint4*>(B + off) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_proxy_async_smem();
+    if (warp == 0) {
+        tc::tmem_alloc_cg2(tmem_slot, kTmemCols);
+        tc::tmem_relinquish_cg2();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    // both CTAs' barriers exist before either signals the other's
+    tc::cluster_sync_all();
+    tc::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer (both CTAs) ----------------
+        if (lane == 0) {
+            uint32_t bytes_own = 0;
+            for (int i = 0; i < a.nseg; ++i)
+                if (static_cast<uint32_t>((a.seg[i].row0 & 255) >> 7) == crank)
+                    bytes_own += static_cast<uint32_t>(a.seg[i].L) * 128u;
+            for (int64_t ks = 0; ks < nsteps; ++ks) {
+                const int s = static_cast<int>(ks % kQBStages);
+                const uint32_t u = static_cast<uint32_t>(ks / kQBStages);
+                // this CTA's half of the stage is free once the pair MMAs that read it finished
+                if (u >= 1 && !tc::mbar_wait_cl(&b_free[s], (u - 1) & 1u, abort_flag, status)) break;
+                tc::mbar_arrive_expect_tx(&tma_full[s], bytes_own);
+                const int x = static_cast<int>((step0 + ks) * kKStep);
+                for (int i = 0; i < a.nseg; ++i) {
+                    const int r0 = a.seg[i].row0;
+                    if (static_cast<uint32_t>((r0 & 255) >> 7) != crank) continue;
+                    uint8_t* dst = B + s * kQBStage + static_cast<uint32_t>(r0 >> 8) * kQHalf +
+                                   static_cast<uint32_t>(r0 & 127) * 128u;
+                    tc::tma_load_2d(dst, &a.tmap[i], x, a.seg[i].f0, &tma_full[s]);
+                }
+            }
+            // drain: this CTA's last copies of each stage have landed before it
+            // leaves (bounded in time only: an abort elsewhere must not cut it short)
+            volatile int no_abort = 0;
+            for (int s = 0; s < kQBStages; ++s) {
+                const int64_t uses = (nsteps - s + kQBStages - 1) / kQBStages;
+                if (uses >= 1) tc::mbar_wait(&tma_full[s], static_cast<uint32_t>(uses - 1) & 1u, &no_abort, status);
+            }
+        }
+    } else if (warp == 3) {
+        // ---------------- relay of the drawn C tiles (the other CTA) ----------------
+        if (lane == 0 && !leader) {
+            for (int64_t ks = 0; ks < nsteps; ++ks) {
+                const int sa = static_cast<int>(ks % kQAStages);
+                if (!tc::mbar_wait(&a_local[sa], static_cast<uint32_t>(ks / kQAStages) & 1u, abort_flag, status))
+                    break;
+                tc::mbar_arrive_cluster(tc::mapa_u32(tc::smem_u32(&a_full[sa]), 0u));
+            }
+        }
+    } else if (warp == 2) {
+        // ---------------- forwarder (the other CTA) ----------------
+        if (lane == 0 && !leader) {
+            for (int64_t ks = 0; ks < nsteps; ++ks) {
+                const int s = static_cast<int>(ks % kQBStages);
+                if (!tc::mbar_wait(&tma_full[s], static_cast<uint32_t>(ks / kQBStages) & 1u, abort_flag, status))
+                    break;
+                tc::mbar_arrive_cluster(tc::mapa_u32(tc::smem_u32(&peer_ready[s]), 0u));
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (leader) ----------------
+        if (lane == 0 && leader) {
+            const uint32_t idesc = tc::idesc_bf16_f32(256, 256);
+            for (int64_t ks = 0; ks < nsteps; ++ks) {
+                const int s = static_cast<int>(ks % kQBStages);
+                const uint32_t pb = static_cast<uint32_t>(ks / kQBStages) & 1u;
+                const int sa = static_cast<int>(ks % kQAStages);
+                const uint32_t pa = static_cast<uint32_t>(ks / kQAStages) & 1u;
+                if (!tc::mbar_wait_cl(&a_full[sa], pa, abort_flag, status)) break;
+                if (!tc::mbar_wait(&tma_full[s], pb, abort_flag, status)) break;
+                if (!tc::mbar_wait_cl(&peer_ready[s], pb, abort_flag, status)) break;
+                tc::tc_fence_after();
+                const uint32_t a_base = tc::smem_u32(A + sa * kPackAStage);
+                const uint32_t b_base = tc::smem_u32(B + s * kQBStage);
+#pragma unroll
+                for (int slot = 0; slot < 2; ++slot) {
+                    if (a.nslot[slot] == 0) continue;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t bdesc = tc::desc_sw128(b_base + slot * kQHalf + kk * 32);
+#pragma unroll
+                        for (int hl = 0; hl < 2; ++hl) {
+                            const uint64_t adesc = tc::desc_sw128(a_base + hl * kTileBytes + kk * 32);
+                            tc::mma_bf16_cg2(tmem_base + slot * kAccCols, adesc, bdesc, idesc,
+                                             (ks | kk | hl) ? 1u : 0u);
+                        }
+                    }
+                }
+                tc::mma_commit_cg2(&b_free[s], 3);
+                tc::mma_commit_cg2(&a_free[sa], 3);
+            }
+            tc::mma_commit_cg2(accum_done, 3);
+        }
+    } else if (warp >= 4) {
+        // ---------------- C generators (warps 4-11, both CTAs) ----------------
+        const int gt = tid - 128;
+        const PhiloxKeys rk = philox_round_keys(a.key);
+        for (int64_t ks = 0; ks < nsteps; ++ks) {
+            const int sa = static_cast<int>(ks % kQAStages);
+            const uint32_t u = static_cast<uint32_t>(ks / kQAStages);
+            if (u >= 1 && !tc::mbar_wait_cl(&a_free[sa], (u - 1) & 1u, abort_flag, status)) break;
+            draw_c_tiles(A + sa * kPackAStage, gt, 1, row0, k, (step0 + ks) * kKStep, a.m, rk);
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(leader ? &a_full[sa] : &a_local[sa]);
+        }
+        // ---------------- epilogue (warps 4-7): this CTA's 128 rows ----------------
+        if (warp < 8) {
+            const bool ok = tc::mbar_wait_cl(accum_done, 0u, abort_flag, status) && !*abort_flag;
+            tc::tc_fence_after();
+            if (ok) {
+                const int quarter = warp & 3;
+                const int row = row0 + quarter * 32 + lane;
+                float* part = a.part + static_cast<int64_t>(split) * kPackRows * k;
+                for (int slot = 0; slot < 2; ++slot) {
+                    for (int c0 = 0; c0 < a.nslot[slot]; c0 += 16) {
+                        uint32_t v[16];
+                        tc::tmem_ld_x16(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + slot * kAccCols + c0,
+                                        v);
+                        tc::tmem_wait_ld();
+                        if (row < k) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                part[static_cast<int64_t>(slot * 256 + c0 + q) * k + row] = __uint_as_float(v[q]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1 && lane == 0) {
+        // no pair MMA may still read either CTA's shared memory or write
+        // tensor memory when the CTAs leave: wait for the last commit
+        volatile int no_abort = 0;
+        tc::mbar_wait_cl(accum_done, 0u, &no_abort, status);
+    }
+    __syncthreads();
+    tc::cluster_sync_all();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc_cg2(tmem_base, kTmemCols);
+    }
+}
+
 // DY of segment blockIdx.y: DY[(f0 + t) k + i] = sum_s part[s][row0 + t][i], FP64, fixed order.
 __global__ void sketch_packed_reduce_kernel(const __grid_constant__ PackArgs a, int splits, int* status) {
     const PackSeg sg = a.seg[blockIdx.y];
@@ -1305,8 +1535,11 @@ cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* co
     st = ensure_buffer(ctx, BUF_SKETCH_PARTIAL, static_cast<size_t>(splits) * kPackRows * k * sizeof(float),
                        reinterpret_cast<void**>(&part));
     if (st != CDMD_OK) return st;
-    const size_t smem = pack_smem_bytes() + 1024;
-    auto packed = sketch_tc_packed_kernel;
+    // CTA pairs (one 2-SM MMA over two 128-row tiles of C) when the row
+    // blocks pair up; single CTAs otherwise
+    const bool pairs = rowblks % 2 == 0;
+    const size_t smem = (pairs ? pair_smem_bytes() : pack_smem_bytes()) + 1024;
+    auto packed = pairs ? sketch_tc_pair_kernel : sketch_tc_packed_kernel;
     CDMD_CHECK_CUDA(cudaFuncSetAttribute(packed, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     PackArgs a{};
     a.part = part;
@@ -1322,7 +1555,23 @@ cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* co
         a.nslot[1] = rows > 256 ? (rows - 256 + 15) / 16 * 16 : 0;
         int maxL = 0;
         for (int i = 0; i < a.nseg; ++i) maxL = std::max(maxL, a.seg[i].L);
-        packed<<<dim3(rowblks, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(a, ctx->d_status);
+        if (pairs) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(static_cast<unsigned>(rowblks), static_cast<unsigned>(splits), 1);
+            cfg.blockDim = dim3(kThreads, 1, 1);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            CDMD_CHECK_CUDA(cudaLaunchKernelEx(&cfg, sketch_tc_pair_kernel, a, ctx->d_status));
+        } else {
+            packed<<<dim3(rowblks, static_cast<unsigned>(splits)), kThreads, smem, stream>>>(a, ctx->d_status);
+        }
         CDMD_CHECK_LAUNCH("sketch_tc_packed_kernel");
         const int64_t tot = static_cast<int64_t>(maxL) * k;
         sketch_packed_reduce_kernel<<<dim3(static_cast<unsigned>((tot + 255) / 256), a.nseg), 256, 0, stream>>>(
@@ -1338,7 +1587,9 @@ cdmd_status launch_sketch_tc_shared(cdmd_ctx* ctx, int nclips, const uint8_t* co
                 st = flush();
                 if (st != CDMD_OK) return st;
             }
-            const int space = 256 - (rows & 255);            // rows left in the current slot
+            // rows left in the current slot (in the current half of it for CTA
+            // pairs, where each half lives in one CTA)
+            const int space = pairs ? 128 - (rows & 127) : 256 - (rows & 255);
             const int L = std::min(n[i] - f, space);
             PackSeg& sg = a.seg[a.nseg];
             sg.DY = DY[i];
