@@ -723,8 +723,9 @@ sketch_tc_packed_kernel(const __grid_constant__ PackArgs a, int* status) {
 // Each CTA draws its own tile of C (A) and holds half of every 256-row B slot
 // (rows 0-127 in the leader, rank 0; 128-255 in the other), so each copies
 // and reads half of the frames a single-CTA launch needs: the frame stages
-// shrink to 32 KB and four of them fit beside three stages of C (the draw of
-// step k + 3 then never waits for the MMAs of step k).
+// shrink to 32 KB and three of them fit beside four stages of C (the draw of
+// step k + 4 never waits for the MMAs of step k; three frame stages cover a
+// copy's latency at this step rate).
 //   warp 0      TMA (both CTAs): this CTA's segments of each stage, on its
 //               own stage barrier (so each CTA can drain its own copies
 //               before it leaves)
@@ -741,8 +742,8 @@ sketch_tc_packed_kernel(const __grid_constant__ PackArgs a, int* status) {
 //               rows of C x every frame column) to the FP32 partials
 // Segments never cross a 128-row half (the host cuts them there).
 // ---------------------------------------------------------------------------
-constexpr int kQAStages = 3;
-constexpr int kQBStages = 4;
+constexpr int kQAStages = 4;
+constexpr int kQBStages = 3;
 constexpr uint32_t kQBStage = kPackRows * 128u / 2u;     // this CTA's half of 512 B rows
 constexpr uint32_t kQHalf = 128u * 128u;                 // one slot's half: 128 rows x 128 bytes
 
