@@ -342,7 +342,12 @@ cdmd_status cdmd_lift(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t
  * c skipped when negative); its amplitude is beta[s] and eigenvalue
  * lambda[s] (both complex double, length r).  mask bit (j, t) is set iff
  * |D[t*ldd + j] - bg_jt| > tau with bg_jt as selected by `mode`.  bg, if not
- * NULL, receives bg_jt as float, frame-major (bg[t*m + j]). */
+ * NULL, receives bg_jt as float, frame-major (bg[t*m + j]).
+ * Mask-only MODULUS and REAL calls (bg NULL) with 32 <= n <= 1024, at most 16
+ * columns and 16-byte aligned D, ldd and Phi run on the tensor cores, with
+ * the background formed from BF16 hi + lo parts (about 2^-16 relative per
+ * term): a decision within about a hundredth of a grey level of tau may
+ * differ from that of a call with a background output, which sums in FP32. */
 cdmd_status cdmd_subtract(cdmd_ctx* ctx, const uint8_t* D, int64_t m, int n, int64_t ldd,
                           const float* Phi, int ncols, const int32_t* cols,
                           const double* beta, const double* lambda, int r,
