@@ -61,7 +61,7 @@ constexpr int kTile = 128;                     // pixels per tensor copy (one ti
 constexpr int kMaxModes = 16;                  // terms per part: 3 x 16 words <= 2 K atoms
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kATile = 128u * 128u;       // one K atom of A: 128 rows x 128 bytes
-constexpr uint32_t kBAtom = 2u * kPix * 128u;  // one K atom of B: 128 rows (B, B') x 128 bytes
+constexpr uint32_t kBAtom = 2u * kPix * 128u;  // one K atom of B: 128 rows x 128 bytes (128 pixels, or 64 and their (v, -u) rows)
 constexpr uint32_t kPhiStage = kTile * kMaxModes * 8u;
 constexpr int kMaxStages = 6;
 constexpr int kMaxAcc = 4;
