@@ -98,10 +98,12 @@ typedef enum {
 /* Arithmetic of the two contractions (sketch and lift).
  *   FP32    CUDA-core FP32 FMA, FP32 partial sums over pixel chunks reduced
  *           in FP64.
- *   BF16X2  tcgen05 tensor cores: uint8 pixels are exact in BF16, the real
- *           operand (Gaussian C or G) is split into hi + lo BF16 parts
- *           (Rademacher C, +1 / -1, is exact and takes one product), FP32
- *           accumulation in tensor memory. */
+ *   BF16X2  tcgen05 tensor cores: the sketch's uint8 pixels are exact in
+ *           BF16 and its Gaussian C is split into hi + lo BF16 parts
+ *           (Rademacher C, +1 / -1, is exact and takes one product); the
+ *           lift's pixels are exact in FP16 and G, scaled by a power of two
+ *           per mode, is split into hi + lo FP16 parts.  FP32 accumulation
+ *           in tensor memory. */
 typedef enum { CDMD_PREC_FP32 = 0, CDMD_PREC_BF16X2 = 1 } cdmd_prec;
 
 /* Background of pixel j in frame t from the selected modes S:
@@ -328,7 +330,8 @@ cdmd_status cdmd_decompose_auto(cdmd_ctx* ctx, const double* DY, int k, int n, i
 /* Phi[j*ncols + c] = sum_{t=0}^{n-2} D[(t+1)*ldd + j] * G[:, cols[c]] for the
  * ncols modes listed in `cols` (device int32, NULL = modes 0..ncols-1; a
  * negative entry yields a zero column).  G: (n-1) x r complex double.
- * Phi: m x ncols complex float, pixel-major.  ncols <= 64.  BF16X2 needs a
+ * Phi: m x ncols complex float, pixel-major.  ncols <= 64.  BF16X2 (FP16
+ * hi + lo parts of G on the tensor cores, about 2^-21 relative) needs a
  * 16-byte aligned D and ldd % 16 == 0 (else CDMD_ERR_INVALID_ARG); clips
  * longer than 256 frames are lifted in chunks of at most 255 frames of X',
  * the later chunks adding into Phi (the product is linear in the frames). */

@@ -339,9 +339,11 @@ def test_sketch_bf16x2_rejects_unaligned_stride(C, ctx):
                                            (33, 9, 256, 30, list(range(29, 9, -1))), (300, 40, 2, 1, [0]),
                                            (48, 20, 300, 12, list(range(12))), (40, 16, 511, 6, [5, 0, 3])])
 def test_lift_bf16x2(C, ctx, w, h, n, r, modes):
-    # G in BF16 hi+lo (2^-16 relative), pixels exact: each Phi column within
-    # 5e-5 of the FP64 oracle in 2-norm.  Clips past 256 frames are lifted in
-    # chunks of at most 255 frames, the later chunks adding into Phi.
+    # G scaled by a power of two per mode and split into FP16 hi+lo (about
+    # 2^-21 relative), pixels exact in FP16: each Phi column within 5e-5 of
+    # the FP64 oracle in 2-norm (G of size 1e-7 exercises the scaling).
+    # Clips past 256 frames are lifted in chunks of at most 255 frames, the
+    # later chunks adding into Phi.
     clip = videogen.make_clip(w, h, n, seed=n + r)
     m = clip.m
     ldd = (m + 15) // 16 * 16
