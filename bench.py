@@ -1038,7 +1038,8 @@ def run_ours(args, rank, world, local_rank):
                        "measurement": ("gaussian (Philox4x32-10, in-kernel); one C for all clips"
                                        + (", one draw of C feeds every frame of a packed launch"
                                           if cps > 1 else "")),
-                       "precision": ("sketch+lift BF16 hi+lo on tcgen05, FP32 accumulation; FP64 small solves"
+                       "precision": ("sketch BF16 hi+lo, lift FP16 hi+lo (G scaled per mode) on tcgen05, FP32 "
+                                     "accumulation; FP64 small solves"
                                      if args.prec == "bf16x2" else "sketch+lift FP32 FMA; FP64 small solves"),
                        "l2": f"clip {m * n / 1e6:.0f} MB each vs 129 MB L2 (no flush)",
                        "parallelism": (f"clips x{world * cps} ({cps} per GPU per step), {len(lanes)} steps in flight "
