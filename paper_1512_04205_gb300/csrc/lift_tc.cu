@@ -154,8 +154,9 @@ lift_tc_kernel(const __grid_constant__ CUtensorMap tmap, int64_t m, int n, const
             inv_scale[c] = static_cast<float>(ldexp(1.0, -sh));
         }
     }
-    // frames p .. kpad-1 of both A tiles stay zero (G is zero there, and the
-    // converters never write them)
+    // frames p .. kpad-1 of both A tiles are zeroed once (the converters never
+    // write them): B is zero there, but uninitialised shared memory could hold
+    // FP16 infinities or NaNs, which a zero factor does not cancel
     for (int idx = tid; idx < 2 * (L.kpad - p) * 16; idx += kThreads) {
         const int a = idx / ((L.kpad - p) * 16);
         const int rem = idx % ((L.kpad - p) * 16);
